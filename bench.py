@@ -1,0 +1,337 @@
+"""Throughput benchmark of the fast discrete Walsh transform pipeline on GB300.
+
+Workload (default): p = 2, s = 32, m = 24 (N = 16,777,216 net points), a batch
+of 32 FP32 product functions f(x) = prod_j (1 + (x_j - 1/2)/j^2) evaluated on
+the net on the device, spectral weight prod_j (1 + k_j)^-2.  One step is the
+whole hot path over the batch: forward transform (Algorithm 1), scaling,
+weighting, the truncation / superposition variance classes with the effective
+dimensions, and the inverse transform (Algorithm 2) -- one dwt_interpolate
+call.  The plan (net, K(C) tables) is built once beforehand and timed apart.
+
+Inputs (2 GiB) are larger than the 126 MB L2, so no flush is needed between
+steps.  Multi-GPU: each rank runs its own batch on its own GPU with no
+collective (the functions are independent), scaling is "weak".
+
+``--impl reference`` times the CPU oracle (the FP64 restatement of the paper
+in oracle/) on a bounded sample of the same workload on the host cores.
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "net points/s (p=2, m=24, s=32, batch 32: forward + weight + effdim + inverse)"
+UNIT = "points/s"
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.Q, "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [x.strip() for x in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx = float(parts[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def _peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        d = json.load(open(path))
+        return d.get("hbm_gbs", 6800.0), "measured"
+    return 6800.0, "fallback"
+
+
+def run_reference(args):
+    """The CPU oracle on a bounded sample of the same workload (one function)."""
+    import numpy as np
+
+    import oracle
+    import synthetic as S
+
+    ws, rank, _ = _dist()
+    if rank != 0:
+        return
+    w = S.workload_p2_m24(batch=1)
+    p, m, s = w["p"], w["m"], w["s"]
+    N = p ** m
+    oracle.lib()
+    # input function: oracle net points and the product function (untimed)
+    Y = oracle.net_points(p, m, w["C"])
+    f = oracle.eval_product(p, m, Y, w["coef"][0])
+    del Y
+    # The timed oracle work (Algorithm 1, weight, class sums, Algorithm 2) does not
+    # depend on the table values, so the plan-time K(C) tables (excluded from the
+    # metric on both arms) are replaced by constants of the same shape here.
+    W = np.ones(N)
+    cls = np.zeros((N, 2), dtype=np.uint8)
+    times = []
+    for _ in range(max(1, args.steps)):
+        t0 = time.perf_counter()
+        oracle.interpolate(p, m, f, W, cls, s)
+        times.append(time.perf_counter() - t0)
+    t = statistics.median(times)
+    value = N / t
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": len(times), "warmup": 0, "ms_per_step": t * 1e3, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": "p2_m24_s32_b32", "p": 2, "m": 24, "s": 32, "global_batch": 32,
+                   "l2": "inputs larger than L2"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": "1 of 32 functions (N=2^24) per step, single thread; value scaled per point"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def cpu_baseline_sample():
+    """Oracle time for one function of the workload (about 10-20 s on one core)."""
+    import numpy as np
+
+    import oracle
+    import synthetic as S
+
+    w = S.workload_p2_m24(batch=1)
+    p, m, s = w["p"], w["m"], w["s"]
+    N = p ** m
+    Y = oracle.net_points(p, m, w["C"])
+    f = oracle.eval_product(p, m, Y, w["coef"][0])
+    del Y
+    W = np.ones(N)
+    cls = np.zeros((N, 2), dtype=np.uint8)
+    t0 = time.perf_counter()
+    oracle.interpolate(p, m, f, W, cls, s)
+    t = time.perf_counter() - t0
+    return {"value": N / t, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": "1 of 32 functions (N=2^24), forward+weight+class sums+inverse in FP64, single thread; "
+                      "K(C) tables replaced by constants (plan time excluded on both arms)"}
+
+
+def run_gpu(args):
+    import numpy as np
+    import torch
+
+    import paper_0808_0487_gb300 as dwt
+    import synthetic as S
+
+    ws, rank, local = _dist()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    pg = None
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+        pg = dist
+    dwt.lib()
+    B = args.batch
+    w = S.workload_p2_m24(batch=B)
+    p, m, s = w["p"], w["m"], w["s"]
+    N = p ** m
+    stream = torch.cuda.current_stream()
+
+    t0 = time.perf_counter()
+    plan = dwt.dwt_plan_create(p, m, s, w["C"])
+    plan_ms = (time.perf_counter() - t0) * 1e3
+
+    f = torch.empty((B, N), dtype=torch.float32, device=dev)
+    coef = torch.tensor(w["coef"], dtype=torch.float64, device=dev)
+    dwt.dwt_eval_product(plan, coef, f, B, N, dwt.DWT_F32)
+    c = torch.empty_like(f)
+    var = torch.empty((B, 2, s + 1), dtype=torch.float64, device=dev)
+    dim = torch.empty((B, 2), dtype=torch.int32, device=dev)
+    torch.cuda.synchronize()
+
+    def step():
+        dwt.dwt_interpolate(plan, f, c, None, B, N, dwt.DWT_F32, dwt.DWT_WEIGHT_INV_SQ_WAVENUMBER,
+                            var=var, dim=dim, stream=stream)
+
+    def timed(fn, K):
+        for _ in range(args.warmup):
+            fn()
+        if pg:
+            pg.barrier()
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        l0 = dwt.dwt_launch_count()
+        e0.record(stream)
+        for _ in range(K):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        launches = dwt.dwt_launch_count() - l0
+        if pg:
+            pg.barrier()
+        ms = e0.elapsed_time(e1)
+        if pg:
+            t = torch.tensor([ms], device=dev)
+            pg.all_reduce(t, op=pg.ReduceOp.MAX)
+            ms = float(t.item())
+        return ms, launches
+
+    with ClockSampler(local) as clk:
+        ms, launches = timed(step, args.steps)
+    clocks = clk.summary()
+    pts = B * N * args.steps * ws
+    value = pts / (ms / 1e3)
+
+    # forward / inverse alone (extra context)
+    def fwd():
+        dwt.dwt_forward(plan, f, c, B, N, N, dwt.DWT_F32, dwt.DWT_F32, stream=stream)
+
+    def inv():
+        dwt.dwt_inverse(plan, c, c, B, N, N, dwt.DWT_F32, dwt.DWT_F32, stream=stream)
+
+    ms_f, _ = timed(fwd, args.steps)
+    ms_i, _ = timed(inv, args.steps)
+    peak, peak_kind = _peaks()
+
+    # per-kernel durations of the same step with events around every launch
+    dwt.dwt_profile_reset()
+    dwt.dwt_profile_enable(True)
+    ms_prof, _ = timed(step, args.steps)
+    dwt.dwt_profile_enable(False)
+    fams = {}
+    for name in ("interp_fwd", "interp_top", "interp_inv", "effdim_finalize"):
+        n, tot = dwt.dwt_profile_query(name)
+        if n:
+            fams[name] = (n, tot)
+    dom = max(fams, key=lambda k: fams[k][1]) if fams else None
+    # algorithmic bytes per launch: every launch covers one function of N points
+    bytes_per_point = {"interp_fwd": 8.0, "interp_top": 14.0, "interp_inv": 8.0}
+    roof = None
+    if dom in bytes_per_point:
+        n, tot = fams[dom]
+        avg_s = tot / n / 1e3
+        ach = bytes_per_point[dom] * N / avg_s / 1e9
+        roof = {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
+                "traffic": None, "kernel": dom, "peak_kind": peak_kind,
+                "avg_launch_us": avg_s * 1e6, "launches": n,
+                "bytes_per_point": bytes_per_point[dom]}
+    dwt.dwt_profile_reset()
+
+    # end to end: pinned host f -> device, the step, c and the variances back
+    fh = torch.empty((B, N), dtype=torch.float32, pin_memory=True)
+    fh.copy_(f)
+    ch = torch.empty((B, N), dtype=torch.float32, pin_memory=True)
+    vh = torch.empty((B, 2, s + 1), dtype=torch.float64, pin_memory=True)
+    dh = torch.empty((B, 2), dtype=torch.int32, pin_memory=True)
+
+    def e2e_step():
+        f.copy_(fh, non_blocking=True)
+        step()
+        ch.copy_(c, non_blocking=True)
+        vh.copy_(var, non_blocking=True)
+        dh.copy_(dim, non_blocking=True)
+
+    K2 = max(1, min(args.steps, 5))
+    ms_e2e, _ = timed(e2e_step, K2)
+    e2e_value = B * N * K2 * ws / (ms_e2e / 1e3)
+
+    cpu = None
+    if rank == 0 and not args.no_cpu:
+        cpu = cpu_baseline_sample()
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "p2_m24_s32_b%d" % B, "p": p, "m": m, "s": s, "global_batch": B * ws,
+                       "N": N, "weight": "prod_j (1+k_j)^-2", "l2": "inputs larger than L2 (2 GiB per rank)",
+                       "parallelism": "replicas" if ws > 1 else "single"},
+            "roofline": roof,
+            "cpu_baseline": cpu,
+            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": B * N * 4,
+                    "d2h_bytes_per_step": B * N * 4 + B * 2 * (s + 1) * 8 + B * 2 * 4},
+            "gpu_launches": launches,
+            "clocks": clocks,
+            "plan_build_ms": plan_ms,
+            "forward_points_per_s": B * N * args.steps * ws / (ms_f / 1e3),
+            "inverse_points_per_s": B * N * args.steps * ws / (ms_i / 1e3),
+            "forward_hbm_frac": (B * N * args.steps * 8 / (ms_f / 1e3) / 1e9) / peak,
+            "inverse_hbm_frac": (B * N * args.steps * 8 / (ms_i / 1e3) / 1e9) / peak,
+            "step_hbm_frac_algorithmic": (B * N * args.steps * (8 + 6.0 / B) / (ms / 1e3) / 1e9) / peak,
+            "kernel_ms": {k: v[1] / v[0] for k, v in fams.items()},
+        }
+        print(json.dumps(line), flush=True)
+    if pg:
+        pg.barrier()
+        pg.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--batch", type=int, default=32)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline leg")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_gpu(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,203 @@
+/*
+ * dwt.h -- C ABI of libdwt, a GB300 (sm_103a) library for the multivariate
+ * fast discrete Walsh transform over digital (t,m,s)-nets and its inverse,
+ * after K.-I. Liu, J. Dick and F. J. Hickernell, "A Multivariate Fast Discrete
+ * Walsh Transform with an Application to Function Interpolation".
+ *
+ * Notation: p prime, m digits, s dimension, N = p^m.  Data f_n are indexed by
+ * n = n_0 + n_1 p + ... + n_{m-1} p^{m-1} (the net point x_n of Def. 1.1);
+ * coefficients are indexed by the coset label H = h_0 + h_1 p + ... with
+ * (h_0..h_{m-1}) = C . k (Sec. 2.1), k being the representative of that coset
+ * in K(C): least nu(k), ties broken by the lexicographically smallest
+ * (k_1, ..., k_s) compared as integers.
+ *
+ * Conventions for every call:
+ *  - Pointers named "device" are CUDA device (or managed) memory owned by the
+ *    caller; the library never frees them.  Host pointers are plain memory.
+ *  - Array arguments are row-major; "ld" is the distance in ELEMENTS between
+ *    consecutive functions of a batch (ld >= N; 16-byte alignment of every
+ *    function start gives the fastest path, any ld works).
+ *  - Complex data (DWT_C64, DWT_C128) is interleaved (re, im).
+ *  - Calls are asynchronous on "stream" (a cudaStream_t, NULL = legacy
+ *    default stream) unless stated otherwise.  dwt_plan_create synchronises.
+ *  - Status codes are returned, never thrown.  After a failed call the outputs
+ *    are unspecified and the plan stays usable, except after DWT_ECUDA, which
+ *    reports a sticky CUDA error.  dwt_last_error() gives a message for the
+ *    last failure of the calling thread.
+ *  - The library runs every step of every call in its own CUDA kernels; it has
+ *    no CPU fallback.
+ */
+#ifndef DWT_H
+#define DWT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ---- */
+#define DWT_OK 0
+#define DWT_EINVAL 1        /* bad argument: p not prime, p^m > 2^31, entry of C >= p, s < 1, ... */
+#define DWT_ESPAN 2         /* rows of C_1..C_s do not span F_p^m: some coset is empty, K(C) undefined */
+#define DWT_ENOMEM 3        /* device or host allocation failed */
+#define DWT_ECUDA 4         /* a CUDA call failed (message in dwt_last_error) */
+#define DWT_ETIMEOUT 5      /* a bounded device-side wait expired */
+#define DWT_EBUSY 6         /* serving queue full */
+#define DWT_EUNSUPPORTED 7  /* valid request this build does not serve (e.g. I32 with p != 2) */
+
+typedef enum { DWT_F32 = 0, DWT_F64 = 1, DWT_I32 = 2, DWT_C64 = 3, DWT_C128 = 4 } dwt_dtype;
+typedef enum { DWT_ALGO_AUTO = 0, DWT_ALGO_BUTTERFLY = 1, DWT_ALGO_TC_SPLIT_BF16 = 2 } dwt_algo;
+typedef enum { DWT_WEIGHT_NONE = 0, DWT_WEIGHT_INV_SQ_WAVENUMBER = 1 } dwt_weight;
+
+/* plan flags */
+#define DWT_PLAN_TRANSFORM_ONLY 1u  /* build no K(C) tables: forward/inverse/points/k->H only */
+#define DWT_PLAN_KEEP_INDEX_MAP 2u  /* keep the coset tables needed by dwt_index_to_wavenumber */
+
+typedef struct dwt_plan_s *dwt_plan_t;
+
+/*
+ * Build a plan for the digital net P(C) of Def. 1.1 (eq. defy).
+ *   p: prime, 2 <= p <= 7;  m >= 1 with p^m <= 2^31;  1 <= s <= 255.
+ *   C: HOST array uint8 [s][m][m], C[j][i][c] in 0..p-1.  Row i of C_j gives
+ *      the point digit y_{j,n,i+1}; column c multiplies the index digit n_c.
+ *   flags: DWT_PLAN_* bits.
+ * Unless DWT_PLAN_TRANSFORM_ONLY is set, the plan computes on the device the
+ * coset representatives k(H) of K(C) (Sec. 2.1) and keeps two tables per H:
+ * the weight W[H] = prod_j (1 + k_j(H))^-2 as FP32, rounded as
+ * RN_f32(1 / RN_f32(prod_j (1+k_j)^2)) from the exact integer product, and the
+ * class (max{j : k_j != 0} counted from 1, #{j : k_j != 0}).
+ * Returns DWT_ESPAN (plan still created, transform calls allowed) when the
+ * rows of C do not span F_p^m, DWT_EUNSUPPORTED (plan still created) when a
+ * least nu reaches 255 or a weight denominator exceeds 64 bits.  On any other
+ * failure *plan is NULL.  Synchronises "stream".
+ */
+int dwt_plan_create(int p, int m, int s, const uint8_t *C, unsigned flags, void *stream, dwt_plan_t *plan);
+
+/* Free a plan and its device tables (synchronises the device). NULL is ignored. */
+int dwt_plan_destroy(dwt_plan_t plan);
+
+/* Plan facts: p, m, s, N, and the status of its coset tables (DWT_OK,
+ * DWT_ESPAN, DWT_EUNSUPPORTED, or -1 when built with TRANSFORM_ONLY). Any
+ * output pointer may be NULL. */
+int dwt_plan_info(dwt_plan_t plan, int *p, int *m, int *s, long long *N, int *tables_status);
+
+/* Device pointers to the plan's tables: W[N] (float) and cls[N][2] (uint8, max
+ * support then support size).  Owned by the plan; valid until destroy. */
+int dwt_plan_tables(dwt_plan_t plan, const float **W, const uint8_t **cls);
+
+/*
+ * Net points of Def. 1.1: Y[j*ldY + n] = sum_{i=1}^m y_{j,n,i} p^{m-i}
+ * (uint32, device [s][ldY], ldY >= N), so x_{j,n} = Y / p^m exactly.
+ */
+int dwt_points(dwt_plan_t plan, uint32_t *Y, long long ldY, void *stream);
+
+/*
+ * Coset label of wavenumber vectors (Sec. 2.1): H = C . k = sum_j C_j^T k_j^{(m)}
+ * over F_p, digits of k_j at positions >= m dropped.
+ *   k: device uint32 [cnt][s];  H: device uint32 [cnt].
+ */
+int dwt_wavenumber_to_index(dwt_plan_t plan, const uint32_t *k, uint32_t *H, long long cnt, void *stream);
+
+/*
+ * Representative k(H) in K(C) of each coset label (Sec. 2.1).
+ *   H: device uint32 [cnt], each < N;  k: device uint32 [cnt][s].
+ * Needs a plan built with DWT_PLAN_KEEP_INDEX_MAP (else DWT_EUNSUPPORTED).
+ */
+int dwt_index_to_wavenumber(dwt_plan_t plan, const uint32_t *H, uint32_t *k, long long cnt, void *stream);
+
+/*
+ * Forward transform, Algorithm 1 with eq. (fdwt):
+ *   out[H] = f~(H) = p^{-m} sum_n in[n] omega^{-(n . h)},  omega = e^{2 pi i / p},
+ * for each of "batch" functions (in at in + b*ld_in, out at out + b*ld_out).
+ * Output in natural H order; in == out (same ld) is allowed when the element
+ * sizes agree.  Types:
+ *   p = 2: in_t = out_t = DWT_F32 or DWT_F64; or DWT_I32 -> DWT_I32, which
+ *          returns G^{(m)} without the factor 2^{-m} (exact; the caller keeps
+ *          N * max|in| < 2^31).
+ *   p > 2: in_t DWT_F32 (real) or DWT_C64 -> out_t DWT_C64; in_t DWT_F64 or
+ *          DWT_C128 -> out_t DWT_C128.
+ * algo: DWT_ALGO_TC_SPLIT_BF16 (p = 2, F32 only) runs the Hadamard stages as
+ * tensor-core tile products on hi/lo BF16 splits with FP32 accumulation.
+ */
+int dwt_forward(dwt_plan_t plan, const void *in, void *out, int batch, long long ld_in, long long ld_out,
+                dwt_dtype in_t, dwt_dtype out_t, dwt_algo algo, void *stream);
+
+/*
+ * Inverse transform, Algorithm 2 (Lemma 3.1):
+ *   out[n] = c_n = sum_H in[H] omega^{+(h . n)}   (no factor),
+ * so dwt_inverse(dwt_forward(f)) = f.  Types as for dwt_forward, except that
+ * for p > 2 the input is complex (DWT_C64 or DWT_C128) and so is the output;
+ * for DWT_I32 the result is D^{(m)} (forward then inverse gives N * f).
+ */
+int dwt_inverse(dwt_plan_t plan, const void *in, void *out, int batch, long long ld_in, long long ld_out,
+                dwt_dtype in_t, dwt_dtype out_t, dwt_algo algo, void *stream);
+
+/*
+ * Spectral weighting and effective dimension in one call (Sec. 3.2-3.3, Sec. 4):
+ *   f~ = forward(f);  g(H) = w(H) f~(H);  c = inverse(g);
+ *   var[b][0][d] = sum_{H != 0, max supp k(H) <= d} |g(H)|^2,
+ *   var[b][1][d] = sum_{H != 0, |supp k(H)| <= d} |g(H)|^2,   d = 0..s,
+ *   dim[b][0] = least d with var[b][0][d] >= threshold * var[b][0][s] (0 if that is 0),
+ *   dim[b][1] = the same with var[b][1].
+ * The weight w is 1 (DWT_WEIGHT_NONE: then c = f, the interpolation property)
+ * or the plan's W[H] (DWT_WEIGHT_INV_SQ_WAVENUMBER).  The variances of the
+ * finite Walsh series sum_H g(H) wal_{k(H)} split by ANOVA support exactly so.
+ *   f: device, ld elements per function, type f_t (p = 2: DWT_F32;
+ *      p > 2: DWT_F32 real input or DWT_C64);
+ *   c: device output, ld elements per function (p = 2: float, p > 2: complex
+ *      float); may equal f when the element sizes agree;
+ *   coef: optional device output of g (same layout as c), or NULL;
+ *   var: optional device double [batch][2][s+1], or NULL;
+ *   dim: optional device int [batch][2], or NULL;
+ *   threshold: in (0, 1], 0.99 in the paper.
+ * Variance sums use per-lane FP32 partials inside a tile, then FP64 in a
+ * fixed order, so results do not depend on scheduling.  Needs plan tables
+ * (DWT_ESPAN / DWT_EUNSUPPORTED otherwise).
+ */
+int dwt_interpolate(dwt_plan_t plan, const void *f, void *c, void *coef, int batch, long long ld,
+                    dwt_dtype f_t, dwt_weight weight, dwt_algo algo, double *var, int *dim,
+                    double threshold, void *stream);
+
+/*
+ * Effective dimension of given coefficients g (Sec. 4), the variance and
+ * threshold part of dwt_interpolate alone.  coef: device, type DWT_F32
+ * (p = 2) or DWT_C64, ld elements per function.  var/dim as above (device).
+ */
+int dwt_effdim(dwt_plan_t plan, const void *coef, int batch, long long ld, dwt_dtype t, double *var,
+               int *dim, double threshold, void *stream);
+
+/*
+ * Synthetic test functions at the net points (for workloads and tests):
+ *   dwt_eval_product: f_b(x_n) = prod_j (1 + coef[b][j] (x_{j,n} - 1/2)),
+ *     coef: device double [batch][s];
+ *   dwt_eval_exp: f_b(x_n) = exp(sum_j x_{j,n} / j^2) (j from 1), every b.
+ * Output f: device, DWT_F32 or DWT_F64, ld elements per function.
+ */
+int dwt_eval_product(dwt_plan_t plan, const double *coef, void *f, int batch, long long ld, dwt_dtype t,
+                     void *stream);
+int dwt_eval_exp(dwt_plan_t plan, void *f, int batch, long long ld, dwt_dtype t, void *stream);
+
+/* Messages. */
+const char *dwt_strerror(int status);
+const char *dwt_last_error(void);
+
+/* Number of kernels this library has launched in this process. */
+long long dwt_launch_count(void);
+
+/*
+ * Optional per-kernel timing with CUDA events recorded on the launching stream
+ * around every launch of this library.  dwt_profile_query synchronises on the
+ * recorded events and returns, for kernel family "name" (see DESIGN notes in
+ * the source: "pass_lo", "pass_hi", "pass_mid", ...), the number of launches
+ * and their summed duration in milliseconds since the last reset.
+ */
+int dwt_profile_enable(int on);
+int dwt_profile_reset(void);
+int dwt_profile_query(const char *name, long long *launches, double *total_ms);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* DWT_H */

@@ -1,0 +1,249 @@
+"""Python binding of libdwt: the multivariate fast discrete Walsh transform over
+digital nets on GB300 (sm_103a).
+
+This module only marshals arguments: every step of every call runs in the CUDA
+kernels of ``libdwt.so`` behind the C ABI declared in ``include/dwt.h``.  The
+functions keep the C names.  Tensors (anything with ``data_ptr()``) or raw
+integer addresses may be passed wherever the C call takes a pointer; streams
+may be ``None`` (torch's current stream), a ``torch.cuda.Stream`` or an integer
+``cudaStream_t``.
+
+There is no fallback: if the library is missing, every call raises.
+"""
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libdwt.so")
+
+# status codes
+DWT_OK = 0
+DWT_EINVAL = 1
+DWT_ESPAN = 2
+DWT_ENOMEM = 3
+DWT_ECUDA = 4
+DWT_ETIMEOUT = 5
+DWT_EBUSY = 6
+DWT_EUNSUPPORTED = 7
+# dtypes
+DWT_F32, DWT_F64, DWT_I32, DWT_C64, DWT_C128 = 0, 1, 2, 3, 4
+# algorithms
+DWT_ALGO_AUTO, DWT_ALGO_BUTTERFLY, DWT_ALGO_TC_SPLIT_BF16 = 0, 1, 2
+# weights
+DWT_WEIGHT_NONE, DWT_WEIGHT_INV_SQ_WAVENUMBER = 0, 1
+# plan flags
+DWT_PLAN_TRANSFORM_ONLY = 1
+DWT_PLAN_KEEP_INDEX_MAP = 2
+
+_lib = None
+
+
+class DwtError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__("%s (status %d): %s" % (_strerror(status), status, msg))
+        self.status = status
+
+
+_VP = ctypes.c_void_p
+_LL = ctypes.c_longlong
+_I = ctypes.c_int
+
+_SIGS = {
+    "dwt_plan_create": (_I, [_I, _I, _I, _VP, ctypes.c_uint, _VP, ctypes.POINTER(_VP)]),
+    "dwt_plan_destroy": (_I, [_VP]),
+    "dwt_plan_info": (_I, [_VP, _VP, _VP, _VP, _VP, _VP]),
+    "dwt_plan_tables": (_I, [_VP, ctypes.POINTER(_VP), ctypes.POINTER(_VP)]),
+    "dwt_points": (_I, [_VP, _VP, _LL, _VP]),
+    "dwt_wavenumber_to_index": (_I, [_VP, _VP, _VP, _LL, _VP]),
+    "dwt_index_to_wavenumber": (_I, [_VP, _VP, _VP, _LL, _VP]),
+    "dwt_forward": (_I, [_VP, _VP, _VP, _I, _LL, _LL, _I, _I, _I, _VP]),
+    "dwt_inverse": (_I, [_VP, _VP, _VP, _I, _LL, _LL, _I, _I, _I, _VP]),
+    "dwt_interpolate": (_I, [_VP, _VP, _VP, _VP, _I, _LL, _I, _I, _I, _VP, _VP, ctypes.c_double, _VP]),
+    "dwt_effdim": (_I, [_VP, _VP, _I, _LL, _I, _VP, _VP, ctypes.c_double, _VP]),
+    "dwt_eval_product": (_I, [_VP, _VP, _VP, _I, _LL, _I, _VP]),
+    "dwt_eval_exp": (_I, [_VP, _VP, _I, _LL, _I, _VP]),
+    "dwt_strerror": (ctypes.c_char_p, [_I]),
+    "dwt_last_error": (ctypes.c_char_p, []),
+    "dwt_launch_count": (_LL, []),
+    "dwt_profile_enable": (_I, [_I]),
+    "dwt_profile_reset": (_I, []),
+    "dwt_profile_query": (_I, [ctypes.c_char_p, ctypes.POINTER(_LL), ctypes.POINTER(ctypes.c_double)]),
+}
+
+
+def lib():
+    """The loaded ``libdwt.so`` (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise DwtError(DWT_EUNSUPPORTED, "libdwt.so is not built; run __graft_entry__.build()")
+        L = ctypes.CDLL(LIB_PATH)
+        for name, (res, args) in _SIGS.items():
+            fn = getattr(L, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = L
+    return _lib
+
+
+def _strerror(status):
+    try:
+        return lib().dwt_strerror(status).decode()
+    except Exception:  # library missing while formatting an error
+        return "status"
+
+
+def _ptr(x):
+    if x is None:
+        return None
+    if hasattr(x, "data_ptr"):
+        return x.data_ptr()
+    if isinstance(x, np.ndarray):
+        return x.ctypes.data
+    return int(x)
+
+
+def _stream(s):
+    if s is None:
+        try:
+            import torch
+            if torch.cuda.is_available():
+                return torch.cuda.current_stream().cuda_stream
+        except ImportError:
+            pass
+        return None
+    if hasattr(s, "cuda_stream"):
+        return s.cuda_stream
+    return int(s)
+
+
+def _check(status, allow=()):
+    if status != DWT_OK and status not in allow:
+        raise DwtError(status, lib().dwt_last_error().decode())
+    return status
+
+
+class Plan:
+    """Owner of a ``dwt_plan_t``; ``status`` holds the coset-table status of creation."""
+
+    def __init__(self, handle, p, m, s, status):
+        self.handle = handle
+        self.p, self.m, self.s = p, m, s
+        self.N = p ** m
+        self.status = status
+
+    @property
+    def _as_parameter_(self):
+        return self.handle
+
+    def close(self):
+        if self.handle:
+            lib().dwt_plan_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def dwt_plan_create(p, m, s, C, flags=0, stream=None):
+    """``dwt_plan_create``: C is a host array uint8 [s][m][m] (numpy)."""
+    C = np.ascontiguousarray(C, dtype=np.uint8)
+    if C.shape != (s, m, m):
+        raise ValueError("C must have shape (s, m, m)")
+    h = _VP()
+    st = lib().dwt_plan_create(p, m, s, C.ctypes.data, flags, _stream(stream), ctypes.byref(h))
+    _check(st, allow=(DWT_ESPAN, DWT_EUNSUPPORTED))
+    return Plan(h.value, p, m, s, st)
+
+
+def dwt_plan_destroy(plan):
+    plan.close()
+    return DWT_OK
+
+
+def dwt_plan_info(plan):
+    p, m, s, t = _I(), _I(), _I(), _I()
+    N = _LL()
+    _check(lib().dwt_plan_info(plan.handle, ctypes.byref(p), ctypes.byref(m), ctypes.byref(s), ctypes.byref(N),
+                               ctypes.byref(t)))
+    return dict(p=p.value, m=m.value, s=s.value, N=N.value, tables_status=t.value)
+
+
+def dwt_plan_tables(plan):
+    """Device addresses (ints) of the plan's W[N] float and cls[N][2] uint8 tables."""
+    W, cls = _VP(), _VP()
+    _check(lib().dwt_plan_tables(plan.handle, ctypes.byref(W), ctypes.byref(cls)))
+    return W.value, cls.value
+
+
+def dwt_points(plan, Y, ldY=None, stream=None):
+    return _check(lib().dwt_points(plan.handle, _ptr(Y), ldY or plan.N, _stream(stream)))
+
+
+def dwt_wavenumber_to_index(plan, k, H, cnt, stream=None):
+    return _check(lib().dwt_wavenumber_to_index(plan.handle, _ptr(k), _ptr(H), cnt, _stream(stream)))
+
+
+def dwt_index_to_wavenumber(plan, H, k, cnt, stream=None):
+    return _check(lib().dwt_index_to_wavenumber(plan.handle, _ptr(H), _ptr(k), cnt, _stream(stream)))
+
+
+def dwt_forward(plan, inp, out, batch, ld_in, ld_out, in_t, out_t, algo=DWT_ALGO_AUTO, stream=None):
+    return _check(lib().dwt_forward(plan.handle, _ptr(inp), _ptr(out), batch, ld_in, ld_out, in_t, out_t, algo,
+                                    _stream(stream)))
+
+
+def dwt_inverse(plan, inp, out, batch, ld_in, ld_out, in_t, out_t, algo=DWT_ALGO_AUTO, stream=None):
+    return _check(lib().dwt_inverse(plan.handle, _ptr(inp), _ptr(out), batch, ld_in, ld_out, in_t, out_t, algo,
+                                    _stream(stream)))
+
+
+def dwt_interpolate(plan, f, c, coef, batch, ld, f_t, weight, algo=DWT_ALGO_AUTO, var=None, dim=None,
+                    threshold=0.99, stream=None):
+    return _check(lib().dwt_interpolate(plan.handle, _ptr(f), _ptr(c), _ptr(coef), batch, ld, f_t, weight, algo,
+                                        _ptr(var), _ptr(dim), threshold, _stream(stream)))
+
+
+def dwt_effdim(plan, coef, batch, ld, t, var=None, dim=None, threshold=0.99, stream=None):
+    return _check(lib().dwt_effdim(plan.handle, _ptr(coef), batch, ld, t, _ptr(var), _ptr(dim), threshold,
+                                   _stream(stream)))
+
+
+def dwt_eval_product(plan, coef, f, batch, ld, t, stream=None):
+    return _check(lib().dwt_eval_product(plan.handle, _ptr(coef), _ptr(f), batch, ld, t, _stream(stream)))
+
+
+def dwt_eval_exp(plan, f, batch, ld, t, stream=None):
+    return _check(lib().dwt_eval_exp(plan.handle, _ptr(f), batch, ld, t, _stream(stream)))
+
+
+def dwt_strerror(status):
+    return lib().dwt_strerror(status).decode()
+
+
+def dwt_last_error():
+    return lib().dwt_last_error().decode()
+
+
+def dwt_launch_count():
+    return lib().dwt_launch_count()
+
+
+def dwt_profile_enable(on=True):
+    return _check(lib().dwt_profile_enable(1 if on else 0))
+
+
+def dwt_profile_reset():
+    return _check(lib().dwt_profile_reset())
+
+
+def dwt_profile_query(name):
+    n = _LL()
+    ms = ctypes.c_double()
+    _check(lib().dwt_profile_query(name.encode(), ctypes.byref(n), ctypes.byref(ms)))
+    return n.value, ms.value

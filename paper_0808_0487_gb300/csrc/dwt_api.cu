@@ -1,0 +1,483 @@
+// dwt_api.cu -- the C ABI of libdwt: plan life cycle, argument checks,
+// dispatch to the kernels, error strings, launch accounting and the optional
+// per-launch event timing.
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <atomic>
+#include <map>
+#include <mutex>
+
+#include "dwt_internal.cuh"
+
+namespace dwt {
+
+static thread_local char g_err[512] = "";
+static std::atomic<long long> g_launches{0};
+
+void set_error(const char* fmt, ...) {
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_err, sizeof g_err, fmt, ap);
+    va_end(ap);
+}
+
+int cuda_fail(cudaError_t e, const char* what, const char* file, int line) {
+    set_error("CUDA error %d (%s) in %s at %s:%d", (int)e, cudaGetErrorString(e), what, file, line);
+    return DWT_ECUDA;
+}
+
+// ---- optional event timing ------------------------------------------------
+struct ProfRec {
+    const char* fam;
+    cudaEvent_t a, b;
+};
+static std::mutex g_prof_mu;
+static bool g_prof_on = false;
+static std::vector<ProfRec> g_prof_open;   // started, not yet closed (stack per call site)
+static std::vector<ProfRec> g_prof_done;
+static std::vector<cudaEvent_t> g_ev_pool;
+
+static cudaEvent_t ev_get() {
+    if (!g_ev_pool.empty()) {
+        cudaEvent_t e = g_ev_pool.back();
+        g_ev_pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    cudaEventCreate(&e);
+    return e;
+}
+
+void launch_begin(const char* fam, cudaStream_t st) {
+    g_launches.fetch_add(1, std::memory_order_relaxed);
+    if (!g_prof_on) return;
+    std::lock_guard<std::mutex> lk(g_prof_mu);
+    ProfRec r{fam, ev_get(), ev_get()};
+    cudaEventRecord(r.a, st);
+    g_prof_open.push_back(r);
+}
+
+void launch_end(const char* fam, cudaStream_t st) {
+    if (!g_prof_on) return;
+    std::lock_guard<std::mutex> lk(g_prof_mu);
+    for (size_t i = g_prof_open.size(); i-- > 0;) {
+        if (g_prof_open[i].fam == fam) {
+            ProfRec r = g_prof_open[i];
+            g_prof_open.erase(g_prof_open.begin() + (long)i);
+            cudaEventRecord(r.b, st);
+            g_prof_done.push_back(r);
+            return;
+        }
+    }
+}
+
+// ---- workspace ----------------------------------------------------------------
+int ensure_workspace(dwt_plan_s* P, size_t bytes) {
+    if (bytes <= P->ws_bytes) return DWT_OK;
+    if (P->d_ws) {
+        DWT_CK(cudaDeviceSynchronize());
+        cudaFree(P->d_ws);
+        P->d_ws = nullptr;
+        P->ws_bytes = 0;
+    }
+    size_t want = bytes < ((size_t)1 << 20) ? ((size_t)1 << 20) : bytes;
+    cudaError_t e = cudaMalloc(&P->d_ws, want);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        set_error("workspace allocation of %zu bytes failed", want);
+        return DWT_ENOMEM;
+    }
+    P->ws_bytes = want;
+    return DWT_OK;
+}
+
+// ---- pass decomposition ---------------------------------------------------------
+// The transform is the Kronecker power of the p-point DFT over the m digits, so
+// digits may be grouped into passes freely.  Pass 0 takes the low digits as one
+// contiguous run of p^b elements; later passes take p^b rows spaced p^d0 apart,
+// Wc consecutive low indices wide, so that every row is a contiguous segment.
+static const size_t kTileBudget = 64 * 1024;   // bytes of shared memory per tile
+
+static void make_pass_plan(int p, int m, int elem, dwt::PassPlan& pp) {
+    long long cap = (long long)(kTileBudget / (size_t)elem);
+    int wc_max = elem >= 8 ? 8 : 16;
+    int blo = 0;
+    while (dwt::ipow_ll(p, blo + 1) <= cap) ++blo;
+    int bhi = 0;
+    while (dwt::ipow_ll(p, bhi + 1) * wc_max <= cap) ++bhi;
+    pp.q = 0;
+    if (m <= blo) {
+        pp.g[0].d0 = 0;
+        pp.g[0].b = m;
+        pp.q = 1;
+    } else {
+        // fewest passes: a low pass of blo digits, the rest shared evenly by nh high passes
+        int nh = 1;
+        while (blo + nh * bhi < m) ++nh;
+        int rest = m - blo, d = blo;
+        pp.g[0].d0 = 0;
+        pp.g[0].b = blo;
+        for (int t = 0; t < nh; ++t) {
+            int b = rest / nh + (t < rest % nh ? 1 : 0);
+            pp.g[t + 1].d0 = d;
+            pp.g[t + 1].b = b;
+            d += b;
+        }
+        pp.q = nh + 1;
+    }
+    long long N = dwt::ipow_ll(p, m);
+    for (int t = 0; t < pp.q; ++t) {
+        PassGeom& g = pp.g[t];
+        g.S = dwt::ipow_ll(p, g.d0);
+        g.R = (int)dwt::ipow_ll(p, g.b);
+        int wc = 1;
+        if (g.d0 > 0) {
+            while (wc * 2 <= wc_max && wc * 2 <= g.S && (long long)g.R * wc * 2 <= cap) wc *= 2;
+        }
+        g.Wc = wc;
+        g.wlog = 0;
+        while ((1 << g.wlog) < wc) ++g.wlog;
+        g.nlo = (g.S + wc - 1) / wc;
+        g.ntile = g.nlo * (N / (g.S * g.R));
+    }
+}
+
+const PassPlan& pass_plan(dwt_plan_s* P, int elem_bytes) {
+    int idx = elem_bytes == 4 ? 0 : elem_bytes == 8 ? 1 : 2;
+    return P->passes[idx];
+}
+
+static bool is_prime_small(int p) { return p == 2 || p == 3 || p == 5 || p == 7; }
+
+}  // namespace dwt
+
+using namespace dwt;
+
+extern "C" {
+
+const char* dwt_strerror(int status) {
+    switch (status) {
+        case DWT_OK: return "ok";
+        case DWT_EINVAL: return "invalid argument";
+        case DWT_ESPAN: return "rows of the generating matrices do not span F_p^m";
+        case DWT_ENOMEM: return "out of memory";
+        case DWT_ECUDA: return "CUDA error";
+        case DWT_ETIMEOUT: return "device-side wait timed out";
+        case DWT_EBUSY: return "queue full";
+        case DWT_EUNSUPPORTED: return "unsupported";
+        default: return "unknown status";
+    }
+}
+
+const char* dwt_last_error(void) { return g_err; }
+
+long long dwt_launch_count(void) { return g_launches.load(); }
+
+int dwt_profile_enable(int on) {
+    std::lock_guard<std::mutex> lk(g_prof_mu);
+    g_prof_on = on != 0;
+    return DWT_OK;
+}
+
+int dwt_profile_reset(void) {
+    std::lock_guard<std::mutex> lk(g_prof_mu);
+    for (auto& r : g_prof_done) {
+        g_ev_pool.push_back(r.a);
+        g_ev_pool.push_back(r.b);
+    }
+    g_prof_done.clear();
+    return DWT_OK;
+}
+
+int dwt_profile_query(const char* name, long long* launches, double* total_ms) {
+    std::lock_guard<std::mutex> lk(g_prof_mu);
+    long long n = 0;
+    double tot = 0.0;
+    for (auto& r : g_prof_done) {
+        if (strcmp(r.fam, name) != 0) continue;
+        DWT_CK(cudaEventSynchronize(r.b));
+        float ms = 0.f;
+        DWT_CK(cudaEventElapsedTime(&ms, r.a, r.b));
+        tot += ms;
+        ++n;
+    }
+    if (launches) *launches = n;
+    if (total_ms) *total_ms = tot;
+    return DWT_OK;
+}
+
+int dwt_plan_create(int p, int m, int s, const uint8_t* C, unsigned flags, void* stream, dwt_plan_t* out) {
+    if (!out) {
+        set_error("plan output pointer is NULL");
+        return DWT_EINVAL;
+    }
+    *out = nullptr;
+    if (!is_prime_small(p)) {
+        set_error("p = %d: supported primes are 2, 3, 5, 7", p);
+        return DWT_EINVAL;
+    }
+    if (m < 1 || s < 1 || s > 255 || !C) {
+        set_error("bad sizes m = %d, s = %d (or C is NULL)", m, s);
+        return DWT_EINVAL;
+    }
+    if (ipow_ll(p, m) > (1ll << 31)) {
+        set_error("p^m = %d^%d exceeds 2^31", p, m);
+        return DWT_EINVAL;
+    }
+    if (flags & ~(DWT_PLAN_TRANSFORM_ONLY | DWT_PLAN_KEEP_INDEX_MAP)) {
+        set_error("unknown plan flags 0x%x", flags);
+        return DWT_EINVAL;
+    }
+    for (size_t t = 0; t < (size_t)s * m * m; ++t)
+        if (C[t] >= p) {
+            set_error("entry %zu of C is %d >= p", t, (int)C[t]);
+            return DWT_EINVAL;
+        }
+    cudaStream_t st = (cudaStream_t)stream;
+    dwt_plan_s* P = new dwt_plan_s();
+    P->p = p;
+    P->m = m;
+    P->s = s;
+    P->N = ipow_ll(p, m);
+    P->flags = flags;
+    P->C.assign(C, C + (size_t)s * m * m);
+    make_pass_plan(p, m, 4, P->passes[0]);
+    make_pass_plan(p, m, 8, P->passes[1]);
+    make_pass_plan(p, m, 16, P->passes[2]);
+    // row coset labels and column point contributions
+    std::vector<uint32_t> R((size_t)s * m), col((size_t)s * m);
+    for (int j = 0; j < s; ++j)
+        for (int i = 0; i < m; ++i) {
+            uint64_t r = 0, pw = 1;
+            for (int c = 0; c < m; ++c, pw *= (uint64_t)p) r += (uint64_t)C[((size_t)j * m + i) * m + c] * pw;
+            R[(size_t)j * m + i] = (uint32_t)r;
+        }
+    for (int j = 0; j < s; ++j)
+        for (int c = 0; c < m; ++c) {
+            uint64_t v = 0;
+            for (int i = 0; i < m; ++i) v = v * (uint64_t)p + C[((size_t)j * m + i) * m + c];
+            col[(size_t)j * m + c] = (uint32_t)v;
+        }
+    int rc = DWT_OK;
+    auto fail = [&](int code) {
+        dwt_plan_destroy(P);
+        return code;
+    };
+    if (cudaMalloc(&P->d_R, R.size() * 4) != cudaSuccess || cudaMalloc(&P->d_col, col.size() * 4) != cudaSuccess ||
+        cudaMalloc(&P->d_C, P->C.size()) != cudaSuccess) {
+        cudaGetLastError();
+        set_error("plan allocation failed");
+        return fail(DWT_ENOMEM);
+    }
+    if (cudaMemcpyAsync(P->d_R, R.data(), R.size() * 4, cudaMemcpyHostToDevice, st) != cudaSuccess ||
+        cudaMemcpyAsync(P->d_col, col.data(), col.size() * 4, cudaMemcpyHostToDevice, st) != cudaSuccess ||
+        cudaMemcpyAsync(P->d_C, P->C.data(), P->C.size(), cudaMemcpyHostToDevice, st) != cudaSuccess) {
+        set_error("plan upload failed: %s", cudaGetErrorString(cudaGetLastError()));
+        return fail(DWT_ECUDA);
+    }
+    if (!(flags & DWT_PLAN_TRANSFORM_ONLY)) {
+        rc = build_coset_tables(P, st);
+        if (rc == DWT_ESPAN || rc == DWT_EUNSUPPORTED) {
+            P->tables_status = rc;
+        } else if (rc != DWT_OK) {
+            return fail(rc);
+        } else {
+            P->tables_status = DWT_OK;
+        }
+    }
+    cudaError_t e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) {
+        cuda_fail(e, "plan build", __FILE__, __LINE__);
+        return fail(DWT_ECUDA);
+    }
+    *out = P;
+    return rc;
+}
+
+int dwt_plan_destroy(dwt_plan_t P) {
+    if (!P) return DWT_OK;
+    cudaDeviceSynchronize();
+    cudaFree(P->d_R);
+    cudaFree(P->d_col);
+    cudaFree(P->d_C);
+    cudaFree(P->d_W);
+    cudaFree(P->d_cls);
+    cudaFree(P->d_T);
+    cudaFree(P->d_D);
+    cudaFree(P->d_ws);
+    delete P;
+    return DWT_OK;
+}
+
+int dwt_plan_info(dwt_plan_t P, int* p, int* m, int* s, long long* N, int* tables_status) {
+    if (!P) {
+        set_error("NULL plan");
+        return DWT_EINVAL;
+    }
+    if (p) *p = P->p;
+    if (m) *m = P->m;
+    if (s) *s = P->s;
+    if (N) *N = P->N;
+    if (tables_status) *tables_status = P->tables_status;
+    return DWT_OK;
+}
+
+int dwt_plan_tables(dwt_plan_t P, const float** W, const uint8_t** cls) {
+    if (!P) {
+        set_error("NULL plan");
+        return DWT_EINVAL;
+    }
+    if (P->tables_status != DWT_OK) {
+        set_error("plan has no coset tables (status %d)", P->tables_status);
+        return P->tables_status < 0 ? DWT_EUNSUPPORTED : P->tables_status;
+    }
+    if (W) *W = P->d_W;
+    if (cls) *cls = P->d_cls;
+    return DWT_OK;
+}
+
+int dwt_points(dwt_plan_t P, uint32_t* Y, long long ldY, void* stream) {
+    if (!P || !Y || ldY < P->N) {
+        set_error("dwt_points: bad arguments");
+        return DWT_EINVAL;
+    }
+    return run_points(P, Y, ldY, (cudaStream_t)stream);
+}
+
+int dwt_wavenumber_to_index(dwt_plan_t P, const uint32_t* k, uint32_t* H, long long cnt, void* stream) {
+    if (!P || cnt < 0 || (cnt > 0 && (!k || !H))) {
+        set_error("dwt_wavenumber_to_index: bad arguments");
+        return DWT_EINVAL;
+    }
+    if (cnt == 0) return DWT_OK;
+    return run_k_to_h(P, k, H, cnt, (cudaStream_t)stream);
+}
+
+int dwt_index_to_wavenumber(dwt_plan_t P, const uint32_t* H, uint32_t* k, long long cnt, void* stream) {
+    if (!P || cnt < 0 || (cnt > 0 && (!k || !H))) {
+        set_error("dwt_index_to_wavenumber: bad arguments");
+        return DWT_EINVAL;
+    }
+    if (!(P->flags & DWT_PLAN_KEEP_INDEX_MAP) || P->tables_status != DWT_OK) {
+        set_error("plan was not built with DWT_PLAN_KEEP_INDEX_MAP or has no coset tables");
+        return P->tables_status > 0 ? P->tables_status : DWT_EUNSUPPORTED;
+    }
+    if (cnt == 0) return DWT_OK;
+    return run_h_to_k(P, H, k, cnt, (cudaStream_t)stream);
+}
+
+static int check_transform_types(dwt_plan_s* P, dwt_dtype in_t, dwt_dtype out_t, int sgn) {
+    if (P->p == 2) {
+        if (in_t != out_t || !(in_t == DWT_F32 || in_t == DWT_F64 || in_t == DWT_I32)) {
+            set_error("p = 2 transforms take F32->F32, F64->F64 or I32->I32");
+            return DWT_EUNSUPPORTED;
+        }
+        return DWT_OK;
+    }
+    bool ok32 = out_t == DWT_C64 && (in_t == DWT_C64 || (sgn < 0 && in_t == DWT_F32));
+    bool ok64 = out_t == DWT_C128 && (in_t == DWT_C128 || (sgn < 0 && in_t == DWT_F64));
+    if (!ok32 && !ok64) {
+        set_error("p > 2 transforms produce complex output (C64 / C128); real input only for the forward");
+        return DWT_EUNSUPPORTED;
+    }
+    return DWT_OK;
+}
+
+static int transform_common(dwt_plan_t P, const void* in, void* out, int batch, long long ld_in, long long ld_out,
+                            dwt_dtype in_t, dwt_dtype out_t, dwt_algo algo, void* stream, int sgn) {
+    if (!P || batch < 0 || (batch > 0 && (!in || !out)) || ld_in < P->N || ld_out < P->N) {
+        set_error("transform: bad arguments (batch %d, ld_in %lld, ld_out %lld, N %lld)", batch, ld_in, ld_out, P ? P->N : 0);
+        return DWT_EINVAL;
+    }
+    int rc = check_transform_types(P, in_t, out_t, sgn);
+    if (rc) return rc;
+    if (batch == 0) return DWT_OK;
+    if (algo == DWT_ALGO_TC_SPLIT_BF16) {
+        if (P->p != 2 || in_t != DWT_F32) {
+            set_error("the split-BF16 tensor-core form needs p = 2 and F32 data");
+            return DWT_EUNSUPPORTED;
+        }
+        return run_tc_transform(P, (const float*)in, (float*)out, batch, ld_in, ld_out, sgn, (cudaStream_t)stream);
+    }
+    if (algo != DWT_ALGO_AUTO && algo != DWT_ALGO_BUTTERFLY) {
+        set_error("unknown algo %d", (int)algo);
+        return DWT_EINVAL;
+    }
+    return run_transform(P, in, out, batch, ld_in, ld_out, in_t, out_t, sgn, (cudaStream_t)stream);
+}
+
+int dwt_forward(dwt_plan_t P, const void* in, void* out, int batch, long long ld_in, long long ld_out, dwt_dtype in_t,
+                dwt_dtype out_t, dwt_algo algo, void* stream) {
+    return transform_common(P, in, out, batch, ld_in, ld_out, in_t, out_t, algo, stream, -1);
+}
+
+int dwt_inverse(dwt_plan_t P, const void* in, void* out, int batch, long long ld_in, long long ld_out, dwt_dtype in_t,
+                dwt_dtype out_t, dwt_algo algo, void* stream) {
+    return transform_common(P, in, out, batch, ld_in, ld_out, in_t, out_t, algo, stream, +1);
+}
+
+int dwt_interpolate(dwt_plan_t P, const void* f, void* c, void* coef, int batch, long long ld, dwt_dtype f_t,
+                    dwt_weight weight, dwt_algo algo, double* var, int* dim, double thr, void* stream) {
+    if (!P || batch < 0 || (batch > 0 && (!f || !c)) || ld < P->N || !(thr > 0.0 && thr <= 1.0)) {
+        set_error("dwt_interpolate: bad arguments");
+        return DWT_EINVAL;
+    }
+    if (weight != DWT_WEIGHT_NONE && weight != DWT_WEIGHT_INV_SQ_WAVENUMBER) {
+        set_error("unknown weight %d", (int)weight);
+        return DWT_EINVAL;
+    }
+    if (P->tables_status != DWT_OK) {
+        set_error("plan has no coset tables (status %d)", P->tables_status);
+        return P->tables_status > 0 ? P->tables_status : DWT_EUNSUPPORTED;
+    }
+    if (P->p == 2 ? f_t != DWT_F32 : (f_t != DWT_F32 && f_t != DWT_C64)) {
+        set_error("dwt_interpolate: p = 2 takes F32; p > 2 takes F32 (real) or C64");
+        return DWT_EUNSUPPORTED;
+    }
+    if (algo != DWT_ALGO_AUTO && algo != DWT_ALGO_BUTTERFLY) {
+        set_error("dwt_interpolate runs the butterfly form");
+        return DWT_EUNSUPPORTED;
+    }
+    if (batch == 0) return DWT_OK;
+    return run_interpolate(P, f, c, coef, batch, ld, f_t, weight, var, dim, thr, (cudaStream_t)stream);
+}
+
+int dwt_effdim(dwt_plan_t P, const void* coef, int batch, long long ld, dwt_dtype t, double* var, int* dim, double thr,
+               void* stream) {
+    if (!P || batch < 0 || (batch > 0 && !coef) || ld < P->N || !(thr > 0.0 && thr <= 1.0)) {
+        set_error("dwt_effdim: bad arguments");
+        return DWT_EINVAL;
+    }
+    if (P->tables_status != DWT_OK) {
+        set_error("plan has no coset tables (status %d)", P->tables_status);
+        return P->tables_status > 0 ? P->tables_status : DWT_EUNSUPPORTED;
+    }
+    if (P->p == 2 ? t != DWT_F32 : t != DWT_C64) {
+        set_error("dwt_effdim: coefficients are F32 (p = 2) or C64 (p > 2)");
+        return DWT_EUNSUPPORTED;
+    }
+    if (batch == 0) return DWT_OK;
+    return run_effdim(P, coef, batch, ld, t, var, dim, thr, (cudaStream_t)stream);
+}
+
+int dwt_eval_product(dwt_plan_t P, const double* coef, void* f, int batch, long long ld, dwt_dtype t, void* stream) {
+    if (!P || batch < 0 || (batch > 0 && (!coef || !f)) || ld < P->N || (t != DWT_F32 && t != DWT_F64)) {
+        set_error("dwt_eval_product: bad arguments");
+        return DWT_EINVAL;
+    }
+    if (batch == 0) return DWT_OK;
+    return run_eval_product(P, coef, f, batch, ld, t, (cudaStream_t)stream);
+}
+
+int dwt_eval_exp(dwt_plan_t P, void* f, int batch, long long ld, dwt_dtype t, void* stream) {
+    if (!P || batch < 0 || (batch > 0 && !f) || ld < P->N || (t != DWT_F32 && t != DWT_F64)) {
+        set_error("dwt_eval_exp: bad arguments");
+        return DWT_EINVAL;
+    }
+    if (batch == 0) return DWT_OK;
+    return run_eval_exp(P, f, batch, ld, t, (cudaStream_t)stream);
+}
+
+}  // extern "C"

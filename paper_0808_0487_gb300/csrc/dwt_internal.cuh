@@ -1,0 +1,113 @@
+// dwt_internal.cuh -- shared internals of libdwt (plan object, error and launch
+// bookkeeping, device helpers).  Not part of the public ABI.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <string>
+#include <vector>
+
+#include "../../include/dwt.h"
+
+namespace dwt {
+
+// ---------------------------------------------------------------------------
+// errors
+void set_error(const char* fmt, ...);
+int cuda_fail(cudaError_t e, const char* what, const char* file, int line);
+
+#define DWT_CK(call)                                                        \
+    do {                                                                    \
+        cudaError_t e_ = (call);                                            \
+        if (e_ != cudaSuccess) return ::dwt::cuda_fail(e_, #call, __FILE__, __LINE__); \
+    } while (0)
+
+#define DWT_CK_LAUNCH(what)                                                 \
+    do {                                                                    \
+        cudaError_t e_ = cudaGetLastError();                                \
+        if (e_ != cudaSuccess) return ::dwt::cuda_fail(e_, what, __FILE__, __LINE__); \
+    } while (0)
+
+// ---------------------------------------------------------------------------
+// launch accounting and optional per-launch event timing
+void launch_begin(const char* family, cudaStream_t st);
+void launch_end(const char* family, cudaStream_t st);
+
+struct LaunchScope {
+    const char* fam;
+    cudaStream_t st;
+    LaunchScope(const char* f, cudaStream_t s) : fam(f), st(s) { launch_begin(fam, st); }
+    ~LaunchScope() { launch_end(fam, st); }
+};
+
+// ---------------------------------------------------------------------------
+// the plan
+struct PassGeom {
+    int d0;          // first digit of the pass
+    int b;           // digits in the pass
+    long long S;     // p^d0: distance between consecutive rows of a tile
+    int R;           // p^b rows per tile
+    int Wc;          // consecutive low indices (columns) per tile, power of 2
+    int wlog;        // log2(Wc)
+    long long nlo;   // ceil(S / Wc)
+    long long ntile; // tiles per function
+};
+
+struct PassPlan {
+    int q = 0;           // number of passes
+    PassGeom g[32];
+};
+
+}  // namespace dwt
+
+struct dwt_plan_s {
+    int p = 0, m = 0, s = 0;
+    long long N = 0;
+    unsigned flags = 0;
+    int tables_status = -1;
+    std::vector<uint8_t> C;       // host copy [s][m][m]
+    // device copies of the generating data
+    uint32_t* d_R = nullptr;      // [s][m]: coset label of row i of C_j, sum_c C[j][i][c] p^c
+    uint32_t* d_col = nullptr;    // [s][m]: point contribution of index digit c = 1, sum_i C[j][i][c] p^{m-1-i}
+    uint8_t* d_C = nullptr;       // [s][m][m]
+    // coset tables
+    float* d_W = nullptr;         // [N]
+    uint8_t* d_cls = nullptr;     // [N][2]
+    uint8_t* d_T = nullptr;       // [(s+1)][N] least-nu tables (kept only with KEEP_INDEX_MAP)
+    uint8_t* d_D = nullptr;       // [s][N] smallest optimal nu(k_j) per coordinate (ditto)
+    // per-call workspace (grown on demand, owned by the plan)
+    void* d_ws = nullptr;
+    size_t ws_bytes = 0;
+    // pass decompositions by element size (4, 8, 16 bytes)
+    dwt::PassPlan passes[3];
+};
+
+namespace dwt {
+
+int ensure_workspace(dwt_plan_s* P, size_t bytes);
+const PassPlan& pass_plan(dwt_plan_s* P, int elem_bytes);
+
+// kernels' host entry points (implemented in the .cu files)
+int run_transform(dwt_plan_s* P, const void* in, void* out, int batch, long long ld_in, long long ld_out,
+                  dwt_dtype in_t, dwt_dtype out_t, int sgn, cudaStream_t st);
+int run_interpolate(dwt_plan_s* P, const void* f, void* c, void* coef, int batch, long long ld, dwt_dtype f_t,
+                    dwt_weight weight, double* var, int* dim, double thr, cudaStream_t st);
+int run_effdim(dwt_plan_s* P, const void* coef, int batch, long long ld, dwt_dtype t, double* var, int* dim,
+               double thr, cudaStream_t st);
+int run_points(dwt_plan_s* P, uint32_t* Y, long long ldY, cudaStream_t st);
+int run_k_to_h(dwt_plan_s* P, const uint32_t* k, uint32_t* H, long long cnt, cudaStream_t st);
+int run_h_to_k(dwt_plan_s* P, const uint32_t* H, uint32_t* k, long long cnt, cudaStream_t st);
+int build_coset_tables(dwt_plan_s* P, cudaStream_t st);
+int run_eval_product(dwt_plan_s* P, const double* coef, void* f, int batch, long long ld, dwt_dtype t,
+                     cudaStream_t st);
+int run_eval_exp(dwt_plan_s* P, void* f, int batch, long long ld, dwt_dtype t, cudaStream_t st);
+int run_tc_transform(dwt_plan_s* P, const float* in, float* out, int batch, long long ld_in, long long ld_out,
+                     int sgn, cudaStream_t st);
+
+static inline long long ipow_ll(int p, int m) {
+    long long v = 1;
+    for (int i = 0; i < m; ++i) v *= p;
+    return v;
+}
+
+}  // namespace dwt

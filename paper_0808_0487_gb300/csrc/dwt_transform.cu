@@ -1,0 +1,640 @@
+// dwt_transform.cu -- radix-p Walsh (Chrestenson) transforms over digital nets,
+// Algorithm 1 (forward, eq. fdwt) and Algorithm 2 (inverse), plus the fused
+// weighting / effective-dimension pass of the interpolation (Sec. 3, Sec. 4).
+//
+// The transform of Sec. 2.2 is the Kronecker power over the m index digits of
+// the p-point DFT F[h][n] = omega^{-hn}: the sum over digit n_r touches nothing
+// but digit r, and the sums over different digits commute.  Digits are
+// therefore processed in passes of b digits each; a pass holds a tile of p^b
+// "rows" (one per value of its digits) times Wc "columns" (consecutive values
+// of the digits below the pass) in shared memory, runs its b stages there, and
+// writes back.  Inside a tile every thread takes p^K elements that differ only
+// in K consecutive digits and runs those K stages in registers; groups of K
+// digits follow one another through shared memory.
+#include <type_traits>
+
+#include "dwt_internal.cuh"
+
+namespace dwt {
+
+// ---------------------------------------------------------------------------
+// element helpers
+struct Tw {
+    float c[8], s[8];     // cos, sin of 2 pi e / p
+    double cd[8], sd[8];
+};
+
+template <typename T> struct IsCplx : std::false_type {};
+template <> struct IsCplx<float2> : std::true_type {};
+template <> struct IsCplx<double2> : std::true_type {};
+
+template <typename T> __device__ __forceinline__ T zero_of();
+template <> __device__ __forceinline__ float zero_of<float>() { return 0.f; }
+template <> __device__ __forceinline__ double zero_of<double>() { return 0.0; }
+template <> __device__ __forceinline__ int zero_of<int>() { return 0; }
+template <> __device__ __forceinline__ float2 zero_of<float2>() { return make_float2(0.f, 0.f); }
+template <> __device__ __forceinline__ double2 zero_of<double2>() { return make_double2(0.0, 0.0); }
+
+template <typename T, typename TI> __device__ __forceinline__ T promote(TI v) { return v; }
+template <> __device__ __forceinline__ float2 promote<float2, float>(float v) { return make_float2(v, 0.f); }
+template <> __device__ __forceinline__ double2 promote<double2, double>(double v) { return make_double2(v, 0.0); }
+
+__device__ __forceinline__ float2 operator+(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ float2 operator-(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+__device__ __forceinline__ double2 operator+(double2 a, double2 b) { return make_double2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ double2 operator-(double2 a, double2 b) { return make_double2(a.x - b.x, a.y - b.y); }
+
+template <typename T> __device__ __forceinline__ T scale_by(T v, double s);
+template <> __device__ __forceinline__ float scale_by<float>(float v, double s) { return v * (float)s; }
+template <> __device__ __forceinline__ double scale_by<double>(double v, double s) { return v * s; }
+template <> __device__ __forceinline__ int scale_by<int>(int v, double) { return v; }
+template <> __device__ __forceinline__ float2 scale_by<float2>(float2 v, double s) {
+    return make_float2(v.x * (float)s, v.y * (float)s);
+}
+template <> __device__ __forceinline__ double2 scale_by<double2>(double2 v, double s) {
+    return make_double2(v.x * s, v.y * s);
+}
+
+// shared-memory index with one pad element per 128 bytes (bank spreading)
+template <typename T> struct PadLog { static constexpr int v = sizeof(T) == 4 ? 5 : sizeof(T) == 8 ? 4 : 3; };
+template <typename T> __device__ __forceinline__ int spad(int i) { return i + (i >> PadLog<T>::v); }
+template <typename T> static inline size_t spad_bytes(int nel) {
+    int last = nel - 1;
+    return (size_t)(last + (last >> PadLog<T>::v) + 1) * sizeof(T);
+}
+
+constexpr int cpow(int p, int k) { return k == 0 ? 1 : p * cpow(p, k - 1); }
+
+// ---------------------------------------------------------------------------
+// one p-point DFT y_t = sum_u omega^{SGN u t} x_u in registers
+template <int P, int SGN, typename T> struct Dft {
+    static __device__ __forceinline__ void run(T* x, const Tw& tw) {
+        static_assert(IsCplx<T>::value, "p > 2 needs complex data");
+        T y[P];
+#pragma unroll
+        for (int t = 0; t < P; ++t) {
+            T acc = x[0];
+#pragma unroll
+            for (int u = 1; u < P; ++u) {
+                const int e = SGN > 0 ? (u * t) % P : (P - (u * t) % P) % P;
+                if (e == 0) {
+                    acc = acc + x[u];
+                } else if (std::is_same<T, float2>::value) {
+                    const float c = tw.c[e], s = tw.s[e];
+                    acc.x += x[u].x * c - x[u].y * s;
+                    acc.y += x[u].x * s + x[u].y * c;
+                } else {
+                    const double c = tw.cd[e], s = tw.sd[e];
+                    acc.x += x[u].x * c - x[u].y * s;
+                    acc.y += x[u].x * s + x[u].y * c;
+                }
+            }
+            y[t] = acc;
+        }
+#pragma unroll
+        for (int t = 0; t < P; ++t) x[t] = y[t];
+    }
+};
+
+// p = 2: omega = -1 both ways
+template <int SGN, typename T> struct Dft<2, SGN, T> {
+    static __device__ __forceinline__ void run(T* x, const Tw&) {
+        T a = x[0], b = x[1];
+        x[0] = a + b;
+        x[1] = a - b;
+    }
+};
+
+// K stages over the K digits of a register array of P^K elements
+template <int P, int NK, int ST, int SGN, typename T> struct RegStages {
+    static __device__ __forceinline__ void run(T* v, const Tw& tw) {
+#pragma unroll
+        for (int blk = 0; blk < NK; blk += ST * P) {
+#pragma unroll
+            for (int off = 0; off < ST; ++off) {
+                T x[P];
+#pragma unroll
+                for (int u = 0; u < P; ++u) x[u] = v[blk + off + u * ST];
+                Dft<P, SGN, T>::run(x, tw);
+#pragma unroll
+                for (int u = 0; u < P; ++u) v[blk + off + u * ST] = x[u];
+            }
+        }
+        RegStages<P, NK, ST * P, SGN, T>::run(v, tw);
+    }
+};
+template <int P, int NK, int SGN, typename T> struct RegStages<P, NK, NK, SGN, T> {
+    static __device__ __forceinline__ void run(T*, const Tw&) {}
+};
+
+// stages on row digits g0 .. g0+K-1 of a tile of R rows x Wc columns in smem
+template <int P, int K, int SGN, typename T>
+__device__ __forceinline__ void group_stage(T* sm, int g0, int R, int wlog, const Tw& tw) {
+    constexpr int NK = cpow(P, K);
+    int Pg0 = 1;
+    for (int i = 0; i < g0; ++i) Pg0 *= P;
+    const int ntask = (R / NK) << wlog;
+    const int cmask = (1 << wlog) - 1;
+    for (int t = threadIdx.x; t < ntask; t += blockDim.x) {
+        const int c = t & cmask;
+        const int q = t >> wlog;
+        const int rl = q % Pg0, rh = q / Pg0;
+        const int r0 = rl + rh * Pg0 * NK;
+        T v[NK];
+#pragma unroll
+        for (int i = 0; i < NK; ++i) v[i] = sm[spad<T>(((r0 + i * Pg0) << wlog) + c)];
+        RegStages<P, NK, 1, SGN, T>::run(v, tw);
+#pragma unroll
+        for (int i = 0; i < NK; ++i) sm[spad<T>(((r0 + i * Pg0) << wlog) + c)] = v[i];
+    }
+}
+
+template <int P, int SGN, typename T, int KMAX>
+__device__ void tile_stages(T* sm, int b, int R, int wlog, const Tw& tw) {
+    int g0 = 0;
+    while (g0 < b) {
+        const int k = min(KMAX, b - g0);
+        switch (k) {
+            case 1: group_stage<P, 1, SGN, T>(sm, g0, R, wlog, tw); break;
+            case 2: if constexpr (KMAX >= 2) group_stage<P, 2, SGN, T>(sm, g0, R, wlog, tw); break;
+            case 3: if constexpr (KMAX >= 3) group_stage<P, 3, SGN, T>(sm, g0, R, wlog, tw); break;
+            case 4: if constexpr (KMAX >= 4) group_stage<P, 4, SGN, T>(sm, g0, R, wlog, tw); break;
+            case 5: if constexpr (KMAX >= 5) group_stage<P, 5, SGN, T>(sm, g0, R, wlog, tw); break;
+            default: break;
+        }
+        __syncthreads();
+        g0 += k;
+    }
+}
+
+template <int P, typename T> struct KMax {
+    static constexpr int v = P == 2 ? (sizeof(T) == 4 ? 5 : 4)
+                                    : (sizeof(T) == 8 ? (P == 3 ? 3 : P == 5 ? 2 : 1) : (P == 3 ? 2 : 1));
+};
+
+// ---------------------------------------------------------------------------
+struct PassArgs {
+    const void* in;
+    void* out;
+    long long ld_in, ld_out;
+    long long S, SR, nlo;
+    int R, b, Wc, wlog;
+    double scale;
+    int do_scale;
+    Tw tw;
+};
+
+// one pass over the digits d0..d0+b-1 of every function: grid (tiles, functions)
+template <int P, typename T, typename TI, int SGN>
+__global__ void __launch_bounds__(256) k_pass(PassArgs a) {
+    extern __shared__ __align__(16) unsigned char smraw[];
+    T* sm = reinterpret_cast<T*>(smraw);
+    const long long fn = blockIdx.y;
+    const long long tile = blockIdx.x;
+    const long long lo0 = (tile % a.nlo) << a.wlog;
+    const long long base = lo0 + (tile / a.nlo) * a.SR;
+    const int ncols = (int)min((long long)a.Wc, a.S - lo0);
+    const int nel = a.R << a.wlog;
+    const int cmask = a.Wc - 1;
+    const TI* in = reinterpret_cast<const TI*>(a.in) + fn * a.ld_in + base;
+    T* out = reinterpret_cast<T*>(a.out) + fn * a.ld_out + base;
+    for (int e = threadIdx.x; e < nel; e += blockDim.x) {
+        const int r = e >> a.wlog, c = e & cmask;
+        T v = zero_of<T>();
+        if (c < ncols) v = promote<T, TI>(in[c + (long long)r * a.S]);
+        sm[spad<T>(e)] = v;
+    }
+    __syncthreads();
+    tile_stages<P, SGN, T, KMax<P, T>::v>(sm, a.b, a.R, a.wlog, a.tw);
+    for (int e = threadIdx.x; e < nel; e += blockDim.x) {
+        const int r = e >> a.wlog, c = e & cmask;
+        if (c < ncols) {
+            T v = sm[spad<T>(e)];
+            if (a.do_scale) v = scale_by<T>(v, a.scale);
+            out[c + (long long)r * a.S] = v;
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// fused top pass of the interpolation: forward stages of the last digits,
+// scale p^-m, weight, per-class variance partials, optional coefficient store,
+// inverse stages of the same digits.
+struct MidArgs {
+    PassArgs pa;
+    const float* W;        // NULL: weight 1
+    const uint8_t* cls;    // [N][2]
+    void* coef;            // optional output of g
+    double* part;          // [fn][ntile][2*nb]
+    long long ntile;
+    int nb;                // s + 1
+};
+
+template <typename T> __device__ __forceinline__ float mag2(T v);
+template <> __device__ __forceinline__ float mag2<float>(float v) { return v * v; }
+template <> __device__ __forceinline__ float mag2<float2>(float2 v) { return v.x * v.x + v.y * v.y; }
+template <typename T> __device__ __forceinline__ T mulw(T v, float w);
+template <> __device__ __forceinline__ float mulw<float>(float v, float w) { return v * w; }
+template <> __device__ __forceinline__ float2 mulw<float2>(float2 v, float w) { return make_float2(v.x * w, v.y * w); }
+
+// per-lane FP32 class sums -> one FP64 value per class and tile, fixed order
+__device__ __forceinline__ void reduce_bins(const float* bins, int nb2, double* out) {
+    const int nw = blockDim.x >> 5, w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (int bi = w; bi < nb2; bi += nw) {
+        float x = 0.f;
+        for (int ww = 0; ww < nw; ++ww) x += bins[(ww * nb2 + bi) * 32 + lane];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+        if (lane == 0) out[bi] = (double)x;
+    }
+}
+
+template <int P, typename T, typename TI>
+__global__ void __launch_bounds__(256) k_mid(MidArgs m) {
+    const PassArgs& a = m.pa;
+    extern __shared__ __align__(16) unsigned char smraw[];
+    T* sm = reinterpret_cast<T*>(smraw);
+    const int nel = a.R << a.wlog;
+    const int tile_elems = nel + ((nel - 1) >> PadLog<T>::v);   // as spad_bytes on the host
+    float* bins = reinterpret_cast<float*>(smraw + ((tile_elems * sizeof(T) + 15) & ~(size_t)15));
+    const int nb2 = 2 * m.nb;
+    const long long fn = blockIdx.y;
+    const long long tile = blockIdx.x;
+    const long long lo0 = (tile % a.nlo) << a.wlog;
+    const long long base = lo0 + (tile / a.nlo) * a.SR;
+    const int ncols = (int)min((long long)a.Wc, a.S - lo0);
+    const int cmask = a.Wc - 1;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const TI* in = reinterpret_cast<const TI*>(a.in) + fn * a.ld_in + base;
+    T* out = reinterpret_cast<T*>(a.out) + fn * a.ld_out + base;
+    for (int e = threadIdx.x; e < nel; e += blockDim.x) {
+        const int r = e >> a.wlog, c = e & cmask;
+        T v = zero_of<T>();
+        if (c < ncols) v = promote<T, TI>(in[c + (long long)r * a.S]);
+        sm[spad<T>(e)] = v;
+    }
+    for (int i = threadIdx.x; i < (int)(blockDim.x >> 5) * nb2 * 32; i += blockDim.x) bins[i] = 0.f;
+    __syncthreads();
+    tile_stages<P, -1, T, KMax<P, T>::v>(sm, a.b, a.R, a.wlog, a.tw);
+    float* mybins = bins + (size_t)w * nb2 * 32 + lane;
+    T* coef = m.coef ? reinterpret_cast<T*>(m.coef) + fn * a.ld_out + base : nullptr;
+    for (int e = threadIdx.x; e < nel; e += blockDim.x) {
+        const int r = e >> a.wlog, c = e & cmask;
+        if (c >= ncols) continue;
+        const long long H = base + c + (long long)r * a.S;
+        T v = scale_by<T>(sm[spad<T>(e)], a.scale);
+        if (m.W) v = mulw<T>(v, __ldg(m.W + H));
+        if (coef) coef[c + (long long)r * a.S] = v;
+        if (H != 0) {
+            const float q = mag2<T>(v);
+            const uchar2 k = __ldg(reinterpret_cast<const uchar2*>(m.cls) + H);
+            mybins[(int)k.x * 32] += q;
+            mybins[(m.nb + (int)k.y) * 32] += q;
+        }
+        sm[spad<T>(e)] = v;
+    }
+    __syncthreads();
+    reduce_bins(bins, nb2, m.part + (fn * m.ntile + tile) * nb2);
+    tile_stages<P, +1, T, KMax<P, T>::v>(sm, a.b, a.R, a.wlog, a.tw);
+    for (int e = threadIdx.x; e < nel; e += blockDim.x) {
+        const int r = e >> a.wlog, c = e & cmask;
+        if (c < ncols) out[c + (long long)r * a.S] = sm[spad<T>(e)];
+    }
+}
+
+// class sums of given coefficients: grid (chunks, functions), 8192 elements per chunk
+template <typename T>
+__global__ void __launch_bounds__(256) k_effdim_bins(const T* coef, long long ld, long long N, const uint8_t* cls,
+                                                     int nb, long long nchunk, double* part) {
+    extern __shared__ __align__(16) unsigned char smraw[];
+    float* bins = reinterpret_cast<float*>(smraw);
+    const int nb2 = 2 * nb, lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    for (int i = threadIdx.x; i < (int)(blockDim.x >> 5) * nb2 * 32; i += blockDim.x) bins[i] = 0.f;
+    __syncthreads();
+    const long long fn = blockIdx.y, chunk = blockIdx.x;
+    const long long h0 = chunk * 8192, h1 = min(N, h0 + 8192);
+    float* mybins = bins + (size_t)w * nb2 * 32 + lane;
+    const T* g = coef + fn * ld;
+    for (long long H = h0 + threadIdx.x; H < h1; H += blockDim.x) {
+        if (H == 0) continue;
+        const float q = mag2<T>(g[H]);
+        const uchar2 k = __ldg(reinterpret_cast<const uchar2*>(cls) + H);
+        mybins[(int)k.x * 32] += q;
+        mybins[(nb + (int)k.y) * 32] += q;
+    }
+    __syncthreads();
+    reduce_bins(bins, nb2, part + (fn * nchunk + chunk) * nb2);
+}
+
+// partials -> cumulative truncation / superposition variances and dimensions
+__global__ void k_effdim_finalize(const double* part, long long nchunk, int nb, double thr, double* var, int* dim) {
+    extern __shared__ double cls_sum[];   // [2*nb]
+    const int nb2 = 2 * nb;
+    const long long fn = blockIdx.x;
+    const double* pp = part + fn * nchunk * nb2;
+    for (int bi = threadIdx.x; bi < nb2; bi += blockDim.x) {
+        double acc = 0.0;
+        for (long long t = 0; t < nchunk; ++t) acc += pp[t * nb2 + bi];
+        cls_sum[bi] = acc;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double ct = 0.0, cs = 0.0;
+        double tot = 0.0;
+        for (int d = 0; d < nb; ++d) tot += cls_sum[d];
+        int dt = 0, ds = 0;
+        bool ft = false, fs = false;
+        for (int d = 0; d < nb; ++d) {
+            ct += cls_sum[d];
+            cs += cls_sum[nb + d];
+            if (var) {
+                var[(fn * 2 + 0) * nb + d] = ct;
+                var[(fn * 2 + 1) * nb + d] = cs;
+            }
+            if (tot > 0.0) {
+                if (!ft && ct >= thr * tot) { dt = d; ft = true; }
+                if (!fs && cs >= thr * tot) { ds = d; fs = true; }
+            }
+        }
+        if (dim) {
+            dim[fn * 2 + 0] = dt;
+            dim[fn * 2 + 1] = ds;
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// host side
+static Tw make_tw(int p) {
+    Tw t;
+    for (int e = 0; e < 8; ++e) {
+        double ang = e < p ? 2.0 * 3.14159265358979323846 * e / p : 0.0;
+        t.cd[e] = cos(ang);
+        t.sd[e] = sin(ang);
+        if (e == 0) { t.cd[e] = 1.0; t.sd[e] = 0.0; }
+        t.c[e] = (float)t.cd[e];
+        t.s[e] = (float)t.sd[e];
+    }
+    return t;
+}
+
+template <typename F>
+static int set_smem(F* kern, size_t bytes) {
+    if (bytes > 48 * 1024) {
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute", __FILE__, __LINE__);
+    }
+    return DWT_OK;
+}
+
+static PassArgs pass_args(const PassGeom& g, const void* in, void* out, long long ld_in, long long ld_out,
+                          const Tw& tw) {
+    PassArgs a;
+    a.in = in;
+    a.out = out;
+    a.ld_in = ld_in;
+    a.ld_out = ld_out;
+    a.S = g.S;
+    a.SR = g.S * g.R;
+    a.nlo = g.nlo;
+    a.R = g.R;
+    a.b = g.b;
+    a.Wc = g.Wc;
+    a.wlog = g.wlog;
+    a.scale = 1.0;
+    a.do_scale = 0;
+    a.tw = tw;
+    return a;
+}
+
+static const char* pass_family(int t, int q) { return t == 0 ? "pass_lo" : (t == q - 1 ? "pass_hi" : "pass_mid"); }
+
+template <int P, typename T, typename TI, int SGN>
+static int launch_pass(const PassGeom& g, const PassArgs& a, int nf, const char* fam, cudaStream_t st) {
+    const size_t smem = spad_bytes<T>(g.R << g.wlog);
+    auto kern = k_pass<P, T, TI, SGN>;
+    int rc = set_smem(kern, smem);
+    if (rc) return rc;
+    dim3 grid((unsigned)g.ntile, (unsigned)nf);
+    {
+        LaunchScope ls(fam, st);
+        kern<<<grid, 256, smem, st>>>(a);
+    }
+    DWT_CK_LAUNCH("k_pass");
+    return DWT_OK;
+}
+
+// L2-sized groups of functions: the passes of one group run back to back so
+// that the intermediate stays in the 126 MB L2 between passes.
+static const long long kL2Group = 48ll << 20;
+
+template <int P, typename T, typename TI, int SGN>
+static int transform_t(dwt_plan_s* Pl, const void* in, void* out, int batch, long long ld_in, long long ld_out,
+                       cudaStream_t st) {
+    const PassPlan& pp = pass_plan(Pl, sizeof(T));
+    const Tw tw = make_tw(P);
+    const long long fbytes = Pl->N * (long long)sizeof(T);
+    int G = (int)std::max(1ll, kL2Group / fbytes);
+    G = std::min(G, 65535);
+    const bool scale = SGN < 0 && !std::is_same<T, int>::value;
+    for (int f0 = 0; f0 < batch; f0 += G) {
+        const int nf = std::min(G, batch - f0);
+        for (int t = 0; t < pp.q; ++t) {
+            const PassGeom& g = pp.g[t];
+            int rc;
+            if (t == 0) {
+                PassArgs a = pass_args(g, (const TI*)in + (long long)f0 * ld_in, (T*)out + (long long)f0 * ld_out,
+                                       ld_in, ld_out, tw);
+                if (scale && pp.q == 1) { a.do_scale = 1; a.scale = 1.0 / (double)Pl->N; }
+                rc = launch_pass<P, T, TI, SGN>(g, a, nf, pass_family(t, pp.q), st);
+            } else {
+                PassArgs a = pass_args(g, (const T*)out + (long long)f0 * ld_out, (T*)out + (long long)f0 * ld_out,
+                                       ld_out, ld_out, tw);
+                if (scale && t == pp.q - 1) { a.do_scale = 1; a.scale = 1.0 / (double)Pl->N; }
+                rc = launch_pass<P, T, T, SGN>(g, a, nf, pass_family(t, pp.q), st);
+            }
+            if (rc) return rc;
+        }
+    }
+    return DWT_OK;
+}
+
+template <int P>
+static int transform_p(dwt_plan_s* Pl, const void* in, void* out, int batch, long long ld_in, long long ld_out,
+                       dwt_dtype in_t, dwt_dtype out_t, int sgn, cudaStream_t st) {
+    if constexpr (P == 2) {
+        if (in_t == DWT_F32)
+            return sgn < 0 ? transform_t<2, float, float, -1>(Pl, in, out, batch, ld_in, ld_out, st)
+                           : transform_t<2, float, float, +1>(Pl, in, out, batch, ld_in, ld_out, st);
+        if (in_t == DWT_F64)
+            return sgn < 0 ? transform_t<2, double, double, -1>(Pl, in, out, batch, ld_in, ld_out, st)
+                           : transform_t<2, double, double, +1>(Pl, in, out, batch, ld_in, ld_out, st);
+        return sgn < 0 ? transform_t<2, int, int, -1>(Pl, in, out, batch, ld_in, ld_out, st)
+                       : transform_t<2, int, int, +1>(Pl, in, out, batch, ld_in, ld_out, st);
+    } else {
+        if (out_t == DWT_C64) {
+            if (sgn < 0)
+                return in_t == DWT_F32 ? transform_t<P, float2, float, -1>(Pl, in, out, batch, ld_in, ld_out, st)
+                                       : transform_t<P, float2, float2, -1>(Pl, in, out, batch, ld_in, ld_out, st);
+            return transform_t<P, float2, float2, +1>(Pl, in, out, batch, ld_in, ld_out, st);
+        }
+        if (sgn < 0)
+            return in_t == DWT_F64 ? transform_t<P, double2, double, -1>(Pl, in, out, batch, ld_in, ld_out, st)
+                                   : transform_t<P, double2, double2, -1>(Pl, in, out, batch, ld_in, ld_out, st);
+        return transform_t<P, double2, double2, +1>(Pl, in, out, batch, ld_in, ld_out, st);
+    }
+}
+
+int run_transform(dwt_plan_s* Pl, const void* in, void* out, int batch, long long ld_in, long long ld_out,
+                  dwt_dtype in_t, dwt_dtype out_t, int sgn, cudaStream_t st) {
+    switch (Pl->p) {
+        case 2: return transform_p<2>(Pl, in, out, batch, ld_in, ld_out, in_t, out_t, sgn, st);
+        case 3: return transform_p<3>(Pl, in, out, batch, ld_in, ld_out, in_t, out_t, sgn, st);
+        case 5: return transform_p<5>(Pl, in, out, batch, ld_in, ld_out, in_t, out_t, sgn, st);
+        case 7: return transform_p<7>(Pl, in, out, batch, ld_in, ld_out, in_t, out_t, sgn, st);
+        default: set_error("unsupported p"); return DWT_EUNSUPPORTED;
+    }
+}
+
+// ---------------------------------------------------------------------------
+static int bins_warps(size_t tile_bytes, int nb2) {
+    const size_t avail = 227 * 1024 - ((tile_bytes + 15) & ~(size_t)15);
+    const size_t per_warp = (size_t)nb2 * 32 * 4;
+    int nw = (int)std::min<size_t>(8, avail / per_warp);
+    return nw;
+}
+
+static int finalize(dwt_plan_s* Pl, const double* part, long long nchunk, int batch, double thr, double* var, int* dim,
+                    cudaStream_t st) {
+    if (!var && !dim) return DWT_OK;
+    const int nb = Pl->s + 1;
+    {
+        LaunchScope ls("effdim_finalize", st);
+        k_effdim_finalize<<<batch, 128, 2 * nb * sizeof(double), st>>>(part, nchunk, nb, thr, var, dim);
+    }
+    DWT_CK_LAUNCH("k_effdim_finalize");
+    return DWT_OK;
+}
+
+template <int P, typename T, typename TI>
+static int interpolate_t(dwt_plan_s* Pl, const void* f, void* c, void* coef, int batch, long long ld,
+                         dwt_weight weight, double* var, int* dim, double thr, cudaStream_t st) {
+    const PassPlan& pp = pass_plan(Pl, sizeof(T));
+    const Tw tw = make_tw(P);
+    const int nb = Pl->s + 1, nb2 = 2 * nb;
+    const PassGeom& gm = pp.g[pp.q - 1];
+    const long long ntile = gm.ntile;
+    const size_t tile_bytes = spad_bytes<T>(gm.R << gm.wlog);
+    const int nw = bins_warps(tile_bytes, nb2);
+    if (nw < 1) {
+        set_error("s = %d too large for the fused variance pass", Pl->s);
+        return DWT_EUNSUPPORTED;
+    }
+    const size_t smem = ((tile_bytes + 15) & ~(size_t)15) + (size_t)nw * nb2 * 32 * 4;
+    int rc = ensure_workspace(Pl, (size_t)batch * ntile * nb2 * sizeof(double));
+    if (rc) return rc;
+    double* part = (double*)Pl->d_ws;
+    auto kmid_first = k_mid<P, T, TI>;   // single pass: reads f directly
+    auto kmid_next = k_mid<P, T, T>;     // after lower passes: in place on c
+    rc = set_smem(kmid_first, smem);
+    if (rc) return rc;
+    rc = set_smem(kmid_next, smem);
+    if (rc) return rc;
+    const long long fbytes = Pl->N * (long long)sizeof(T);
+    int G = (int)std::max(1ll, kL2Group / fbytes);
+    G = std::min(G, 65535);
+    for (int f0 = 0; f0 < batch; f0 += G) {
+        const int nf = std::min(G, batch - f0);
+        const long long off = (long long)f0 * ld;
+        // forward passes below the top one: f -> c
+        for (int t = 0; t + 1 < pp.q; ++t) {
+            const PassGeom& g = pp.g[t];
+            if (t == 0) {
+                PassArgs a = pass_args(g, (const TI*)f + off, (T*)c + off, ld, ld, tw);
+                rc = launch_pass<P, T, TI, -1>(g, a, nf, "interp_fwd", st);
+            } else {
+                PassArgs a = pass_args(g, (const T*)c + off, (T*)c + off, ld, ld, tw);
+                rc = launch_pass<P, T, T, -1>(g, a, nf, "interp_fwd", st);
+            }
+            if (rc) return rc;
+        }
+        // fused top pass
+        MidArgs m;
+        if (pp.q == 1) m.pa = pass_args(gm, (const TI*)f + off, (T*)c + off, ld, ld, tw);
+        else m.pa = pass_args(gm, (const T*)c + off, (T*)c + off, ld, ld, tw);
+        m.pa.scale = 1.0 / (double)Pl->N;
+        m.W = weight == DWT_WEIGHT_INV_SQ_WAVENUMBER ? Pl->d_W : nullptr;
+        m.cls = Pl->d_cls;
+        m.coef = coef ? (void*)((T*)coef + off) : nullptr;
+        m.part = part + (long long)f0 * ntile * nb2;
+        m.ntile = ntile;
+        m.nb = nb;
+        {
+            LaunchScope ls("interp_top", st);
+            dim3 grid((unsigned)ntile, (unsigned)nf);
+            if (pp.q == 1) kmid_first<<<grid, nw * 32, smem, st>>>(m);
+            else kmid_next<<<grid, nw * 32, smem, st>>>(m);
+        }
+        DWT_CK_LAUNCH("k_mid");
+        // inverse passes below the top one, in place on c
+        for (int t = pp.q - 2; t >= 0; --t) {
+            const PassGeom& g = pp.g[t];
+            PassArgs a = pass_args(g, (const T*)c + off, (T*)c + off, ld, ld, tw);
+            rc = launch_pass<P, T, T, +1>(g, a, nf, "interp_inv", st);
+            if (rc) return rc;
+        }
+    }
+    return finalize(Pl, part, ntile, batch, thr, var, dim, st);
+}
+
+int run_interpolate(dwt_plan_s* Pl, const void* f, void* c, void* coef, int batch, long long ld, dwt_dtype f_t,
+                    dwt_weight weight, double* var, int* dim, double thr, cudaStream_t st) {
+    switch (Pl->p) {
+        case 2: return interpolate_t<2, float, float>(Pl, f, c, coef, batch, ld, weight, var, dim, thr, st);
+        case 3:
+            return f_t == DWT_F32 ? interpolate_t<3, float2, float>(Pl, f, c, coef, batch, ld, weight, var, dim, thr, st)
+                                  : interpolate_t<3, float2, float2>(Pl, f, c, coef, batch, ld, weight, var, dim, thr, st);
+        case 5:
+            return f_t == DWT_F32 ? interpolate_t<5, float2, float>(Pl, f, c, coef, batch, ld, weight, var, dim, thr, st)
+                                  : interpolate_t<5, float2, float2>(Pl, f, c, coef, batch, ld, weight, var, dim, thr, st);
+        case 7:
+            return f_t == DWT_F32 ? interpolate_t<7, float2, float>(Pl, f, c, coef, batch, ld, weight, var, dim, thr, st)
+                                  : interpolate_t<7, float2, float2>(Pl, f, c, coef, batch, ld, weight, var, dim, thr, st);
+        default: set_error("unsupported p"); return DWT_EUNSUPPORTED;
+    }
+}
+
+template <typename T>
+static int effdim_t(dwt_plan_s* Pl, const void* coef, int batch, long long ld, double* var, int* dim, double thr,
+                    cudaStream_t st) {
+    const int nb = Pl->s + 1, nb2 = 2 * nb;
+    const long long nchunk = (Pl->N + 8191) / 8192;
+    const int nw = bins_warps(0, nb2);
+    if (nw < 1) {
+        set_error("s = %d too large for the variance pass", Pl->s);
+        return DWT_EUNSUPPORTED;
+    }
+    const size_t smem = (size_t)nw * nb2 * 32 * 4;
+    int rc = ensure_workspace(Pl, (size_t)batch * nchunk * nb2 * sizeof(double));
+    if (rc) return rc;
+    double* part = (double*)Pl->d_ws;
+    auto kern = k_effdim_bins<T>;
+    rc = set_smem(kern, smem);
+    if (rc) return rc;
+    for (int f0 = 0; f0 < batch; f0 += 65535) {
+        const int nf = std::min(65535, batch - f0);
+        LaunchScope ls("effdim_bins", st);
+        kern<<<dim3((unsigned)nchunk, (unsigned)nf), nw * 32, smem, st>>>(
+            (const T*)coef + (long long)f0 * ld, ld, Pl->N, Pl->d_cls, nb, nchunk, part + (long long)f0 * nchunk * nb2);
+    }
+    DWT_CK_LAUNCH("k_effdim_bins");
+    return finalize(Pl, part, nchunk, batch, thr, var, dim, st);
+}
+
+int run_effdim(dwt_plan_s* Pl, const void* coef, int batch, long long ld, dwt_dtype t, double* var, int* dim,
+               double thr, cudaStream_t st) {
+    if (t == DWT_F32) return effdim_t<float>(Pl, coef, batch, ld, var, dim, thr, st);
+    return effdim_t<float2>(Pl, coef, batch, ld, var, dim, thr, st);
+}
+
+}  // namespace dwt

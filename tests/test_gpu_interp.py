@@ -1,0 +1,146 @@
+"""GPU parity of the weighting / inverse / effective-dimension path (dwt_interpolate,
+dwt_effdim) and of the synthetic test functions."""
+import numpy as np
+import pytest
+import torch
+
+import synthetic as S
+from conftest import rel_l2
+
+pytestmark = pytest.mark.gpu
+
+
+def _np(t):
+    return t.detach().cpu().numpy()
+
+
+def _cplx(a):
+    return a[..., 0::2] + 1j * a[..., 1::2]
+
+
+def _check_dims(got, dt, ds, vt, vs, thr=0.99):
+    """Dimensions must agree unless the oracle's cumulative ratio is within 1e-6 of the threshold."""
+    tot = vt[-1]
+    for d_got, d_ref, v in ((got[0], dt, vt), (got[1], ds, vs)):
+        if d_got != d_ref:
+            lo, hi = sorted((d_got, d_ref))
+            assert all(abs(v[d] / tot - thr) < 1e-6 for d in range(lo, hi)), (d_got, d_ref)
+
+
+@pytest.mark.parametrize("weight", [1, 0])
+def test_interpolate_pr1(dwt, dev, orc, weight):
+    w = S.workload_pr1()
+    p, m, s, C = w["p"], w["m"], w["s"], w["C"]
+    N = p ** m
+    plan = dwt.dwt_plan_create(p, m, s, C)
+    f = orc.eval_product(p, m, orc.net_points(p, m, C), w["coef"][0])
+    tab = orc.coset_leaders_dp(p, m, C)
+    Wt = tab["W64"] if weight else np.ones(N)
+    cref, g, vt, vs, dt, ds = orc.interpolate(p, m, f, Wt, tab["cls"], s)
+    fin = torch.tensor(f.astype(np.float32), device=dev)
+    c = torch.empty(N, device=dev)
+    coef = torch.empty(N, device=dev)
+    var = torch.empty((1, 2, s + 1), dtype=torch.float64, device=dev)
+    dim = torch.empty((1, 2), dtype=torch.int32, device=dev)
+    dwt.dwt_interpolate(plan, fin, c, coef, 1, N, dwt.DWT_F32, weight, var=var, dim=dim)
+    assert rel_l2(_np(c), cref.real) < 1e-5
+    assert rel_l2(_np(coef), g.real) < 1e-5
+    if not weight:
+        assert rel_l2(_np(c), f) < 1e-5         # interpolation property: c = f
+    v = _np(var)[0]
+    assert np.allclose(v[0], vt, rtol=1e-5, atol=1e-14 * vt[-1])
+    assert np.allclose(v[1], vs, rtol=1e-5, atol=1e-14 * vt[-1])
+    _check_dims(_np(dim)[0], dt, ds, vt, vs)
+
+
+def test_interpolate_m20_batch(dwt, dev, orc):
+    w = S.workload_p2_m20()
+    p, m, s, C = w["p"], w["m"], w["s"], w["C"]
+    N = p ** m
+    B = 4
+    plan = dwt.dwt_plan_create(p, m, s, C)
+    Y = orc.net_points(p, m, C)
+    fs = np.stack([orc.eval_product(p, m, Y, w["coef"][b]) for b in range(B)])
+    tab = orc.coset_leaders_dp(p, m, C)
+    fin = torch.tensor(fs.astype(np.float32), device=dev)
+    c = torch.empty((B, N), device=dev)
+    var = torch.empty((B, 2, s + 1), dtype=torch.float64, device=dev)
+    dim = torch.empty((B, 2), dtype=torch.int32, device=dev)
+    dwt.dwt_interpolate(plan, fin, c, None, B, N, dwt.DWT_F32, dwt.DWT_WEIGHT_INV_SQ_WAVENUMBER, var=var, dim=dim)
+    cg, vg, dg = _np(c), _np(var), _np(dim)
+    for b in range(B):
+        cref, g, vt, vs, dt, ds = orc.interpolate(p, m, fs[b], tab["W64"], tab["cls"], s)
+        assert rel_l2(cg[b], cref.real) < 1e-5
+        assert np.allclose(vg[b, 0], vt, rtol=1e-5, atol=1e-14 * vt[-1])
+        assert np.allclose(vg[b, 1], vs, rtol=1e-5, atol=1e-14 * vt[-1])
+        _check_dims(dg[b], dt, ds, vt, vs)
+
+
+def test_interpolate_p3_m13(dwt, dev, orc):
+    w = S.workload_p3_m13()
+    p, m, s, C = w["p"], w["m"], w["s"], w["C"]
+    N = p ** m
+    plan = dwt.dwt_plan_create(p, m, s, C)
+    f = orc.eval_exp(p, m, orc.net_points(p, m, C))
+    tab = orc.coset_leaders_dp(p, m, C)
+    cref, g, vt, vs, dt, ds = orc.interpolate(p, m, f, tab["W64"], tab["cls"], s)
+    fin = torch.tensor(f.astype(np.float32), device=dev)
+    c = torch.empty(2 * N, device=dev)
+    coef = torch.empty(2 * N, device=dev)
+    var = torch.empty((1, 2, s + 1), dtype=torch.float64, device=dev)
+    dim = torch.empty((1, 2), dtype=torch.int32, device=dev)
+    dwt.dwt_interpolate(plan, fin, c, coef, 1, N, dwt.DWT_F32, dwt.DWT_WEIGHT_INV_SQ_WAVENUMBER, var=var, dim=dim)
+    assert rel_l2(_cplx(_np(c)), cref) < 1e-5
+    assert rel_l2(_cplx(_np(coef)), g) < 1e-5
+    v = _np(var)[0]
+    assert np.allclose(v[0], vt, rtol=1e-5, atol=1e-14 * vt[-1])
+    assert np.allclose(v[1], vs, rtol=1e-5, atol=1e-14 * vt[-1])
+    _check_dims(_np(dim)[0], dt, ds, vt, vs)
+
+
+@pytest.mark.parametrize("p,m,s", [(2, 12, 4), (5, 5, 3), (7, 4, 6)])
+def test_effdim_standalone(dwt, dev, orc, p, m, s):
+    C = S.workload_pr1()["C"] if p == 2 else S.small_net(p, m, s, index=5)
+    N = p ** m
+    plan = dwt.dwt_plan_create(p, m, s, C)
+    tab = orc.coset_leaders_dp(p, m, C)
+    B = 3
+    g = (S.uniform(S.stream_seed(23, S.P_VALUES, p), 2 * B * N) - 0.5).reshape(B, 2 * N)
+    if p == 2:
+        gin = torch.tensor(g[:, :N].astype(np.float32), device=dev)
+        gref = gin.double().cpu().numpy()
+        t = dwt.DWT_F32
+    else:
+        gin = torch.tensor(g.astype(np.float32), device=dev)
+        gref = _cplx(gin.double().cpu().numpy())
+        t = dwt.DWT_C64
+    var = torch.empty((B, 2, s + 1), dtype=torch.float64, device=dev)
+    dim = torch.empty((B, 2), dtype=torch.int32, device=dev)
+    dwt.dwt_effdim(plan, gin, B, N if p == 2 else N, t, var=var, dim=dim, threshold=0.9)
+    for b in range(B):
+        vt, vs, dt, ds = orc.effdim(gref[b], tab["cls"], s, 0.9)
+        assert np.allclose(_np(var)[b, 0], vt, rtol=1e-5)
+        assert np.allclose(_np(var)[b, 1], vs, rtol=1e-5)
+        _check_dims(_np(dim)[b], dt, ds, vt, vs, 0.9)
+
+
+@pytest.mark.parametrize("p,m,s", [(2, 12, 4), (3, 7, 5), (2, 20, 16)])
+def test_eval_functions(dwt, dev, orc, p, m, s):
+    C = S.workload_p2_m20()["C"] if m == 20 else (S.workload_pr1()["C"] if p == 2 else S.small_net(p, m, s, index=6))
+    N = p ** m
+    plan = dwt.dwt_plan_create(p, m, s, C, dwt.DWT_PLAN_TRANSFORM_ONLY)
+    Y = orc.net_points(p, m, C)
+    B = 3
+    coef = S.uniform(S.stream_seed(24, S.P_COEFFS, p), B * s).reshape(B, s)
+    f = torch.empty((B, N), device=dev)
+    dwt.dwt_eval_product(plan, torch.tensor(coef, device=dev), f, B, N, dwt.DWT_F32)
+    f64 = torch.empty((B, N), dtype=torch.float64, device=dev)
+    dwt.dwt_eval_product(plan, torch.tensor(coef, device=dev), f64, B, N, dwt.DWT_F64)
+    for b in range(B):
+        ref = orc.eval_product(p, m, Y, coef[b])
+        assert np.abs(_np(f)[b] - ref).max() < 1e-5 * np.abs(ref).max()
+        assert np.abs(_np(f64)[b] - ref).max() < 1e-13 * np.abs(ref).max()
+    e = torch.empty((1, N), device=dev)
+    dwt.dwt_eval_exp(plan, e, 1, N, dwt.DWT_F32)
+    ref = orc.eval_exp(p, m, Y)
+    assert np.abs(_np(e)[0] - ref).max() < 1e-5 * np.abs(ref).max()
