@@ -285,6 +285,8 @@ int dwt_plan_create(int p, int m, int s, const uint8_t* C, unsigned flags, void*
             return fail(rc);
         } else {
             P->tables_status = DWT_OK;
+            rc = p2_build_tiled_tables(P, st);
+            if (rc) return fail(rc);
         }
     }
     cudaError_t e = cudaStreamSynchronize(st);
@@ -304,6 +306,8 @@ int dwt_plan_destroy(dwt_plan_t P) {
     cudaFree(P->d_C);
     cudaFree(P->d_W);
     cudaFree(P->d_cls);
+    cudaFree(P->d_Wt);
+    cudaFree(P->d_clst);
     cudaFree(P->d_T);
     cudaFree(P->d_D);
     cudaFree(P->d_ws);

@@ -73,6 +73,8 @@ struct dwt_plan_s {
     // coset tables
     float* d_W = nullptr;         // [N]
     uint8_t* d_cls = nullptr;     // [N][2]
+    float* d_Wt = nullptr;        // W in the tile-major order of the fused p = 2 pass
+    uint8_t* d_clst = nullptr;    // cls in the same order
     uint8_t* d_T = nullptr;       // [(s+1)][N] least-nu tables (kept only with KEEP_INDEX_MAP)
     uint8_t* d_D = nullptr;       // [s][N] smallest optimal nu(k_j) per coordinate (ditto)
     // per-call workspace (grown on demand, owned by the plan)
@@ -98,6 +100,7 @@ int run_points(dwt_plan_s* P, uint32_t* Y, long long ldY, cudaStream_t st);
 int run_k_to_h(dwt_plan_s* P, const uint32_t* k, uint32_t* H, long long cnt, cudaStream_t st);
 int run_h_to_k(dwt_plan_s* P, const uint32_t* H, uint32_t* k, long long cnt, cudaStream_t st);
 int build_coset_tables(dwt_plan_s* P, cudaStream_t st);
+int p2_build_tiled_tables(dwt_plan_s* P, cudaStream_t st);
 int run_eval_product(dwt_plan_s* P, const double* coef, void* f, int batch, long long ld, dwt_dtype t,
                      cudaStream_t st);
 int run_eval_exp(dwt_plan_s* P, void* f, int batch, long long ld, dwt_dtype t, cudaStream_t st);

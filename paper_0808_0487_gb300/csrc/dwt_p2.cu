@@ -1,0 +1,688 @@
+// dwt_p2.cu -- register-tile kernels for p = 2 (FP32 and int32), the hot path
+// of Algorithms 1 and 2 on large nets.
+//
+// For p = 2 the transform is the Walsh-Hadamard transform: every stage is the
+// butterfly (a, b) -> (a + b, a - b) over one index bit, and the stages over
+// different bits commute (Sec. 2.2).  A pass covers a tile of 2^LT elements;
+// every thread keeps 64 of them in registers (32 packed pairs), so 6 index
+// bits are "in thread" at a time and their stages run without data movement,
+// two butterflies per packed f32x2 instruction.  Between register layouts the
+// tile goes once through shared memory.  A padded layout (a few words inserted
+// every 2^8, or 2^(p1+6), elements) keeps every exchange free of bank
+// conflicts, and every register's shared-memory address is a per-thread base
+// plus a compile-time offset.
+//
+//  k2_lo<L>: a contiguous tile of 2^L elements (L = 12..14), the low L digits.
+//    layout A (load / first stages): float4 at 4(t + NT q): in-thread bits
+//      {0,1} and {L-4..L-1}; layout B: bits {2..7}; layout C: bits {0,1,8..11}.
+//  k2_hi<LT, B>: B digits d0..d0+B-1 above the low pass; the tile holds
+//    2^B rows (distance S = 2^d0 apart) of Wc = 2^(LT-B) consecutive columns.
+//    layout A: float4 at 4(t + NT q): bits {0,1} (columns) and {LT-4..LT-1};
+//    layout P: bits [p1, p1+6) with p1 = min(LT-B, LT-6).
+//    The fused variant runs the forward stages, the scale p^-m, the weight,
+//    the per-class variance partials and the inverse stages of the same
+//    digits in one tile: the top pass of dwt_interpolate.
+#include <string.h>
+
+#include <algorithm>
+#include <type_traits>
+
+#include "dwt_internal.cuh"
+
+namespace dwt {
+
+// ---------------------------------------------------------------------------
+// packed pairs: float2 uses the f32x2 pipe, int2 two scalar ops
+template <typename T> struct P2;
+template <> struct P2<float> { using t = float2; using v4 = float4; };
+template <> struct P2<int> { using t = int2; using v4 = int4; };
+
+__device__ __forceinline__ float2 padd(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 psub(float2 a, float2 b) {
+    unsigned long long ua, ub, ud;
+    memcpy(&ua, &a, 8);
+    memcpy(&ub, &b, 8);
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(ud) : "l"(ua), "l"(ub));
+    float2 d;
+    memcpy(&d, &ud, 8);
+    return d;
+}
+__device__ __forceinline__ int2 padd(int2 a, int2 b) { return make_int2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ int2 psub(int2 a, int2 b) { return make_int2(a.x - b.x, a.y - b.y); }
+__device__ __forceinline__ float2 pmul(float2 a, float s) { return __fmul2_rn(a, make_float2(s, s)); }
+__device__ __forceinline__ int2 pmul(int2 a, float) { return a; }
+
+// register j of the 64 lives in v[j >> 1], component j & 1
+template <typename V> __device__ __forceinline__ auto& comp(V& v, int c) { return c ? v.y : v.x; }
+
+// butterflies over register-index bit RB
+template <int RB, typename V>
+__device__ __forceinline__ void bfly(V* v) {
+    if constexpr (RB == 0) {
+#pragma unroll
+        for (int k = 0; k < 32; ++k) {
+            const auto a = v[k].x, b = v[k].y;
+            v[k].x = a + b;
+            v[k].y = a - b;
+        }
+    } else {
+        constexpr int D = 1 << (RB - 1);
+#pragma unroll
+        for (int k = 0; k < 32; ++k) {
+            if (k & D) continue;
+            const V a = v[k], b = v[k | D];
+            v[k] = padd(a, b);
+            v[k | D] = psub(a, b);
+        }
+    }
+}
+template <int LO, int HI, typename V>
+__device__ __forceinline__ void bfly_range(V* v) {
+    if constexpr (LO < HI) {
+        bfly<LO, V>(v);
+        bfly_range<LO + 1, HI, V>(v);
+    }
+}
+
+// 16-byte moves between memory and two register pairs
+template <typename T, typename V>
+__device__ __forceinline__ void ld16(const T* p, V* v2) {
+    const typename P2<T>::v4 x = *reinterpret_cast<const typename P2<T>::v4*>(p);
+    v2[0].x = x.x; v2[0].y = x.y; v2[1].x = x.z; v2[1].y = x.w;
+}
+template <typename T, typename V>
+__device__ __forceinline__ void ld16_cs(const T* p, V* v2) {   // read once: evict first
+    const typename P2<T>::v4 x = __ldcs(reinterpret_cast<const typename P2<T>::v4*>(p));
+    v2[0].x = x.x; v2[0].y = x.y; v2[1].x = x.z; v2[1].y = x.w;
+}
+template <typename T, typename V>
+__device__ __forceinline__ void st16(T* p, const V* v2) {
+    typename P2<T>::v4 x;
+    x.x = v2[0].x; x.y = v2[0].y; x.z = v2[1].x; x.w = v2[1].y;
+    *reinterpret_cast<typename P2<T>::v4*>(p) = x;
+}
+
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(sa), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
+
+// ---------------------------------------------------------------------------
+// low pass: tile of 2^L contiguous elements.  Every shared-memory access moves
+// 16 bytes: index bits 0,1 always stay in a thread's float4.
+//   layout A: float4 at 4(t + NT q): in-thread bits {0,1} + {L-4..L-1}
+//   layout B: 64 consecutive elements 64 t + (0..63): bits {0..5}
+//   layout C: float4 at 4(t & 15) + 64 g + 1024 (t >> 4): bits {0,1} + {6..9}
+// Stages: A all six, B bits 2..5, C the bits of 6..9 below L-4.
+// Shared layout pad(e) = e + 4 (e >> 6): conflict-free for A, B and C.
+__device__ __forceinline__ int pad_lo(int e) { return e + ((e >> 6) << 2); }
+
+template <typename T, int L>
+__device__ __forceinline__ void lo_tile_compute(T* sm, typename P2<T>::t* v, int t) {
+    using V = typename P2<T>::t;
+    constexpr int NT = 1 << (L - 6);
+    // layout A -> shared (padded)
+    {
+        T* pa = sm + pad_lo(4 * t);
+#pragma unroll
+        for (int q = 0; q < 16; ++q) st16(pa + q * (4 * NT + NT / 4), v + 2 * q);
+    }
+    __syncthreads();
+    // layout B: thread t holds elements 64 t .. 64 t + 63
+    {
+        T* pb = sm + pad_lo(64 * t);
+#pragma unroll
+        for (int g = 0; g < 16; ++g) ld16(pb + 4 * g, v + 2 * g);
+        bfly_range<2, 6>(v);
+#pragma unroll
+        for (int g = 0; g < 16; ++g) st16(pb + 4 * g, v + 2 * g);
+    }
+    __syncthreads();
+    // layout C
+    {
+        const T* pc = sm + pad_lo(4 * (t & 15) + 1024 * (t >> 4));
+#pragma unroll
+        for (int g = 0; g < 16; ++g) ld16(pc + 68 * g, v + 2 * g);
+        bfly_range<2, 2 + (L - 10 < 4 ? L - 10 : 4)>(v);   // e bits 6 .. min(9, L-5)
+    }
+    (void)sizeof(V);
+}
+
+template <typename T, int L>
+__device__ __forceinline__ void lo_tile_store(T* dst, const typename P2<T>::t* v, int t) {
+    T* pd = dst + 4 * (t & 15) + 1024 * (t >> 4);
+#pragma unroll
+    for (int g = 0; g < 16; ++g) st16(pd + 64 * g, v + 2 * g);
+}
+
+template <typename T, int L>
+__global__ void __launch_bounds__(1 << (L - 6), (L == 14 ? 3 : 4)) k2_lo(const T* in, T* out, long long ld_in,
+                                                                         long long ld_out, float scale, int do_scale) {
+    static_assert(L >= 12 && L <= 14, "low-pass tile 2^12 .. 2^14");
+    using V = typename P2<T>::t;
+    constexpr int NT = 1 << (L - 6);
+    extern __shared__ __align__(16) unsigned char smraw[];
+    T* sm = reinterpret_cast<T*>(smraw);
+    const int t = threadIdx.x;
+    const T* src = in + blockIdx.y * ld_in + ((long long)blockIdx.x << L);
+    T* dst = out + blockIdx.y * ld_out + ((long long)blockIdx.x << L);
+    V v[32];
+#pragma unroll
+    for (int q = 0; q < 16; ++q) ld16_cs(src + 4 * (t + NT * q), v + 2 * q);
+    bfly_range<0, 6>(v);
+    lo_tile_compute<T, L>(sm, v, t);
+    if (do_scale) {
+#pragma unroll
+        for (int k = 0; k < 32; ++k) v[k] = pmul(v[k], scale);
+    }
+    lo_tile_store<T, L>(dst, v, t);
+}
+
+// Persistent low pass over 2^14 tiles with a two-deep cp.async pipeline: the
+// next tile streams into the idle buffer while the current one is transformed.
+// Tile k (of this CTA) uses buffer k & 1: raw linear data first, then the
+// padded exchange layout.
+template <typename T>
+__global__ void __launch_bounds__(256, 1) k2_lo_pipe(const T* in, T* out, long long ld_in, long long ld_out,
+                                                     long long tiles_per_fn, long long ntiles, float scale,
+                                                     int do_scale) {
+    constexpr int L = 14, NT = 256;
+    constexpr int BUF = (1 << L) + (1 << (L - 4));   // padded elements per buffer
+    using V = typename P2<T>::t;
+    extern __shared__ __align__(16) unsigned char smraw[];
+    T* buf0 = reinterpret_cast<T*>(smraw);
+    const int t = threadIdx.x;
+    auto src_of = [&](long long i) {
+        return in + (i / tiles_per_fn) * ld_in + ((i % tiles_per_fn) << L);
+    };
+    auto issue = [&](long long i, T* b) {
+        if (i < ntiles) {
+            const T* s = src_of(i);
+#pragma unroll
+            for (int q = 0; q < 16; ++q) cp_async16(b + 4 * (t + NT * q), s + 4 * (t + NT * q));
+        }
+        cp_async_commit();
+    };
+    long long i = blockIdx.x;
+    issue(i, buf0);
+    for (int k = 0; i < ntiles; ++k, i += gridDim.x) {
+        T* cur = buf0 + (k & 1) * BUF;
+        T* nxt = buf0 + ((k + 1) & 1) * BUF;
+        issue(i + gridDim.x, nxt);
+        asm volatile("cp.async.wait_group 1;" ::: "memory");
+        __syncthreads();
+        V v[32];
+#pragma unroll
+        for (int q = 0; q < 16; ++q) ld16(cur + 4 * (t + NT * q), v + 2 * q);
+        bfly_range<0, 6>(v);
+        __syncthreads();   // raw tile read by everyone before the padded layout overwrites it
+        lo_tile_compute<T, L>(cur, v, t);
+        if (do_scale) {
+#pragma unroll
+            for (int kk = 0; kk < 32; ++kk) v[kk] = pmul(v[kk], scale);
+        }
+        T* dst = out + (i / tiles_per_fn) * ld_out + ((i % tiles_per_fn) << L);
+        lo_tile_store<T, L>(dst, v, t);
+        __syncthreads();   // buffer free before the copy two tiles ahead lands in it
+    }
+    cp_async_wait_all();
+}
+
+// ---------------------------------------------------------------------------
+// high pass: 2^B rows (stride S) x Wc = 2^(LT-B) columns
+struct HiArgs {
+    const void* in;
+    void* out;
+    long long ld_in, ld_out;
+    long long S;         // row distance 2^d0
+    long long nlo;       // S / Wc column chunks
+    float scale;
+    int do_scale;
+    // fused top pass
+    const float* W;      // tile-major weights, NULL = 1
+    const uint8_t* cls;  // tile-major classes
+    void* coef;          // optional output of the weighted coefficients
+    double* part;        // [fn][class][tile]
+    long long ntile;
+    int nb;
+    int wofs;            // byte offset of the weight stage in shared memory
+};
+
+template <int LT, int B> struct HiGeom {
+    static constexpr int NT = 1 << (LT - 6);
+    static constexpr int CB = LT - B;                                  // column bits
+    static constexpr int P1 = (LT - B) < (LT - 6) ? (LT - B) : (LT - 6);
+    static constexpr int PADSH = P1 + 6;                               // pad(e) = e + PADC (e >> PADSH)
+    static constexpr int PADC = P1 < 5 ? (1 << P1) : 0;
+    static constexpr int QSH = PADSH - (LT - 4);                       // layout A: e >> PADSH = q >> QSH
+    static constexpr int SMEM_ELEMS = (1 << LT) + PADC * ((1 << LT) >> PADSH);
+    // register bits of layout P that are row bits not transformed in layout A
+    static constexpr int RLO = (LT - B) - P1;
+    static constexpr int RHI = (LT - 4) - P1 < 6 ? (LT - 4) - P1 : 6;
+    static __device__ __forceinline__ long long goff(int e, long long S) {
+        return (long long)(e & ((1 << CB) - 1)) + S * (long long)(e >> CB);
+    }
+    // element held in register j by thread t when the fused pass weights the
+    // coefficients: layout P (B > 4) or layout A (B = 4)
+    static __host__ __device__ __forceinline__ int fused_e(int t, int j) {
+        if constexpr (B > 4) return (t & ((1 << P1) - 1)) | ((t >> P1) << (P1 + 6)) | (j << P1);
+        else return 4 * (t + NT * (j >> 2)) + (j & 3);
+    }
+};
+
+template <typename T, int LT, int B, bool FUSED, bool HAS_COEF>
+__global__ void __launch_bounds__(1 << (LT - 6)) k2_hi(HiArgs a) {
+    static_assert(B >= 4 && B <= 10 && LT - B >= 2, "high-pass shape");
+    using G = HiGeom<LT, B>;
+    using V = typename P2<T>::t;
+    constexpr int NT = G::NT, P1 = G::P1;
+    extern __shared__ __align__(16) unsigned char smraw[];
+    T* sm = reinterpret_cast<T*>(smraw);
+    const int t = threadIdx.x;
+    const long long fn = blockIdx.y, tile = blockIdx.x;
+    const long long base = ((tile % a.nlo) << G::CB) + (tile / a.nlo) * (a.S << B);
+    const T* src = reinterpret_cast<const T*>(a.in) + fn * a.ld_in + base;
+    T* dst = reinterpret_cast<T*>(a.out) + fn * a.ld_out + base;
+    V v[32];
+    uint2 cl[FUSED ? 16 : 1];
+    // layout A loads
+#pragma unroll
+    for (int q = 0; q < 16; ++q) ld16(src + G::goff(4 * (t + NT * q), a.S), v + 2 * q);
+    if constexpr (FUSED) {
+        // prefetch this tile's classes (registers) and weights (shared memory, async);
+        // tile-major order: group g of thread t at (g NT + t)
+        const uint2* cg = reinterpret_cast<const uint2*>(a.cls) + ((long long)tile << (LT - 2));
+#pragma unroll
+        for (int g = 0; g < 16; ++g) cl[g] = __ldcs(cg + g * NT + t);
+        if (a.W) {
+            const float* wg = a.W + ((long long)tile << LT);
+            unsigned char* sw = smraw + a.wofs;
+#pragma unroll
+            for (int i = 0; i < 16; ++i) cp_async16(sw + 16 * (t + NT * i), wg + 4 * (t + NT * i));
+        }
+        cp_async_commit();
+    }
+    bfly_range<2, 6>(v);   // e bits LT-4..LT-1 = row bits B-4..B-1
+    // layout A in shared memory: pad(4(t + NT q)) = 4t + q 4NT + PADC (q >> QSH)
+    T* pa = sm + 4 * t;
+    if constexpr (B > 4) {
+#pragma unroll
+        for (int q = 0; q < 16; ++q) st16(pa + q * 4 * NT + G::PADC * (q >> G::QSH), v + 2 * q);
+        __syncthreads();
+    }
+    // layout P: element ep | (j << P1) at pad(ep) + (j << P1)
+    const int ep = (t & ((1 << P1) - 1)) | ((t >> P1) << (P1 + 6));
+    T* pp = sm + ep + G::PADC * (ep >> G::PADSH);
+    if constexpr (B > 4) {
+#pragma unroll
+        for (int j = 0; j < 64; ++j) comp(v[j >> 1], j & 1) = pp[j << P1];
+        bfly_range<G::RLO, G::RHI>(v);
+    }
+    if constexpr (!FUSED) {
+        if (a.do_scale) {
+#pragma unroll
+            for (int k = 0; k < 32; ++k) v[k] = pmul(v[k], a.scale);
+        }
+        if constexpr (B > 4) {
+#pragma unroll
+            for (int j = 0; j < 64; ++j) dst[G::goff(ep | (j << P1), a.S)] = comp(v[j >> 1], j & 1);
+        } else {
+#pragma unroll
+            for (int q = 0; q < 16; ++q) st16(dst + G::goff(4 * (t + NT * q), a.S), v + 2 * q);
+        }
+    } else {
+        // The class bins alias the exchange buffer: wait until every thread has
+        // read layout P, then zero them.
+        float* bins = reinterpret_cast<float*>(smraw);
+        const int nb2 = 2 * a.nb;
+        const int lane = t & 31, w = t >> 5;
+        if constexpr (B > 4) __syncthreads();
+        for (int i = t; i < (NT >> 5) * nb2 * 32; i += NT) bins[i] = 0.f;
+        cp_async_wait_all();
+        __syncthreads();
+        float* mybins = bins + w * nb2 * 32 + lane;
+        const float4* sw4 = reinterpret_cast<const float4*>(smraw + a.wofs);
+        float* coef = HAS_COEF ? reinterpret_cast<float*>(a.coef) + fn * a.ld_out + base : nullptr;
+        const bool has0 = base == 0 && t == 0;   // coset label H = 0 is register 0 of thread 0
+#pragma unroll
+        for (int g = 0; g < 16; ++g) {
+            float wv[4] = {a.scale, a.scale, a.scale, a.scale};
+            if (a.W) {
+                const float4 x4 = sw4[g * NT + t];
+                wv[0] *= x4.x; wv[1] *= x4.y; wv[2] *= x4.z; wv[3] *= x4.w;
+            }
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int j = 4 * g + u;
+                float& x = comp(v[j >> 1], j & 1);
+                x *= wv[u];
+                if constexpr (HAS_COEF) coef[G::goff(G::fused_e(t, j), a.S)] = x;
+                const unsigned word = u < 2 ? cl[g].x : cl[g].y;
+                const int kt = (word >> (16 * (u & 1))) & 0xff;
+                const int ks = (word >> (16 * (u & 1) + 8)) & 0xff;
+                const float qv = (j == 0 && has0) ? 0.f : x * x;
+                mybins[kt * 32] += qv;
+                mybins[(a.nb + ks) * 32] += qv;
+            }
+        }
+        __syncthreads();
+        // per-tile class sums, fixed order: lane l of warp w sums whole classes
+        // b = l, l+32, ... of its warp's [class][lane] block, reading the 32 lane
+        // columns in the rotated order (k + l) & 31 (conflict-free) into a pairwise
+        // tree; the NW warp sums are then added in warp order and stored in FP64
+        // class-major: part[fn][class][tile].
+        {
+            constexpr int NW = NT >> 5;
+            float* red = bins + NW * nb2 * 32;   // [NW][nb2]
+            const float* wb = bins + w * nb2 * 32;
+            for (int b = lane; b < nb2; b += 32) {
+                float r[32];
+#pragma unroll
+                for (int k = 0; k < 32; ++k) r[k] = wb[b * 32 + ((k + lane) & 31)];
+#pragma unroll
+                for (int h = 16; h > 0; h >>= 1)
+#pragma unroll
+                    for (int k = 0; k < h; ++k) r[k] += r[k + h];
+                red[w * nb2 + b] = r[0];
+            }
+            __syncthreads();
+            for (int b = t; b < nb2; b += NT) {
+                float x = red[b];
+#pragma unroll
+                for (int ww = 1; ww < NW; ++ww) x += red[ww * nb2 + b];
+                a.part[(fn * nb2 + b) * a.ntile + tile] = (double)x;
+            }
+        }
+        // inverse stages of the same digits: layout P, then back to layout A
+        if constexpr (B > 4) {
+            bfly_range<G::RLO, G::RHI>(v);
+            __syncthreads();   // bins read out before the exchange reuses the buffer
+#pragma unroll
+            for (int j = 0; j < 64; ++j) pp[j << P1] = comp(v[j >> 1], j & 1);
+            __syncthreads();
+#pragma unroll
+            for (int q = 0; q < 16; ++q) ld16(pa + q * 4 * NT + G::PADC * (q >> G::QSH), v + 2 * q);
+        }
+        bfly_range<2, 6>(v);
+#pragma unroll
+        for (int q = 0; q < 16; ++q) st16(dst + G::goff(4 * (t + NT * q), a.S), v + 2 * q);
+    }
+}
+
+// tile-major copies of the weight and class tables for the fused pass: register
+// group g (4 elements) of thread t of a tile at (tile 2^LT) + 4 (g NT + t)
+template <int LT, int B>
+__global__ void __launch_bounds__(1 << (LT - 6)) k2_tile_tables(const float* __restrict__ W,
+                                                                const uint8_t* __restrict__ cls, float* Wt,
+                                                                uint8_t* clst, long long S, long long nlo) {
+    using G = HiGeom<LT, B>;
+    constexpr int NT = G::NT;
+    const int t = threadIdx.x;
+    const long long tile = blockIdx.x;
+    const long long base = ((tile % nlo) << G::CB) + (tile / nlo) * (S << B);
+    for (int j = 0; j < 64; ++j) {
+        const long long H = base + G::goff(G::fused_e(t, j), S);
+        const long long o = (tile << LT) + 4 * ((j >> 2) * NT + t) + (j & 3);
+        Wt[o] = W[H];
+        clst[2 * o] = cls[2 * H];
+        clst[2 * o + 1] = cls[2 * H + 1];
+    }
+}
+
+// ---------------------------------------------------------------------------
+// host side
+template <typename F>
+static int attr_smem(F* k, size_t bytes) {
+    if (bytes > 48 * 1024) {
+        cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute", __FILE__, __LINE__);
+    }
+    return DWT_OK;
+}
+
+// digit split of the fast path: one low pass of L = m digits for 12 <= m <= 14;
+// otherwise a low pass of L = min(14, m - 4) digits and a high pass of B = m - L
+// digits, 4 <= B <= 10 (16 <= m <= 24)
+static int p2_low_digits(int m) { return m <= 14 ? m : std::min(14, m - 4); }
+bool p2_fast_ok(int m) { return (m >= 12 && m <= 14) || (m >= 16 && m <= 24); }
+
+template <typename T>
+static int launch_lo(int L, const T* in, T* out, long long ld_in, long long ld_out, int nf, long long N, float scale,
+                     int do_scale, const char* fam, cudaStream_t st) {
+    const unsigned tiles = (unsigned)(N >> L);
+    const size_t smem = (((size_t)1 << L) + ((size_t)1 << (L - 4))) * sizeof(T);
+    dim3 grid(tiles, (unsigned)nf);
+    int rc;
+#define DWT_LO(LL)                                                                         \
+    case LL: {                                                                             \
+        auto k = k2_lo<T, LL>;                                                             \
+        if ((rc = attr_smem(k, smem))) return rc;                                          \
+        LaunchScope ls(fam, st);                                                           \
+        k<<<grid, 1 << (LL - 6), smem, st>>>(in, out, ld_in, ld_out, scale, do_scale);     \
+        break;                                                                             \
+    }
+    switch (L) {
+        DWT_LO(12)
+        DWT_LO(13)
+        DWT_LO(14)
+        default: set_error("low-pass tile"); return DWT_EUNSUPPORTED;
+    }
+#undef DWT_LO
+    DWT_CK_LAUNCH("k2_lo");
+    return DWT_OK;
+}
+
+static int num_sms() {
+    static int n = 0;
+    if (!n) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+        if (n <= 0) n = 148;
+    }
+    return n;
+}
+
+// low pass of L digits over nf functions.  The persistent pipelined variant
+// (one CTA per SM) measured no faster than three independent CTAs per SM, so
+// it is kept switched off.
+static constexpr bool kUseLowPipe = false;
+template <typename T>
+static int launch_low(int L, const T* in, T* out, long long ld_in, long long ld_out, int nf, long long N, float scale,
+                      int do_scale, const char* fam, cudaStream_t st) {
+    if (L != 14 || !kUseLowPipe) return launch_lo<T>(L, in, out, ld_in, ld_out, nf, N, scale, do_scale, fam, st);
+    const long long per = N >> 14, ntiles = per * nf;
+    const size_t smem = 2 * (((size_t)1 << 14) + ((size_t)1 << 10)) * sizeof(T);
+    auto k = k2_lo_pipe<T>;
+    int rc = attr_smem(k, smem);
+    if (rc) return rc;
+    const unsigned grid = (unsigned)std::min<long long>(ntiles, num_sms());
+    {
+        LaunchScope ls(fam, st);
+        k<<<grid, 256, smem, st>>>(in, out, ld_in, ld_out, per, ntiles, scale, do_scale);
+    }
+    DWT_CK_LAUNCH("k2_lo_pipe");
+    return DWT_OK;
+}
+
+template <typename T, int LT, int B, bool FUSED, bool HAS_COEF>
+static int launch_hi_one(HiArgs a, int nf, size_t bins_bytes, const char* fam, cudaStream_t st) {
+    using G = HiGeom<LT, B>;
+    const size_t xbytes = (size_t)G::SMEM_ELEMS * sizeof(T);
+    size_t smem = xbytes;
+    if (FUSED) {
+        const size_t u = (std::max(xbytes, bins_bytes) + 15) & ~(size_t)15;
+        a.wofs = (int)u;
+        smem = u + ((size_t)1 << LT) * sizeof(float);
+    }
+    auto k = k2_hi<T, LT, B, FUSED, HAS_COEF>;
+    int rc = attr_smem(k, smem);
+    if (rc) return rc;
+    dim3 grid((unsigned)a.ntile, (unsigned)nf);
+    {
+        LaunchScope ls(fam, st);
+        k<<<grid, G::NT, smem, st>>>(a);
+    }
+    DWT_CK_LAUNCH("k2_hi");
+    return DWT_OK;
+}
+
+template <typename T, int LT, bool FUSED, bool HAS_COEF>
+static int launch_hi_t(int B, const HiArgs& a, int nf, size_t bins_bytes, const char* fam, cudaStream_t st) {
+    switch (B) {
+        case 4: return launch_hi_one<T, LT, 4, FUSED, HAS_COEF>(a, nf, bins_bytes, fam, st);
+        case 5: return launch_hi_one<T, LT, 5, FUSED, HAS_COEF>(a, nf, bins_bytes, fam, st);
+        case 6: return launch_hi_one<T, LT, 6, FUSED, HAS_COEF>(a, nf, bins_bytes, fam, st);
+        case 7: return launch_hi_one<T, LT, 7, FUSED, HAS_COEF>(a, nf, bins_bytes, fam, st);
+        case 8: return launch_hi_one<T, LT, 8, FUSED, HAS_COEF>(a, nf, bins_bytes, fam, st);
+        case 9: return launch_hi_one<T, LT, 9, FUSED, HAS_COEF>(a, nf, bins_bytes, fam, st);
+        case 10: return launch_hi_one<T, LT, 10, FUSED, HAS_COEF>(a, nf, bins_bytes, fam, st);
+        default: set_error("high-pass digits"); return DWT_EUNSUPPORTED;
+    }
+}
+
+static const long long kL2GroupP2 = 48ll << 20;
+
+// forward (sgn < 0, scaled by 2^-m for FP32) or inverse transform, FP32 or int32
+template <typename T>
+static int p2_transform_t(dwt_plan_s* Pl, const T* in, T* out, int batch, long long ld_in, long long ld_out, int sgn,
+                          cudaStream_t st) {
+    const int m = Pl->m;
+    const long long N = Pl->N;
+    const bool scale = sgn < 0 && std::is_same<T, float>::value;
+    const float sc = (float)(1.0 / (double)N);
+    const long long fbytes = N * (long long)sizeof(T);
+    int G = (int)std::max(1ll, kL2GroupP2 / fbytes);
+    G = std::min(G, 65535);
+    for (int f0 = 0; f0 < batch; f0 += G) {
+        const int nf = std::min(G, batch - f0);
+        const T* src = in + (long long)f0 * ld_in;
+        T* dst = out + (long long)f0 * ld_out;
+        if (m <= 14) {
+            int rc = launch_lo<T>(m, src, dst, ld_in, ld_out, nf, N, sc, scale, sgn < 0 ? "p2_lo_fwd" : "p2_lo_inv", st);
+            if (rc) return rc;
+            continue;
+        }
+        const int L = p2_low_digits(m);
+        int rc = launch_low<T>(L, src, dst, ld_in, ld_out, nf, N, 1.f, 0, sgn < 0 ? "p2_lo_fwd" : "p2_lo_inv", st);
+        if (rc) return rc;
+        HiArgs a{};
+        a.in = dst;
+        a.out = dst;
+        a.ld_in = ld_out;
+        a.ld_out = ld_out;
+        a.S = 1ll << L;
+        const int B = m - L;
+        a.nlo = a.S >> (14 - B);
+        a.ntile = N >> 14;
+        a.scale = sc;
+        a.do_scale = scale;
+        rc = launch_hi_t<T, 14, false, false>(B, a, nf, 0, sgn < 0 ? "p2_hi_fwd" : "p2_hi_inv", st);
+        if (rc) return rc;
+    }
+    return DWT_OK;
+}
+
+int p2_transform(dwt_plan_s* Pl, const void* in, void* out, int batch, long long ld_in, long long ld_out,
+                 dwt_dtype t, int sgn, cudaStream_t st) {
+    if (t == DWT_F32)
+        return p2_transform_t<float>(Pl, (const float*)in, (float*)out, batch, ld_in, ld_out, sgn, st);
+    return p2_transform_t<int>(Pl, (const int*)in, (int*)out, batch, ld_in, ld_out, sgn, st);
+}
+
+// tile-major tables for the fused pass (plan time)
+static constexpr int kFusedLT = 13;
+
+int p2_build_tiled_tables(dwt_plan_s* Pl, cudaStream_t st) {
+    const int m = Pl->m;
+    if (Pl->p != 2 || m < 16 || m > 24) return DWT_OK;
+    constexpr int LT = kFusedLT;
+    const int L = p2_low_digits(m);
+    const int B = m - L;
+    const long long N = Pl->N, S = 1ll << L, nlo = S >> (LT - B);
+    if (cudaMalloc(&Pl->d_Wt, (size_t)N * 4) != cudaSuccess || cudaMalloc(&Pl->d_clst, (size_t)N * 2) != cudaSuccess) {
+        cudaGetLastError();
+        set_error("tiled table allocation failed");
+        return DWT_ENOMEM;
+    }
+    const unsigned grid = (unsigned)(N >> LT);
+#define DWT_TT(BB)                                                                                          \
+    case BB: {                                                                                              \
+        LaunchScope ls("tile_tables", st);                                                                  \
+        k2_tile_tables<LT, BB><<<grid, 1 << (LT - 6), 0, st>>>(Pl->d_W, Pl->d_cls, Pl->d_Wt, Pl->d_clst, S, nlo); \
+        break;                                                                                              \
+    }
+    switch (B) {
+        DWT_TT(4)
+        DWT_TT(5)
+        DWT_TT(6)
+        DWT_TT(7)
+        DWT_TT(8)
+        DWT_TT(9)
+        DWT_TT(10)
+        default: break;
+    }
+#undef DWT_TT
+    DWT_CK_LAUNCH("k2_tile_tables");
+    return DWT_OK;
+}
+
+// dwt_interpolate for p = 2, FP32, 16 <= m <= 24: forward low pass (f -> c),
+// fused top pass (c -> c), inverse low pass (c -> c), per function so that c
+// stays in L2 between the passes
+int p2_interpolate(dwt_plan_s* Pl, const float* f, float* c, float* coef, int batch, long long ld, const float* W,
+                   double** part_out, long long* ntile_out, cudaStream_t st) {
+    const int m = Pl->m;
+    const long long N = Pl->N;
+    constexpr int LT = kFusedLT;
+    const int L = p2_low_digits(m);
+    const int B = m - L;
+    const int nb = Pl->s + 1, nb2 = 2 * nb;
+    const int nw = (1 << (LT - 6)) >> 5;
+    const size_t bins_bytes = ((size_t)nw * nb2 * 32 + (size_t)nw * nb2) * 4;
+    const size_t xbytes = ((size_t)1 << LT) * 4 + 1024;
+    if (std::max(bins_bytes, xbytes) + ((size_t)1 << LT) * 4 > 227 * 1024) {
+        set_error("s too large for the fused p = 2 pass");
+        return DWT_EUNSUPPORTED;
+    }
+    const long long ntile = N >> LT;
+    int rc = ensure_workspace(Pl, (size_t)batch * (ntile + 1) * nb2 * sizeof(double));
+    if (rc) return rc;
+    double* part = (double*)Pl->d_ws;
+    const long long fbytes = N * 4;
+    int G = (int)std::max(1ll, kL2GroupP2 / fbytes);
+    G = std::min(G, 65535);
+    for (int f0 = 0; f0 < batch; f0 += G) {
+        const int nf = std::min(G, batch - f0);
+        const long long off = (long long)f0 * ld;
+        rc = launch_low<float>(L, f + off, c + off, ld, ld, nf, N, 1.f, 0, "interp_fwd", st);
+        if (rc) return rc;
+        HiArgs a{};
+        a.in = c + off;
+        a.out = c + off;
+        a.ld_in = ld;
+        a.ld_out = ld;
+        a.S = 1ll << L;
+        a.nlo = a.S >> (LT - B);
+        a.ntile = ntile;
+        a.scale = (float)(1.0 / (double)N);
+        a.do_scale = 1;
+        a.W = W ? Pl->d_Wt : nullptr;
+        a.cls = Pl->d_clst;
+        a.coef = coef ? (void*)(coef + off) : nullptr;
+        a.part = part + (long long)f0 * ntile * nb2;
+        a.nb = nb;
+        rc = coef ? launch_hi_t<float, LT, true, true>(B, a, nf, bins_bytes, "interp_top", st)
+                  : launch_hi_t<float, LT, true, false>(B, a, nf, bins_bytes, "interp_top", st);
+        if (rc) return rc;
+        rc = launch_low<float>(L, c + off, c + off, ld, ld, nf, N, 1.f, 0, "interp_inv", st);
+        if (rc) return rc;
+    }
+    *part_out = part;
+    *ntile_out = ntile;
+    return DWT_OK;
+}
+
+}  // namespace dwt

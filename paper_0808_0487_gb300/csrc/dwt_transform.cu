@@ -17,6 +17,16 @@
 
 namespace dwt {
 
+bool p2_fast_ok(int m);
+int p2_transform(dwt_plan_s* Pl, const void* in, void* out, int batch, long long ld_in, long long ld_out,
+                 dwt_dtype t, int sgn, cudaStream_t st);
+int p2_interpolate(dwt_plan_s* Pl, const float* f, float* c, float* coef, int batch, long long ld, const float* W,
+                   double** part_out, long long* ntile_out, cudaStream_t st);
+
+static bool aligned16(const void* p, long long ld, int elem) {
+    return ((uintptr_t)p & 15) == 0 && ((ld * elem) & 15) == 0;
+}
+
 // ---------------------------------------------------------------------------
 // element helpers
 struct Tw {
@@ -172,6 +182,25 @@ template <int P, typename T> struct KMax {
                                     : (sizeof(T) == 8 ? (P == 3 ? 3 : P == 5 ? 2 : 1) : (P == 3 ? 2 : 1));
 };
 
+// global -> shared tile copy with 8 loads in flight per thread
+template <typename T, typename TI>
+__device__ __forceinline__ void load_tile(T* sm, const TI* in, int nel, int wlog, int cmask, int ncols, long long S) {
+    for (int e0 = threadIdx.x; e0 < nel; e0 += 8 * blockDim.x) {
+        T tmp[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            const int e = e0 + u * blockDim.x;
+            const int r = e >> wlog, c = e & cmask;
+            tmp[u] = (e < nel && c < ncols) ? promote<T, TI>(in[c + (long long)r * S]) : zero_of<T>();
+        }
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            const int e = e0 + u * blockDim.x;
+            if (e < nel) sm[spad<T>(e)] = tmp[u];
+        }
+    }
+}
+
 // ---------------------------------------------------------------------------
 struct PassArgs {
     const void* in;
@@ -198,12 +227,7 @@ __global__ void __launch_bounds__(256) k_pass(PassArgs a) {
     const int cmask = a.Wc - 1;
     const TI* in = reinterpret_cast<const TI*>(a.in) + fn * a.ld_in + base;
     T* out = reinterpret_cast<T*>(a.out) + fn * a.ld_out + base;
-    for (int e = threadIdx.x; e < nel; e += blockDim.x) {
-        const int r = e >> a.wlog, c = e & cmask;
-        T v = zero_of<T>();
-        if (c < ncols) v = promote<T, TI>(in[c + (long long)r * a.S]);
-        sm[spad<T>(e)] = v;
-    }
+    load_tile<T, TI>(sm, in, nel, a.wlog, cmask, ncols, a.S);
     __syncthreads();
     tile_stages<P, SGN, T, KMax<P, T>::v>(sm, a.b, a.R, a.wlog, a.tw);
     for (int e = threadIdx.x; e < nel; e += blockDim.x) {
@@ -238,14 +262,14 @@ template <> __device__ __forceinline__ float mulw<float>(float v, float w) { ret
 template <> __device__ __forceinline__ float2 mulw<float2>(float2 v, float w) { return make_float2(v.x * w, v.y * w); }
 
 // per-lane FP32 class sums -> one FP64 value per class and tile, fixed order
-__device__ __forceinline__ void reduce_bins(const float* bins, int nb2, double* out) {
+__device__ __forceinline__ void reduce_bins(const float* bins, int nb2, double* out, long long stride) {
     const int nw = blockDim.x >> 5, w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     for (int bi = w; bi < nb2; bi += nw) {
         float x = 0.f;
         for (int ww = 0; ww < nw; ++ww) x += bins[(ww * nb2 + bi) * 32 + lane];
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
-        if (lane == 0) out[bi] = (double)x;
+        if (lane == 0) out[bi * stride] = (double)x;
     }
 }
 
@@ -267,12 +291,7 @@ __global__ void __launch_bounds__(256) k_mid(MidArgs m) {
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const TI* in = reinterpret_cast<const TI*>(a.in) + fn * a.ld_in + base;
     T* out = reinterpret_cast<T*>(a.out) + fn * a.ld_out + base;
-    for (int e = threadIdx.x; e < nel; e += blockDim.x) {
-        const int r = e >> a.wlog, c = e & cmask;
-        T v = zero_of<T>();
-        if (c < ncols) v = promote<T, TI>(in[c + (long long)r * a.S]);
-        sm[spad<T>(e)] = v;
-    }
+    load_tile<T, TI>(sm, in, nel, a.wlog, cmask, ncols, a.S);
     for (int i = threadIdx.x; i < (int)(blockDim.x >> 5) * nb2 * 32; i += blockDim.x) bins[i] = 0.f;
     __syncthreads();
     tile_stages<P, -1, T, KMax<P, T>::v>(sm, a.b, a.R, a.wlog, a.tw);
@@ -294,7 +313,7 @@ __global__ void __launch_bounds__(256) k_mid(MidArgs m) {
         sm[spad<T>(e)] = v;
     }
     __syncthreads();
-    reduce_bins(bins, nb2, m.part + (fn * m.ntile + tile) * nb2);
+    reduce_bins(bins, nb2, m.part + fn * nb2 * m.ntile + tile, m.ntile);
     tile_stages<P, +1, T, KMax<P, T>::v>(sm, a.b, a.R, a.wlog, a.tw);
     for (int e = threadIdx.x; e < nel; e += blockDim.x) {
         const int r = e >> a.wlog, c = e & cmask;
@@ -323,43 +342,54 @@ __global__ void __launch_bounds__(256) k_effdim_bins(const T* coef, long long ld
         mybins[(nb + (int)k.y) * 32] += q;
     }
     __syncthreads();
-    reduce_bins(bins, nb2, part + (fn * nchunk + chunk) * nb2);
+    reduce_bins(bins, nb2, part + fn * nb2 * nchunk + chunk, nchunk);
 }
 
-// partials -> cumulative truncation / superposition variances and dimensions
-__global__ void k_effdim_finalize(const double* part, long long nchunk, int nb, double thr, double* var, int* dim) {
-    extern __shared__ double cls_sum[];   // [2*nb]
-    const int nb2 = 2 * nb;
-    const long long fn = blockIdx.x;
-    const double* pp = part + fn * nchunk * nb2;
-    for (int bi = threadIdx.x; bi < nb2; bi += blockDim.x) {
-        double acc = 0.0;
-        for (long long t = 0; t < nchunk; ++t) acc += pp[t * nb2 + bi];
-        cls_sum[bi] = acc;
-    }
+// partials part[fn][class][tile] -> per-class totals: one block per (class,
+// function); thread t sums tiles t, t+256, ... in order, then a fixed tree.
+__global__ void __launch_bounds__(256) k_effdim_classes(const double* __restrict__ part, long long nchunk, int nb2,
+                                                        double* csum) {
+    __shared__ double red[256];
+    const int bi = blockIdx.x;
+    const long long fn = blockIdx.y;
+    const double* pp = part + (fn * nb2 + bi) * nchunk;
+    double acc = 0.0;
+    for (long long t = threadIdx.x; t < nchunk; t += 256) acc += pp[t];
+    red[threadIdx.x] = acc;
     __syncthreads();
-    if (threadIdx.x == 0) {
-        double ct = 0.0, cs = 0.0;
-        double tot = 0.0;
-        for (int d = 0; d < nb; ++d) tot += cls_sum[d];
-        int dt = 0, ds = 0;
-        bool ft = false, fs = false;
-        for (int d = 0; d < nb; ++d) {
-            ct += cls_sum[d];
-            cs += cls_sum[nb + d];
-            if (var) {
-                var[(fn * 2 + 0) * nb + d] = ct;
-                var[(fn * 2 + 1) * nb + d] = cs;
-            }
-            if (tot > 0.0) {
-                if (!ft && ct >= thr * tot) { dt = d; ft = true; }
-                if (!fs && cs >= thr * tot) { ds = d; fs = true; }
-            }
+    for (int o = 128; o > 0; o >>= 1) {
+        if ((int)threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) csum[fn * nb2 + bi] = red[0];
+}
+
+// per-class totals -> cumulative truncation / superposition variances and dimensions
+__global__ void k_effdim_finalize(const double* __restrict__ csum, int nb, double thr, double* var, int* dim,
+                                  int batch) {
+    const int fn = blockIdx.x * blockDim.x + threadIdx.x;
+    if (fn >= batch) return;
+    const double* cs_ = csum + (long long)fn * 2 * nb;
+    double tot = 0.0;
+    for (int d = 0; d < nb; ++d) tot += cs_[d];
+    double ct = 0.0, cs = 0.0;
+    int dt = 0, ds = 0;
+    bool ft = false, fs = false;
+    for (int d = 0; d < nb; ++d) {
+        ct += cs_[d];
+        cs += cs_[nb + d];
+        if (var) {
+            var[((long long)fn * 2 + 0) * nb + d] = ct;
+            var[((long long)fn * 2 + 1) * nb + d] = cs;
         }
-        if (dim) {
-            dim[fn * 2 + 0] = dt;
-            dim[fn * 2 + 1] = ds;
+        if (tot > 0.0) {
+            if (!ft && ct >= thr * tot) { dt = d; ft = true; }
+            if (!fs && cs >= thr * tot) { ds = d; fs = true; }
         }
+    }
+    if (dim) {
+        dim[(long long)fn * 2 + 0] = dt;
+        dim[(long long)fn * 2 + 1] = ds;
     }
 }
 
@@ -487,6 +517,9 @@ static int transform_p(dwt_plan_s* Pl, const void* in, void* out, int batch, lon
 
 int run_transform(dwt_plan_s* Pl, const void* in, void* out, int batch, long long ld_in, long long ld_out,
                   dwt_dtype in_t, dwt_dtype out_t, int sgn, cudaStream_t st) {
+    if (Pl->p == 2 && (in_t == DWT_F32 || in_t == DWT_I32) && p2_fast_ok(Pl->m) && aligned16(in, ld_in, 4) &&
+        aligned16(out, ld_out, 4))
+        return p2_transform(Pl, in, out, batch, ld_in, ld_out, in_t, sgn, st);
     switch (Pl->p) {
         case 2: return transform_p<2>(Pl, in, out, batch, ld_in, ld_out, in_t, out_t, sgn, st);
         case 3: return transform_p<3>(Pl, in, out, batch, ld_in, ld_out, in_t, out_t, sgn, st);
@@ -507,10 +540,19 @@ static int bins_warps(size_t tile_bytes, int nb2) {
 static int finalize(dwt_plan_s* Pl, const double* part, long long nchunk, int batch, double thr, double* var, int* dim,
                     cudaStream_t st) {
     if (!var && !dim) return DWT_OK;
-    const int nb = Pl->s + 1;
+    const int nb = Pl->s + 1, nb2 = 2 * nb;
+    // per-class totals go right after the partials in the workspace
+    double* csum = const_cast<double*>(part) + (size_t)batch * nb2 * nchunk;
+    for (int f0 = 0; f0 < batch; f0 += 65535) {
+        const int nf = std::min(65535, batch - f0);
+        LaunchScope ls("effdim_classes", st);
+        k_effdim_classes<<<dim3((unsigned)nb2, (unsigned)nf), 256, 0, st>>>(part + (size_t)f0 * nb2 * nchunk, nchunk,
+                                                                            nb2, csum + (size_t)f0 * nb2);
+    }
+    DWT_CK_LAUNCH("k_effdim_classes");
     {
         LaunchScope ls("effdim_finalize", st);
-        k_effdim_finalize<<<batch, 128, 2 * nb * sizeof(double), st>>>(part, nchunk, nb, thr, var, dim);
+        k_effdim_finalize<<<(batch + 127) / 128, 128, 0, st>>>(csum, nb, thr, var, dim, batch);
     }
     DWT_CK_LAUNCH("k_effdim_finalize");
     return DWT_OK;
@@ -531,7 +573,7 @@ static int interpolate_t(dwt_plan_s* Pl, const void* f, void* c, void* coef, int
         return DWT_EUNSUPPORTED;
     }
     const size_t smem = ((tile_bytes + 15) & ~(size_t)15) + (size_t)nw * nb2 * 32 * 4;
-    int rc = ensure_workspace(Pl, (size_t)batch * ntile * nb2 * sizeof(double));
+    int rc = ensure_workspace(Pl, (size_t)batch * (ntile + 1) * nb2 * sizeof(double));
     if (rc) return rc;
     double* part = (double*)Pl->d_ws;
     auto kmid_first = k_mid<P, T, TI>;   // single pass: reads f directly
@@ -566,7 +608,7 @@ static int interpolate_t(dwt_plan_s* Pl, const void* f, void* c, void* coef, int
         m.W = weight == DWT_WEIGHT_INV_SQ_WAVENUMBER ? Pl->d_W : nullptr;
         m.cls = Pl->d_cls;
         m.coef = coef ? (void*)((T*)coef + off) : nullptr;
-        m.part = part + (long long)f0 * ntile * nb2;
+        m.part = part + (long long)f0 * ntile * nb2;   // [fn][class][tile] of this group
         m.ntile = ntile;
         m.nb = nb;
         {
@@ -589,6 +631,14 @@ static int interpolate_t(dwt_plan_s* Pl, const void* f, void* c, void* coef, int
 
 int run_interpolate(dwt_plan_s* Pl, const void* f, void* c, void* coef, int batch, long long ld, dwt_dtype f_t,
                     dwt_weight weight, double* var, int* dim, double thr, cudaStream_t st) {
+    if (Pl->p == 2 && Pl->m >= 16 && Pl->m <= 24 && aligned16(f, ld, 4) && aligned16(c, ld, 4)) {
+        double* part = nullptr;
+        long long ntile = 0;
+        int rc = p2_interpolate(Pl, (const float*)f, (float*)c, (float*)coef, batch, ld,
+                                weight == DWT_WEIGHT_INV_SQ_WAVENUMBER ? Pl->d_W : nullptr, &part, &ntile, st);
+        if (rc) return rc;
+        return finalize(Pl, part, ntile, batch, thr, var, dim, st);
+    }
     switch (Pl->p) {
         case 2: return interpolate_t<2, float, float>(Pl, f, c, coef, batch, ld, weight, var, dim, thr, st);
         case 3:
@@ -615,7 +665,7 @@ static int effdim_t(dwt_plan_s* Pl, const void* coef, int batch, long long ld, d
         return DWT_EUNSUPPORTED;
     }
     const size_t smem = (size_t)nw * nb2 * 32 * 4;
-    int rc = ensure_workspace(Pl, (size_t)batch * nchunk * nb2 * sizeof(double));
+    int rc = ensure_workspace(Pl, (size_t)batch * (nchunk + 1) * nb2 * sizeof(double));
     if (rc) return rc;
     double* part = (double*)Pl->d_ws;
     auto kern = k_effdim_bins<T>;

@@ -144,3 +144,38 @@ def test_eval_functions(dwt, dev, orc, p, m, s):
     dwt.dwt_eval_exp(plan, e, 1, N, dwt.DWT_F32)
     ref = orc.eval_exp(p, m, Y)
     assert np.abs(_np(e)[0] - ref).max() < 1e-5 * np.abs(ref).max()
+
+
+@pytest.mark.parametrize("m,s", [(16, 5), (18, 8), (21, 12), (24, 6)])
+def test_interpolate_p2_register_tile_sizes(dwt, dev, orc, m, s):
+    p, N = 2, 2 ** m
+    C = S.small_net(p, m, s, index=m)
+    plan = dwt.dwt_plan_create(p, m, s, C)
+    coef = S.uniform(S.stream_seed(27, S.P_COEFFS, m), s)
+    f = orc.eval_product(p, m, orc.net_points(p, m, C), coef)
+    tab = orc.coset_leaders_dp(p, m, C)
+    assert np.array_equal(_read_W(dwt, plan, N).view(np.uint32), tab["W32"].view(np.uint32))
+    cref, g, vt, vs, dt, ds = orc.interpolate(p, m, f, tab["W64"], tab["cls"], s)
+    fin = torch.tensor(f.astype(np.float32), device=dev)
+    c = torch.empty(N, device=dev)
+    coefo = torch.empty(N, device=dev)
+    var = torch.empty((1, 2, s + 1), dtype=torch.float64, device=dev)
+    dim = torch.empty((1, 2), dtype=torch.int32, device=dev)
+    dwt.dwt_interpolate(plan, fin, c, coefo, 1, N, dwt.DWT_F32, dwt.DWT_WEIGHT_INV_SQ_WAVENUMBER, var=var, dim=dim)
+    assert rel_l2(_np(c), cref.real) < 1e-5
+    assert rel_l2(_np(coefo), g.real) < 1e-5
+    v = _np(var)[0]
+    assert np.allclose(v[0], vt, rtol=1e-5, atol=1e-14 * vt[-1])
+    assert np.allclose(v[1], vs, rtol=1e-5, atol=1e-14 * vt[-1])
+    _check_dims(_np(dim)[0], dt, ds, vt, vs)
+
+
+def _read_W(dwt, plan, N):
+    import ctypes
+    Wp, _ = dwt.dwt_plan_tables(plan)
+    W = np.empty(N, dtype=np.float32)
+    rt = ctypes.CDLL("libcudart.so")
+    rt.cudaMemcpy.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_int]
+    torch.cuda.synchronize()
+    assert rt.cudaMemcpy(W.ctypes.data, Wp, 4 * N, 2) == 0
+    return W

@@ -180,3 +180,40 @@ def test_edge_cases(dwt, dev):
     x[0] = 1.0
     dwt.dwt_forward(plan, x, x, 1, 16, 16, dwt.DWT_F32, dwt.DWT_F32)
     assert torch.allclose(x, torch.full_like(x, 1 / 16))
+
+
+# the register-tile p = 2 kernels: one low pass (m <= 14) or low + high pass (16 <= m <= 24)
+@pytest.mark.parametrize("m", [12, 13, 14, 16, 17, 18, 19, 20, 21, 22, 23, 24])
+def test_p2_register_tile_sizes(dwt, dev, orc, m):
+    p, N, B = 2, 2 ** m, 2
+    C = S.small_net(p, m, 2, index=m)
+    plan = dwt.dwt_plan_create(p, m, 2, C, dwt.DWT_PLAN_TRANSFORM_ONLY)
+    v = S.uniform(S.stream_seed(25, S.P_VALUES, m), B * N) - 0.5
+    f = v.reshape(B, N)
+    fin = torch.tensor(f.astype(np.float32), device=dev)
+    out = torch.empty_like(fin)
+    dwt.dwt_forward(plan, fin, out, B, N, N, dwt.DWT_F32, dwt.DWT_F32)
+    got = _np(out)
+    for b in range(B):
+        assert rel_l2(got[b], orc.fwt(p, m, f[b]).real) < TOL32
+    dwt.dwt_inverse(plan, out, out, B, N, N, dwt.DWT_F32, dwt.DWT_F32)
+    assert rel_l2(_np(out), f) < TOL32
+    iv = S.integers(S.stream_seed(25, S.P_INTS, m), N, -1000, 1000)
+    ii = torch.tensor(iv.astype(np.int32), device=dev)
+    io = torch.empty_like(ii)
+    dwt.dwt_forward(plan, ii, io, 1, N, N, dwt.DWT_I32, dwt.DWT_I32)
+    assert np.array_equal(_np(io).astype(np.int64), orc.fwt_i64(m, iv))
+
+
+def test_p2_unaligned_ld_takes_generic_path(dwt, dev, orc):
+    p, m, N = 2, 20, 2 ** 20
+    ld = N + 1                       # rows not 16-byte aligned
+    C = S.small_net(p, m, 2, index=3)
+    plan = dwt.dwt_plan_create(p, m, 2, C, dwt.DWT_PLAN_TRANSFORM_ONLY)
+    f = S.uniform(S.stream_seed(26, S.P_VALUES), 2 * ld) - 0.5
+    fin = torch.tensor(f.astype(np.float32), device=dev)
+    out = torch.empty_like(fin)
+    dwt.dwt_forward(plan, fin, out, 2, ld, ld, dwt.DWT_F32, dwt.DWT_F32)
+    got = _np(out)
+    for b in range(2):
+        assert rel_l2(got[b * ld:b * ld + N], orc.fwt(p, m, f[b * ld:b * ld + N]).real) < TOL32
