@@ -169,6 +169,32 @@ int dwt_effdim(dwt_plan_t plan, const void *coef, int batch, long long ld, dwt_d
                int *dim, double threshold, void *stream);
 
 /*
+ * dwt_effdim_static: dwt_effdim that allocates nothing.  (The paper has no
+ * counterpart; this is a service of the library.)
+ * For callers that must not have the library allocate device memory: a host
+ * program that hands out its whole device-memory budget itself and forbids
+ * any later cudaMalloc, or a latency-critical loop that cannot absorb the
+ * device-wide synchronisation that cudaMalloc / cudaFree may cause.
+ * dwt_effdim keeps its per-tile class partials in a workspace that the plan
+ * grows with cudaMalloc; this call keeps them in one fixed 8 MiB array
+ * compiled into the library (every GPU that loads the library holds it until
+ * the process exits), and calls no allocating routine.
+ * Arguments, results and tolerance are those of dwt_effdim.
+ * Limit: one function may need at most 2^20 partials, i.e.
+ * 2 (s+1) (ceil(N / 8192) + 1) <= 1048576 (for s = 32, N <= 2^27); larger
+ * requests return DWT_EINVAL with a message.  Batches go through the array in
+ * groups, in stream order.
+ * The first call on each device looks up the array's device address (with
+ * that device current); make that first call before any stream capture.
+ * All calls on a device share the one array and it keeps the last call's
+ * contents (every entry a call reads it has written first, so nothing needs
+ * clearing); calls whose work overlaps on the GPU (different streams, or
+ * threads) race on it and must be serialised by the caller.
+ */
+int dwt_effdim_static(dwt_plan_t plan, const void *coef, int batch, long long ld, dwt_dtype t, double *var,
+                      int *dim, double threshold, void *stream);
+
+/*
  * Synthetic test functions at the net points (for workloads and tests):
  *   dwt_eval_product: f_b(x_n) = prod_j (1 + coef[b][j] (x_{j,n} - 1/2)),
  *     coef: device double [batch][s];

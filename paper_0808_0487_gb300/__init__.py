@@ -62,6 +62,7 @@ _SIGS = {
     "dwt_inverse": (_I, [_VP, _VP, _VP, _I, _LL, _LL, _I, _I, _I, _VP]),
     "dwt_interpolate": (_I, [_VP, _VP, _VP, _VP, _I, _LL, _I, _I, _I, _VP, _VP, ctypes.c_double, _VP]),
     "dwt_effdim": (_I, [_VP, _VP, _I, _LL, _I, _VP, _VP, ctypes.c_double, _VP]),
+    "dwt_effdim_static": (_I, [_VP, _VP, _I, _LL, _I, _VP, _VP, ctypes.c_double, _VP]),
     "dwt_eval_product": (_I, [_VP, _VP, _VP, _I, _LL, _I, _VP]),
     "dwt_eval_exp": (_I, [_VP, _VP, _I, _LL, _I, _VP]),
     "dwt_strerror": (ctypes.c_char_p, [_I]),
@@ -212,6 +213,12 @@ def dwt_interpolate(plan, f, c, coef, batch, ld, f_t, weight, algo=DWT_ALGO_AUTO
 def dwt_effdim(plan, coef, batch, ld, t, var=None, dim=None, threshold=0.99, stream=None):
     return _check(lib().dwt_effdim(plan.handle, _ptr(coef), batch, ld, t, _ptr(var), _ptr(dim), threshold,
                                    _stream(stream)))
+
+
+def dwt_effdim_static(plan, coef, batch, ld, t, var=None, dim=None, threshold=0.99, stream=None):
+    """dwt_effdim without any device allocation (fixed in-library scratch; see include/dwt.h)."""
+    return _check(lib().dwt_effdim_static(plan.handle, _ptr(coef), batch, ld, t, _ptr(var), _ptr(dim), threshold,
+                                          _stream(stream)))
 
 
 def dwt_eval_product(plan, coef, f, batch, ld, t, stream=None):

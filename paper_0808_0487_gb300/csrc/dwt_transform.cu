@@ -681,6 +681,47 @@ static int effdim_t(dwt_plan_s* Pl, const void* coef, int batch, long long ld, d
     return finalize(Pl, part, nchunk, batch, thr, var, dim, st);
 }
 
+// The class sums of effdim_t, with the partials and totals in a scratch array
+// supplied by the caller (cap doubles) instead of the plan's workspace:
+// functions go through in groups whose partials fit, one group after another
+// on the stream, so the array is reused in stream order.  Makes no allocation.
+template <typename T>
+static int effdim_scratch_t(dwt_plan_s* Pl, const void* coef, int batch, long long ld, double* var, int* dim,
+                            double thr, double* scratch, long long cap, cudaStream_t st) {
+    const int nb = Pl->s + 1, nb2 = 2 * nb;
+    const long long nchunk = (Pl->N + 8191) / 8192;
+    const long long per = (long long)nb2 * (nchunk + 1);
+    const int nw = bins_warps(0, nb2);
+    if (nw < 1 || per > cap) {
+        set_error("class partials of one function do not fit the scratch array");
+        return DWT_EINVAL;
+    }
+    const size_t smem = (size_t)nw * nb2 * 32 * 4;
+    auto kern = k_effdim_bins<T>;
+    int rc = set_smem(kern, smem);
+    if (rc) return rc;
+    const int G = (int)std::min<long long>(std::min<long long>(cap / per, 65535), batch);
+    for (int f0 = 0; f0 < batch; f0 += G) {
+        const int nf = std::min(G, batch - f0);
+        {
+            LaunchScope ls("effdim_bins", st);
+            kern<<<dim3((unsigned)nchunk, (unsigned)nf), nw * 32, smem, st>>>(
+                (const T*)coef + (long long)f0 * ld, ld, Pl->N, Pl->d_cls, nb, nchunk, scratch);
+        }
+        DWT_CK_LAUNCH("k_effdim_bins");
+        rc = finalize(Pl, scratch, nchunk, nf, thr, var ? var + (long long)f0 * 2 * nb : nullptr,
+                      dim ? dim + (long long)f0 * 2 : nullptr, st);
+        if (rc) return rc;
+    }
+    return DWT_OK;
+}
+
+int effdim_into_scratch(dwt_plan_s* Pl, const void* coef, int batch, long long ld, dwt_dtype t, double* var, int* dim,
+                        double thr, double* scratch, long long cap, cudaStream_t st) {
+    if (t == DWT_F32) return effdim_scratch_t<float>(Pl, coef, batch, ld, var, dim, thr, scratch, cap, st);
+    return effdim_scratch_t<float2>(Pl, coef, batch, ld, var, dim, thr, scratch, cap, st);
+}
+
 int run_effdim(dwt_plan_s* Pl, const void* coef, int batch, long long ld, dwt_dtype t, double* var, int* dim,
                double thr, cudaStream_t st) {
     if (t == DWT_F32) return effdim_t<float>(Pl, coef, batch, ld, var, dim, thr, st);
