@@ -250,18 +250,21 @@ def run_gpu(args):
     ms_prof, _ = timed(step, args.steps)
     dwt.dwt_profile_enable(False)
     fams = {}
-    for name in ("interp_fwd", "interp_top", "interp_inv", "effdim_finalize"):
+    for name in ("interp_fwd", "interp_top", "interp_inv", "interp_inv_fwd", "effdim_classes", "effdim_finalize"):
         n, tot = dwt.dwt_profile_query(name)
         if n:
             fams[name] = (n, tot)
     dom = max(fams, key=lambda k: fams[k][1]) if fams else None
-    # algorithmic bytes per launch: every launch covers one function of N points
-    bytes_per_point = {"interp_fwd": 8.0, "interp_top": 14.0, "interp_inv": 8.0}
+    # algorithmic bytes per point of the launch's own inputs and outputs: a low pass
+    # reads and writes 4 B per point; the fused top pass also reads the weight (4 B)
+    # and class (2 B) tables; interp_inv_fwd holds two low passes (2N points).
+    bytes_per_point = {"interp_fwd": 8.0, "interp_top": 14.0, "interp_inv": 8.0, "interp_inv_fwd": 8.0}
+    points_per_launch = {"interp_inv_fwd": 2 * N}
     roof = None
     if dom in bytes_per_point:
         n, tot = fams[dom]
         avg_s = tot / n / 1e3
-        ach = bytes_per_point[dom] * N / avg_s / 1e9
+        ach = bytes_per_point[dom] * points_per_launch.get(dom, N) / avg_s / 1e9
         roof = {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
                 "traffic": None, "kernel": dom, "peak_kind": peak_kind,
                 "avg_launch_us": avg_s * 1e6, "launches": n,
@@ -318,6 +321,59 @@ def run_gpu(args):
         pg.destroy_process_group()
 
 
+def run_serve(args):
+    """The serving workload: requests with their own nets, Poisson arrivals, continuous batching."""
+    import numpy as np
+
+    import paper_0808_0487_gb300 as dwt
+    import synthetic as S
+
+    ws, rank, local = _dist()
+    import torch
+    torch.cuda.set_device(local)
+    dwt.lib()
+    reqs = S.serving_requests(args.requests, first=rank * args.requests)
+    warm = S.serving_requests(16, first=10 ** 6)
+
+    def run(rate, label):
+        srv = dwt.dwt_server_create(0, slots=args.slots, max_queue=1 << 20)
+        for r in warm:
+            dwt.dwt_server_wait(srv, dwt.dwt_server_submit(srv, r["p"], r["m"], r["s"], r["C"], r["coef"]))
+        t_arr = None if rate is None else S.poisson_arrivals(len(reqs), rate)
+        t0 = time.perf_counter()
+        tickets = []
+        for i, r in enumerate(reqs):
+            if t_arr is not None:
+                dt = t0 + t_arr[i] - time.perf_counter()
+                if dt > 0:
+                    time.sleep(dt)
+            tickets.append(dwt.dwt_server_submit(srv, r["p"], r["m"], r["s"], r["C"], r["coef"]))
+        res = [dwt.dwt_server_wait(srv, t, 3600.0) for t in tickets]
+        wall = time.perf_counter() - t0
+        srv.close()
+        assert all(x["status"] == 0 for x in res), [x["status"] for x in res if x["status"]][:5]
+        lat = np.array([(x["t_done"] - x["t_submit"]) * 1e3 for x in res])
+        svc = np.array([(x["t_done"] - x["t_admit"]) * 1e3 for x in res])
+        plan = np.array([(x["t_plan"] - x["t_admit"]) * 1e3 for x in res])
+        pts = float(sum(r["p"] ** r["m"] for r in reqs))
+        return {"label": label, "rate_req_s": rate, "wall_s": wall, "req_per_s": len(reqs) / wall,
+                "points_per_s": pts / wall, "p50_ms": float(np.percentile(lat, 50)),
+                "p99_ms": float(np.percentile(lat, 99)), "service_p50_ms": float(np.percentile(svc, 50)),
+                "service_p99_ms": float(np.percentile(svc, 99)), "plan_p50_ms": float(np.percentile(plan, 50)),
+                "plan_p99_ms": float(np.percentile(plan, 99))}
+
+    sat = run(None, "saturated")
+    runs = [sat]
+    for frac in (0.5, 0.9):
+        runs.append(run(frac * sat["req_per_s"], "poisson_%.1f" % frac))
+    if rank == 0:
+        line = {"metric": "served p99 latency (ms), 10k-request mix p in {2,3,5}, N 2^10..2^22, s 2..64",
+                "value": runs[-1]["p99_ms"], "unit": "ms", "n_gpus": ws, "higher_is_better": False,
+                "requests": len(reqs), "slots": args.slots, "data": "synthetic", "dtype": "f32",
+                "config": {"workload": "serving_mix", "requests": len(reqs)}, "runs": runs}
+        print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -326,7 +382,13 @@ def main():
     ap.add_argument("--batch", type=int, default=32)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline leg")
+    ap.add_argument("--serve", action="store_true", help="run the serving workload instead")
+    ap.add_argument("--requests", type=int, default=10000)
+    ap.add_argument("--slots", type=int, default=8)
     args = ap.parse_args()
+    if args.serve:
+        run_serve(args)
+        return
     if args.impl == "reference":
         run_reference(args)
     else:

@@ -78,6 +78,13 @@ int dwt_plan_create(int p, int m, int s, const uint8_t *C, unsigned flags, void 
 /* Free a plan and its device tables (synchronises the device). NULL is ignored. */
 int dwt_plan_destroy(dwt_plan_t plan);
 
+/* Free a plan without synchronising: its device memory is released in stream
+ * order on "stream" (cudaFreeAsync).  The caller guarantees that all work that
+ * uses the plan is ordered before that point on "stream".  Plans are built
+ * with stream-ordered allocations, so concurrent streams that build, use and
+ * free their own plans never wait for one another. */
+int dwt_plan_destroy_async(dwt_plan_t plan, void *stream);
+
 /* Plan facts: p, m, s, N, and the status of its coset tables (DWT_OK,
  * DWT_ESPAN, DWT_EUNSUPPORTED, or -1 when built with TRANSFORM_ONLY). Any
  * output pointer may be NULL. */
@@ -204,6 +211,54 @@ int dwt_effdim_static(dwt_plan_t plan, const void *coef, int batch, long long ld
 int dwt_eval_product(dwt_plan_t plan, const double *coef, void *f, int batch, long long ld, dwt_dtype t,
                      void *stream);
 int dwt_eval_exp(dwt_plan_t plan, void *f, int batch, long long ld, dwt_dtype t, void *stream);
+
+/*
+ * Serving: a continuous-batching engine.  One request is a complete job of the
+ * method on its own net: build the plan of (p, m, s, C), sample the product
+ * test function f(x) = prod_j (1 + coef[j] (x_j - 1/2)) on it, and run
+ * dwt_interpolate (forward, weight, class variances / effective dimensions,
+ * inverse).  Requests queue FIFO; "slots" worker threads, one CUDA stream
+ * each, admit the head of the queue as soon as a slot is idle and its device
+ * footprint fits the budget left, so requests that arrive while others run
+ * are started as slots and memory free up, and their work overlaps on the GPU.
+ * All device memory on that path is stream-ordered (no device-wide sync).
+ */
+typedef struct dwt_server_s *dwt_server_t;
+
+typedef struct {
+    int p, m, s;            /* the net */
+    const uint8_t *C;       /* host [s][m][m], copied at submit */
+    const double *coef;     /* host [s] product-function coefficients, copied at submit */
+    int weight;             /* dwt_weight */
+    double threshold;       /* effective-dimension threshold, e.g. 0.99 */
+    float *c_out;           /* optional host output for c (N floats for p = 2, 2N for p > 2),
+                               written before the request completes; NULL = not returned */
+} dwt_request;
+
+typedef struct {
+    int status;             /* DWT_OK or the error of the request */
+    int s;
+    int d_trc, d_sup;
+    double var_trc[256];    /* cumulative, entries 0..s */
+    double var_sup[256];
+    double t_submit, t_admit, t_plan, t_done;   /* seconds since server creation */
+} dwt_result;
+
+/* hbm_budget_bytes: device bytes the admitted requests may hold together
+ * (0 = half the free memory); slots: concurrent requests (1..64);
+ * max_queue: queued requests before dwt_server_submit returns DWT_EBUSY. */
+int dwt_server_create(size_t hbm_budget_bytes, int slots, int max_queue, dwt_server_t *server);
+/* Queue a request; *ticket identifies it.  DWT_EBUSY: queue full; DWT_ENOMEM:
+ * the request alone exceeds the budget; DWT_EINVAL: bad shape. */
+int dwt_server_submit(dwt_server_t server, const dwt_request *req, unsigned long long *ticket);
+/* DWT_OK and *res when done (the ticket is then forgotten), DWT_EBUSY while pending. */
+int dwt_server_poll(dwt_server_t server, unsigned long long ticket, dwt_result *res);
+/* Block until done or timeout_s seconds pass (DWT_ETIMEOUT). */
+int dwt_server_wait(dwt_server_t server, unsigned long long ticket, double timeout_s, dwt_result *res);
+/* Queue length, device bytes held by admitted requests, server clock. */
+int dwt_server_stats(dwt_server_t server, long long *queued, size_t *bytes_in_use, double *now_s);
+/* Finish every queued request, then stop the workers and free the server. */
+int dwt_server_destroy(dwt_server_t server);
 
 /* Messages. */
 const char *dwt_strerror(int status);

@@ -40,6 +40,19 @@ DWT_PLAN_KEEP_INDEX_MAP = 2
 _lib = None
 
 
+class dwt_request(ctypes.Structure):
+    _fields_ = [("p", ctypes.c_int), ("m", ctypes.c_int), ("s", ctypes.c_int),
+                ("C", ctypes.c_void_p), ("coef", ctypes.c_void_p), ("weight", ctypes.c_int),
+                ("threshold", ctypes.c_double), ("c_out", ctypes.c_void_p)]
+
+
+class dwt_result(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int), ("s", ctypes.c_int), ("d_trc", ctypes.c_int), ("d_sup", ctypes.c_int),
+                ("var_trc", ctypes.c_double * 256), ("var_sup", ctypes.c_double * 256),
+                ("t_submit", ctypes.c_double), ("t_admit", ctypes.c_double), ("t_plan", ctypes.c_double),
+                ("t_done", ctypes.c_double)]
+
+
 class DwtError(RuntimeError):
     def __init__(self, status, msg):
         super().__init__("%s (status %d): %s" % (_strerror(status), status, msg))
@@ -53,6 +66,7 @@ _I = ctypes.c_int
 _SIGS = {
     "dwt_plan_create": (_I, [_I, _I, _I, _VP, ctypes.c_uint, _VP, ctypes.POINTER(_VP)]),
     "dwt_plan_destroy": (_I, [_VP]),
+    "dwt_plan_destroy_async": (_I, [_VP, _VP]),
     "dwt_plan_info": (_I, [_VP, _VP, _VP, _VP, _VP, _VP]),
     "dwt_plan_tables": (_I, [_VP, ctypes.POINTER(_VP), ctypes.POINTER(_VP)]),
     "dwt_points": (_I, [_VP, _VP, _LL, _VP]),
@@ -65,6 +79,13 @@ _SIGS = {
     "dwt_effdim_static": (_I, [_VP, _VP, _I, _LL, _I, _VP, _VP, ctypes.c_double, _VP]),
     "dwt_eval_product": (_I, [_VP, _VP, _VP, _I, _LL, _I, _VP]),
     "dwt_eval_exp": (_I, [_VP, _VP, _I, _LL, _I, _VP]),
+    "dwt_server_create": (_I, [ctypes.c_size_t, _I, _I, ctypes.POINTER(_VP)]),
+    "dwt_server_submit": (_I, [_VP, ctypes.POINTER(dwt_request), ctypes.POINTER(ctypes.c_ulonglong)]),
+    "dwt_server_poll": (_I, [_VP, ctypes.c_ulonglong, ctypes.POINTER(dwt_result)]),
+    "dwt_server_wait": (_I, [_VP, ctypes.c_ulonglong, ctypes.c_double, ctypes.POINTER(dwt_result)]),
+    "dwt_server_stats": (_I, [_VP, ctypes.POINTER(_LL), ctypes.POINTER(ctypes.c_size_t),
+                              ctypes.POINTER(ctypes.c_double)]),
+    "dwt_server_destroy": (_I, [_VP]),
     "dwt_strerror": (ctypes.c_char_p, [_I]),
     "dwt_last_error": (ctypes.c_char_p, []),
     "dwt_launch_count": (_LL, []),
@@ -167,6 +188,12 @@ def dwt_plan_destroy(plan):
     return DWT_OK
 
 
+def dwt_plan_destroy_async(plan, stream=None):
+    st = lib().dwt_plan_destroy_async(plan.handle, _stream(stream))
+    plan.handle = None
+    return _check(st)
+
+
 def dwt_plan_info(plan):
     p, m, s, t = _I(), _I(), _I(), _I()
     N = _LL()
@@ -254,3 +281,81 @@ def dwt_profile_query(name):
     ms = ctypes.c_double()
     _check(lib().dwt_profile_query(name.encode(), ctypes.byref(n), ctypes.byref(ms)))
     return n.value, ms.value
+
+
+# ---- serving ------------------------------------------------------------------
+class Server:
+    """Owner of a ``dwt_server_t`` (continuous-batching engine, see include/dwt.h)."""
+
+    def __init__(self, handle):
+        self.handle = handle
+        self._keep = {}
+
+    def close(self):
+        if self.handle:
+            lib().dwt_server_destroy(self.handle)
+            self.handle = None
+        self._keep.clear()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def dwt_server_create(hbm_budget_bytes=0, slots=8, max_queue=1 << 16):
+    h = _VP()
+    _check(lib().dwt_server_create(hbm_budget_bytes, slots, max_queue, ctypes.byref(h)))
+    return Server(h.value)
+
+
+def dwt_server_submit(server, p, m, s, C, coef, weight=DWT_WEIGHT_INV_SQ_WAVENUMBER, threshold=0.99, c_out=None):
+    """Queue one request; returns its ticket.  C and coef are copied by the call;
+    c_out (a host array) must stay alive until the request is done."""
+    C = np.ascontiguousarray(C, dtype=np.uint8)
+    coef = np.ascontiguousarray(coef, dtype=np.float64)
+    req = dwt_request(p, m, s, C.ctypes.data, coef.ctypes.data, weight, threshold, _ptr(c_out))
+    t = ctypes.c_ulonglong()
+    _check(lib().dwt_server_submit(server.handle, ctypes.byref(req), ctypes.byref(t)))
+    if c_out is not None:
+        server._keep[t.value] = c_out
+    return t.value
+
+
+def _result(r):
+    s = r.s
+    return dict(status=r.status, d_trc=r.d_trc, d_sup=r.d_sup, var_trc=np.array(r.var_trc[:s + 1]),
+                var_sup=np.array(r.var_sup[:s + 1]), t_submit=r.t_submit, t_admit=r.t_admit, t_plan=r.t_plan,
+                t_done=r.t_done)
+
+
+def dwt_server_poll(server, ticket):
+    """The result dict when done, else None."""
+    r = dwt_result()
+    st = lib().dwt_server_poll(server.handle, ticket, ctypes.byref(r))
+    if st == DWT_EBUSY:
+        return None
+    _check(st)
+    server._keep.pop(ticket, None)
+    return _result(r)
+
+
+def dwt_server_wait(server, ticket, timeout_s=600.0):
+    r = dwt_result()
+    _check(lib().dwt_server_wait(server.handle, ticket, timeout_s, ctypes.byref(r)))
+    server._keep.pop(ticket, None)
+    return _result(r)
+
+
+def dwt_server_stats(server):
+    q = _LL()
+    b = ctypes.c_size_t()
+    t = ctypes.c_double()
+    _check(lib().dwt_server_stats(server.handle, ctypes.byref(q), ctypes.byref(b), ctypes.byref(t)))
+    return dict(queued=q.value, bytes_in_use=b.value, now=t.value)
+
+
+def dwt_server_destroy(server):
+    server.close()
+    return DWT_OK

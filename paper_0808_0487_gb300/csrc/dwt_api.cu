@@ -74,21 +74,32 @@ void launch_end(const char* fam, cudaStream_t st) {
 }
 
 // ---- workspace ----------------------------------------------------------------
-int ensure_workspace(dwt_plan_s* P, size_t bytes) {
-    if (bytes <= P->ws_bytes) return DWT_OK;
-    if (P->d_ws) {
-        DWT_CK(cudaDeviceSynchronize());
-        cudaFree(P->d_ws);
-        P->d_ws = nullptr;
-        P->ws_bytes = 0;
-    }
-    size_t want = bytes < ((size_t)1 << 20) ? ((size_t)1 << 20) : bytes;
-    cudaError_t e = cudaMalloc(&P->d_ws, want);
+int dmalloc(void** p, size_t bytes, cudaStream_t st) {
+    *p = nullptr;
+    if (bytes == 0) bytes = 16;
+    cudaError_t e = cudaMallocAsync(p, bytes, st);
     if (e != cudaSuccess) {
         cudaGetLastError();
-        set_error("workspace allocation of %zu bytes failed", want);
+        *p = nullptr;
+        set_error("device allocation of %zu bytes failed (%s)", bytes, cudaGetErrorString(e));
         return DWT_ENOMEM;
     }
+    return DWT_OK;
+}
+
+void dfree(void* p, cudaStream_t st) {
+    if (p) cudaFreeAsync(p, st);
+}
+
+int ensure_workspace(dwt_plan_s* P, size_t bytes, cudaStream_t st) {
+    if (bytes <= P->ws_bytes) return DWT_OK;
+    // stream-ordered: the old buffer is released after the work queued on st
+    dfree(P->d_ws, st);
+    P->d_ws = nullptr;
+    P->ws_bytes = 0;
+    size_t want = bytes < ((size_t)1 << 20) ? ((size_t)1 << 20) : bytes;
+    int rc = dmalloc(&P->d_ws, want, st);
+    if (rc) return rc;
     P->ws_bytes = want;
     return DWT_OK;
 }
@@ -261,14 +272,14 @@ int dwt_plan_create(int p, int m, int s, const uint8_t* C, unsigned flags, void*
             col[(size_t)j * m + c] = (uint32_t)v;
         }
     int rc = DWT_OK;
+    P->st_create = st;
+    P->R_host = R;
     auto fail = [&](int code) {
         dwt_plan_destroy(P);
         return code;
     };
-    if (cudaMalloc(&P->d_R, R.size() * 4) != cudaSuccess || cudaMalloc(&P->d_col, col.size() * 4) != cudaSuccess ||
-        cudaMalloc(&P->d_C, P->C.size()) != cudaSuccess) {
-        cudaGetLastError();
-        set_error("plan allocation failed");
+    if (dmalloc((void**)&P->d_R, R.size() * 4, st) || dmalloc((void**)&P->d_col, col.size() * 4, st) ||
+        dmalloc((void**)&P->d_C, P->C.size(), st)) {
         return fail(DWT_ENOMEM);
     }
     if (cudaMemcpyAsync(P->d_R, R.data(), R.size() * 4, cudaMemcpyHostToDevice, st) != cudaSuccess ||
@@ -311,6 +322,23 @@ int dwt_plan_destroy(dwt_plan_t P) {
     cudaFree(P->d_T);
     cudaFree(P->d_D);
     cudaFree(P->d_ws);
+    delete P;
+    return DWT_OK;
+}
+
+int dwt_plan_destroy_async(dwt_plan_t P, void* stream) {
+    if (!P) return DWT_OK;
+    cudaStream_t st = (cudaStream_t)stream;
+    dfree(P->d_R, st);
+    dfree(P->d_col, st);
+    dfree(P->d_C, st);
+    dfree(P->d_W, st);
+    dfree(P->d_cls, st);
+    dfree(P->d_Wt, st);
+    dfree(P->d_clst, st);
+    dfree(P->d_T, st);
+    dfree(P->d_D, st);
+    dfree(P->d_ws, st);
     delete P;
     return DWT_OK;
 }

@@ -281,8 +281,8 @@ struct DpBuffers {
     uint8_t* D = nullptr;     // [s][N]
     uint8_t* M = nullptr;     // [m][N]  (M_0 aliases T_{j+1}, slots 1..m-1 used)
     uint8_t* M2 = nullptr;    // [2][N] ping-pong for the backward sweep
-    void free_all() {
-        cudaFree(T); cudaFree(D); cudaFree(M); cudaFree(M2);
+    void free_all(cudaStream_t st) {
+        dfree(T, st); dfree(D, st); dfree(M, st); dfree(M2, st);
         T = D = M = M2 = nullptr;
     }
 };
@@ -295,19 +295,16 @@ static int coset_tables_p(dwt_plan_s* Pl, cudaStream_t st) {
         set_error("rows of C_1..C_s span a space of dimension < m");
         return DWT_ESPAN;
     }
-    std::vector<uint32_t> R((size_t)s * m);
-    DWT_CK(cudaMemcpy(R.data(), Pl->d_R, R.size() * 4, cudaMemcpyDeviceToHost));
+    const std::vector<uint32_t>& R = Pl->R_host;
     DpBuffers b;
     auto oom = [&]() {
-        cudaGetLastError();
-        b.free_all();
-        set_error("coset table allocation failed");
+        b.free_all(st);
         return DWT_ENOMEM;
     };
-    if (cudaMalloc(&b.T, (size_t)(s + 1) * N) != cudaSuccess) return oom();
-    if (cudaMalloc(&b.D, (size_t)s * N) != cudaSuccess) return oom();
-    if (cudaMalloc(&b.M, (size_t)m * N) != cudaSuccess) return oom();
-    if (cudaMalloc(&b.M2, (size_t)2 * N) != cudaSuccess) return oom();
+    if (dmalloc((void**)&b.T, (size_t)(s + 1) * N, st)) return oom();
+    if (dmalloc((void**)&b.D, (size_t)s * N, st)) return oom();
+    if (dmalloc((void**)&b.M, (size_t)m * N, st)) return oom();
+    if (dmalloc((void**)&b.M2, (size_t)2 * N, st)) return oom();
     const unsigned gN = grid_for(N);
     // backward sweep
     {
@@ -333,7 +330,7 @@ static int coset_tables_p(dwt_plan_s* Pl, cudaStream_t st) {
     DWT_CK_LAUNCH("coset backward sweep");
     // saturation check on T_1
     unsigned* d_flag = nullptr;
-    DWT_CK(cudaMalloc(&d_flag, 2 * sizeof(unsigned)));
+    if (dmalloc((void**)&d_flag, 2 * sizeof(unsigned), st)) return oom();
     DWT_CK(cudaMemsetAsync(d_flag, 0, 2 * sizeof(unsigned), st));
     {
         LaunchScope ls("dp_check", st);
@@ -343,19 +340,19 @@ static int coset_tables_p(dwt_plan_s* Pl, cudaStream_t st) {
     DWT_CK(cudaMemcpyAsync(&mx, d_flag, sizeof(unsigned), cudaMemcpyDeviceToHost, st));
     DWT_CK(cudaStreamSynchronize(st));
     if (mx >= kInf) {
-        cudaFree(d_flag);
-        b.free_all();
+        dfree(d_flag, st);
+        b.free_all(st);
         set_error("a least nu over some coset reaches 255");
         return DWT_EUNSUPPORTED;
     }
     // forward reconstruction over all labels
     uint32_t* G = nullptr;
     unsigned long long* Pden = nullptr;
-    if (cudaMalloc(&G, (size_t)N * 4) != cudaSuccess || cudaMalloc(&Pden, (size_t)N * 8) != cudaSuccess ||
-        cudaMalloc(&Pl->d_W, (size_t)N * 4) != cudaSuccess || cudaMalloc(&Pl->d_cls, (size_t)N * 2) != cudaSuccess) {
-        cudaFree(G);
-        cudaFree(Pden);
-        cudaFree(d_flag);
+    if (dmalloc((void**)&G, (size_t)N * 4, st) || dmalloc((void**)&Pden, (size_t)N * 8, st) ||
+        dmalloc((void**)&Pl->d_W, (size_t)N * 4, st) || dmalloc((void**)&Pl->d_cls, (size_t)N * 2, st)) {
+        dfree(G, st);
+        dfree(Pden, st);
+        dfree(d_flag, st);
         return oom();
     }
     uint32_t* d_R = Pl->d_R;
@@ -389,15 +386,15 @@ static int coset_tables_p(dwt_plan_s* Pl, cudaStream_t st) {
     int over = 0;
     DWT_CK(cudaMemcpyAsync(&over, d_over, sizeof(int), cudaMemcpyDeviceToHost, st));
     DWT_CK(cudaStreamSynchronize(st));
-    cudaFree(G);
-    cudaFree(Pden);
-    cudaFree(d_flag);
+    dfree(G, st);
+    dfree(Pden, st);
+    dfree(d_flag, st);
     if (Pl->flags & DWT_PLAN_KEEP_INDEX_MAP) {
         Pl->d_T = b.T;
         Pl->d_D = b.D;
         b.T = b.D = nullptr;
     }
-    b.free_all();
+    b.free_all(st);
     if (over) {
         set_error("a weight denominator prod (1+k_j)^2 exceeds 64 bits");
         return DWT_EUNSUPPORTED;
@@ -419,9 +416,8 @@ template <int P>
 static int h_to_k_p(dwt_plan_s* Pl, const uint32_t* H, uint32_t* k, long long cnt, cudaStream_t st) {
     const long long N = Pl->N;
     const int m = Pl->m, s = Pl->s;
-    std::vector<uint32_t> R((size_t)s * m);
-    DWT_CK(cudaMemcpy(R.data(), Pl->d_R, R.size() * 4, cudaMemcpyDeviceToHost));
-    int rc = ensure_workspace(Pl, (size_t)m * N + (size_t)cnt * 4 + 256);
+    const std::vector<uint32_t>& R = Pl->R_host;
+    int rc = ensure_workspace(Pl, (size_t)m * N + (size_t)cnt * 4 + 256, st);
     if (rc) return rc;
     uint8_t* M = (uint8_t*)Pl->d_ws;
     uint32_t* G = (uint32_t*)((uint8_t*)Pl->d_ws + (((size_t)m * N + 255) & ~(size_t)255));

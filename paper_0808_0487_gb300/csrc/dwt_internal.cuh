@@ -66,6 +66,8 @@ struct dwt_plan_s {
     unsigned flags = 0;
     int tables_status = -1;
     std::vector<uint8_t> C;       // host copy [s][m][m]
+    std::vector<uint32_t> R_host; // host copy of d_R
+    cudaStream_t st_create = nullptr;   // stream the plan was built on
     // device copies of the generating data
     uint32_t* d_R = nullptr;      // [s][m]: coset label of row i of C_j, sum_c C[j][i][c] p^c
     uint32_t* d_col = nullptr;    // [s][m]: point contribution of index digit c = 1, sum_i C[j][i][c] p^{m-1-i}
@@ -86,7 +88,10 @@ struct dwt_plan_s {
 
 namespace dwt {
 
-int ensure_workspace(dwt_plan_s* P, size_t bytes);
+int ensure_workspace(dwt_plan_s* P, size_t bytes, cudaStream_t st);
+// stream-ordered device allocations (no device-wide synchronisation)
+int dmalloc(void** p, size_t bytes, cudaStream_t st);
+void dfree(void* p, cudaStream_t st);
 const PassPlan& pass_plan(dwt_plan_s* P, int elem_bytes);
 
 // kernels' host entry points (implemented in the .cu files)

@@ -151,23 +151,52 @@ __device__ __forceinline__ void lo_tile_compute(T* sm, typename P2<T>::t* v, int
 }
 
 template <typename T, int L>
-__device__ __forceinline__ void lo_tile_store(T* dst, const typename P2<T>::t* v, int t) {
+__device__ __forceinline__ void lo_tile_store(T* dst, const typename P2<T>::t* v, int t, bool stream_out) {
     T* pd = dst + 4 * (t & 15) + 1024 * (t >> 4);
+    if (stream_out) {   // final output: evict first from L2
 #pragma unroll
-    for (int g = 0; g < 16; ++g) st16(pd + 64 * g, v + 2 * g);
+        for (int g = 0; g < 16; ++g) {
+            typename P2<T>::v4 x;
+            x.x = v[2 * g].x; x.y = v[2 * g].y; x.z = v[2 * g + 1].x; x.w = v[2 * g + 1].y;
+            __stcs(reinterpret_cast<typename P2<T>::v4*>(pd + 64 * g), x);
+        }
+    } else {
+#pragma unroll
+        for (int g = 0; g < 16; ++g) st16(pd + 64 * g, v + 2 * g);
+    }
 }
 
+// One low-pass job: nf functions, tiles of 2^L elements.
+template <typename T> struct LoJob {
+    const T* in;
+    T* out;
+    long long ld_in, ld_out;
+    int nf;
+    float scale;
+    int do_scale;
+    int stream_out;   // store with evict-first (final results)
+};
+
+// Tiles [0, tiles0) belong to job 0, the rest to job 1: two independent low
+// passes share one launch (e.g. the inverse of one function and the forward of
+// the next), which keeps the memory system busy while either one computes.
 template <typename T, int L>
-__global__ void __launch_bounds__(1 << (L - 6), (L == 14 ? 3 : 4)) k2_lo(const T* in, T* out, long long ld_in,
-                                                                         long long ld_out, float scale, int do_scale) {
+__global__ void __launch_bounds__(1 << (L - 6), (L == 14 ? 3 : 4))
+    k2_lo(LoJob<T> j0, LoJob<T> j1, unsigned tiles0) {
     static_assert(L >= 12 && L <= 14, "low-pass tile 2^12 .. 2^14");
     using V = typename P2<T>::t;
     constexpr int NT = 1 << (L - 6);
     extern __shared__ __align__(16) unsigned char smraw[];
     T* sm = reinterpret_cast<T*>(smraw);
     const int t = threadIdx.x;
-    const T* src = in + blockIdx.y * ld_in + ((long long)blockIdx.x << L);
-    T* dst = out + blockIdx.y * ld_out + ((long long)blockIdx.x << L);
+    const bool second = blockIdx.x >= tiles0;
+    if ((int)blockIdx.y >= (second ? j1.nf : j0.nf)) return;
+    const long long tile = second ? blockIdx.x - tiles0 : blockIdx.x;
+    const T* src = (second ? j1.in : j0.in) + blockIdx.y * (second ? j1.ld_in : j0.ld_in) + (tile << L);
+    T* dst = (second ? j1.out : j0.out) + blockIdx.y * (second ? j1.ld_out : j0.ld_out) + (tile << L);
+    const float scale = second ? j1.scale : j0.scale;
+    const int do_scale = second ? j1.do_scale : j0.do_scale;
+    const bool stream_out = (second ? j1.stream_out : j0.stream_out) != 0;
     V v[32];
 #pragma unroll
     for (int q = 0; q < 16; ++q) ld16_cs(src + 4 * (t + NT * q), v + 2 * q);
@@ -177,7 +206,7 @@ __global__ void __launch_bounds__(1 << (L - 6), (L == 14 ? 3 : 4)) k2_lo(const T
 #pragma unroll
         for (int k = 0; k < 32; ++k) v[k] = pmul(v[k], scale);
     }
-    lo_tile_store<T, L>(dst, v, t);
+    lo_tile_store<T, L>(dst, v, t, stream_out);
 }
 
 // Persistent low pass over 2^14 tiles with a two-deep cp.async pipeline: the
@@ -224,7 +253,7 @@ __global__ void __launch_bounds__(256, 1) k2_lo_pipe(const T* in, T* out, long l
             for (int kk = 0; kk < 32; ++kk) v[kk] = pmul(v[kk], scale);
         }
         T* dst = out + (i / tiles_per_fn) * ld_out + ((i % tiles_per_fn) << L);
-        lo_tile_store<T, L>(dst, v, t);
+        lo_tile_store<T, L>(dst, v, t, false);
         __syncthreads();   // buffer free before the copy two tiles ahead lands in it
     }
     cp_async_wait_all();
@@ -348,21 +377,27 @@ __global__ void __launch_bounds__(1 << (LT - 6)) k2_hi(HiArgs a) {
         const bool has0 = base == 0 && t == 0;   // coset label H = 0 is register 0 of thread 0
 #pragma unroll
         for (int g = 0; g < 16; ++g) {
-            float wv[4] = {a.scale, a.scale, a.scale, a.scale};
+            // the tile-major weights carry the factor 2^-m already (exact: a power of 2)
+            float2 w01 = make_float2(a.scale, a.scale), w23 = w01;
             if (a.W) {
                 const float4 x4 = sw4[g * NT + t];
-                wv[0] *= x4.x; wv[1] *= x4.y; wv[2] *= x4.z; wv[3] *= x4.w;
+                w01 = make_float2(x4.x, x4.y);
+                w23 = make_float2(x4.z, x4.w);
             }
+            V& v01 = v[2 * g];
+            V& v23 = v[2 * g + 1];
+            v01 = __fmul2_rn(v01, w01);
+            v23 = __fmul2_rn(v23, w23);
+            const float2 q01 = __fmul2_rn(v01, v01), q23 = __fmul2_rn(v23, v23);
 #pragma unroll
             for (int u = 0; u < 4; ++u) {
                 const int j = 4 * g + u;
-                float& x = comp(v[j >> 1], j & 1);
-                x *= wv[u];
-                if constexpr (HAS_COEF) coef[G::goff(G::fused_e(t, j), a.S)] = x;
+                if constexpr (HAS_COEF) coef[G::goff(G::fused_e(t, j), a.S)] = comp(v[j >> 1], j & 1);
                 const unsigned word = u < 2 ? cl[g].x : cl[g].y;
                 const int kt = (word >> (16 * (u & 1))) & 0xff;
                 const int ks = (word >> (16 * (u & 1) + 8)) & 0xff;
-                const float qv = (j == 0 && has0) ? 0.f : x * x;
+                float qv = u == 0 ? q01.x : u == 1 ? q01.y : u == 2 ? q23.x : q23.y;
+                if (j == 0 && has0) qv = 0.f;
                 mybins[kt * 32] += qv;
                 mybins[(a.nb + ks) * 32] += qv;
             }
@@ -416,7 +451,8 @@ __global__ void __launch_bounds__(1 << (LT - 6)) k2_hi(HiArgs a) {
 template <int LT, int B>
 __global__ void __launch_bounds__(1 << (LT - 6)) k2_tile_tables(const float* __restrict__ W,
                                                                 const uint8_t* __restrict__ cls, float* Wt,
-                                                                uint8_t* clst, long long S, long long nlo) {
+                                                                uint8_t* clst, long long S, long long nlo,
+                                                                float scale) {
     using G = HiGeom<LT, B>;
     constexpr int NT = G::NT;
     const int t = threadIdx.x;
@@ -425,7 +461,7 @@ __global__ void __launch_bounds__(1 << (LT - 6)) k2_tile_tables(const float* __r
     for (int j = 0; j < 64; ++j) {
         const long long H = base + G::goff(G::fused_e(t, j), S);
         const long long o = (tile << LT) + 4 * ((j >> 2) * NT + t) + (j & 3);
-        Wt[o] = W[H];
+        Wt[o] = W[H] * scale;   // scale = 2^-m: exact
         clst[2 * o] = cls[2 * H];
         clst[2 * o + 1] = cls[2 * H + 1];
     }
@@ -449,18 +485,19 @@ static int p2_low_digits(int m) { return m <= 14 ? m : std::min(14, m - 4); }
 bool p2_fast_ok(int m) { return (m >= 12 && m <= 14) || (m >= 16 && m <= 24); }
 
 template <typename T>
-static int launch_lo(int L, const T* in, T* out, long long ld_in, long long ld_out, int nf, long long N, float scale,
-                     int do_scale, const char* fam, cudaStream_t st) {
+static int launch_lo2(int L, const LoJob<T>& a, const LoJob<T>* b, long long N, const char* fam, cudaStream_t st) {
     const unsigned tiles = (unsigned)(N >> L);
     const size_t smem = (((size_t)1 << L) + ((size_t)1 << (L - 4))) * sizeof(T);
-    dim3 grid(tiles, (unsigned)nf);
+    const int nf = b ? std::max(a.nf, b->nf) : a.nf;
+    dim3 grid(b ? 2 * tiles : tiles, (unsigned)nf);
+    const LoJob<T> jb = b ? *b : a;
     int rc;
 #define DWT_LO(LL)                                                                         \
     case LL: {                                                                             \
         auto k = k2_lo<T, LL>;                                                             \
         if ((rc = attr_smem(k, smem))) return rc;                                          \
         LaunchScope ls(fam, st);                                                           \
-        k<<<grid, 1 << (LL - 6), smem, st>>>(in, out, ld_in, ld_out, scale, do_scale);     \
+        k<<<grid, 1 << (LL - 6), smem, st>>>(a, jb, tiles);                                \
         break;                                                                             \
     }
     switch (L) {
@@ -472,6 +509,13 @@ static int launch_lo(int L, const T* in, T* out, long long ld_in, long long ld_o
 #undef DWT_LO
     DWT_CK_LAUNCH("k2_lo");
     return DWT_OK;
+}
+
+template <typename T>
+static int launch_lo(int L, const T* in, T* out, long long ld_in, long long ld_out, int nf, long long N, float scale,
+                     int do_scale, const char* fam, cudaStream_t st) {
+    LoJob<T> a{in, out, ld_in, ld_out, nf, scale, do_scale, 0};
+    return launch_lo2<T>(L, a, nullptr, N, fam, st);
 }
 
 static int num_sms() {
@@ -602,16 +646,14 @@ int p2_build_tiled_tables(dwt_plan_s* Pl, cudaStream_t st) {
     const int L = p2_low_digits(m);
     const int B = m - L;
     const long long N = Pl->N, S = 1ll << L, nlo = S >> (LT - B);
-    if (cudaMalloc(&Pl->d_Wt, (size_t)N * 4) != cudaSuccess || cudaMalloc(&Pl->d_clst, (size_t)N * 2) != cudaSuccess) {
-        cudaGetLastError();
-        set_error("tiled table allocation failed");
+    if (dmalloc((void**)&Pl->d_Wt, (size_t)N * 4, st) || dmalloc((void**)&Pl->d_clst, (size_t)N * 2, st))
         return DWT_ENOMEM;
-    }
     const unsigned grid = (unsigned)(N >> LT);
+    const float sc = (float)(1.0 / (double)N);
 #define DWT_TT(BB)                                                                                          \
     case BB: {                                                                                              \
         LaunchScope ls("tile_tables", st);                                                                  \
-        k2_tile_tables<LT, BB><<<grid, 1 << (LT - 6), 0, st>>>(Pl->d_W, Pl->d_cls, Pl->d_Wt, Pl->d_clst, S, nlo); \
+        k2_tile_tables<LT, BB><<<grid, 1 << (LT - 6), 0, st>>>(Pl->d_W, Pl->d_cls, Pl->d_Wt, Pl->d_clst, S, nlo, sc); \
         break;                                                                                              \
     }
     switch (B) {
@@ -648,17 +690,23 @@ int p2_interpolate(dwt_plan_s* Pl, const float* f, float* c, float* coef, int ba
         return DWT_EUNSUPPORTED;
     }
     const long long ntile = N >> LT;
-    int rc = ensure_workspace(Pl, (size_t)batch * (ntile + 1) * nb2 * sizeof(double));
+    int rc = ensure_workspace(Pl, (size_t)batch * (ntile + 1) * nb2 * sizeof(double), st);
     if (rc) return rc;
     double* part = (double*)Pl->d_ws;
     const long long fbytes = N * 4;
     int G = (int)std::max(1ll, kL2GroupP2 / fbytes);
     G = std::min(G, 65535);
+    // forward low pass of the first group; then per group: fused top pass, and one
+    // launch holding this group's inverse low pass and the next group's forward
+    {
+        const int nf0 = std::min(G, batch);
+        LoJob<float> fw{f, c, ld, ld, nf0, 1.f, 0, 0};
+        rc = launch_lo2<float>(L, fw, nullptr, N, "interp_fwd", st);
+        if (rc) return rc;
+    }
     for (int f0 = 0; f0 < batch; f0 += G) {
         const int nf = std::min(G, batch - f0);
         const long long off = (long long)f0 * ld;
-        rc = launch_low<float>(L, f + off, c + off, ld, ld, nf, N, 1.f, 0, "interp_fwd", st);
-        if (rc) return rc;
         HiArgs a{};
         a.in = c + off;
         a.out = c + off;
@@ -677,7 +725,16 @@ int p2_interpolate(dwt_plan_s* Pl, const float* f, float* c, float* coef, int ba
         rc = coef ? launch_hi_t<float, LT, true, true>(B, a, nf, bins_bytes, "interp_top", st)
                   : launch_hi_t<float, LT, true, false>(B, a, nf, bins_bytes, "interp_top", st);
         if (rc) return rc;
-        rc = launch_low<float>(L, c + off, c + off, ld, ld, nf, N, 1.f, 0, "interp_inv", st);
+        LoJob<float> inv{c + off, c + off, ld, ld, nf, 1.f, 0, 1};
+        const int g1 = f0 + G;
+        if (g1 < batch) {
+            const int nf1 = std::min(G, batch - g1);
+            const long long off1 = (long long)g1 * ld;
+            LoJob<float> fw{f + off1, c + off1, ld, ld, nf1, 1.f, 0, 0};
+            rc = launch_lo2<float>(L, inv, &fw, N, "interp_inv_fwd", st);
+        } else {
+            rc = launch_lo2<float>(L, inv, nullptr, N, "interp_inv", st);
+        }
         if (rc) return rc;
     }
     *part_out = part;

@@ -573,7 +573,7 @@ static int interpolate_t(dwt_plan_s* Pl, const void* f, void* c, void* coef, int
         return DWT_EUNSUPPORTED;
     }
     const size_t smem = ((tile_bytes + 15) & ~(size_t)15) + (size_t)nw * nb2 * 32 * 4;
-    int rc = ensure_workspace(Pl, (size_t)batch * (ntile + 1) * nb2 * sizeof(double));
+    int rc = ensure_workspace(Pl, (size_t)batch * (ntile + 1) * nb2 * sizeof(double), st);
     if (rc) return rc;
     double* part = (double*)Pl->d_ws;
     auto kmid_first = k_mid<P, T, TI>;   // single pass: reads f directly
@@ -665,7 +665,7 @@ static int effdim_t(dwt_plan_s* Pl, const void* coef, int batch, long long ld, d
         return DWT_EUNSUPPORTED;
     }
     const size_t smem = (size_t)nw * nb2 * 32 * 4;
-    int rc = ensure_workspace(Pl, (size_t)batch * (nchunk + 1) * nb2 * sizeof(double));
+    int rc = ensure_workspace(Pl, (size_t)batch * (nchunk + 1) * nb2 * sizeof(double), st);
     if (rc) return rc;
     double* part = (double*)Pl->d_ws;
     auto kern = k_effdim_bins<T>;

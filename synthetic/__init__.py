@@ -163,3 +163,29 @@ def sample_indices(count, N, index=0, config=11):
     if count > 1:
         v[-1] = N - 1
     return v
+
+
+def serving_requests(count, config=5, first=0):
+    """The serving mix: p uniform in {2, 3, 5}; log2 N uniform in [10, 22], m = round(log_p N)
+    clamped to 10..22 (p=2), 7..13 (p=3), 5..9 (p=5); s uniform in 2..64; each request has its
+    own seeded upper-triangular net (seed = request id) and product-function coefficients
+    c_j ~ U(0,1).  Returns a list of dicts (p, m, s, C, coef)."""
+    out = []
+    lim = {2: (10, 22), 3: (7, 13), 5: (5, 9)}
+    for r in range(first, first + count):
+        u = uniform(stream_seed(config, P_SERVE, r), 3)
+        p = (2, 3, 5)[min(2, int(u[0] * 3))]
+        log2n = 10.0 + 12.0 * u[1]
+        m = int(round(log2n / np.log2(p)))
+        m = max(lim[p][0], min(lim[p][1], m))
+        s = 2 + min(62, int(u[2] * 63))
+        C = upper_triangular_matrices(p, m, s, stream_seed(config, P_MATRICES, r))
+        coef = uniform(stream_seed(config, P_COEFFS, r), s)
+        out.append(dict(id=r, p=p, m=m, s=s, C=C, coef=coef))
+    return out
+
+
+def poisson_arrivals(count, rate, config=5):
+    """Arrival times (seconds) of a Poisson process of the given rate."""
+    u = uniform(stream_seed(config, P_SERVE, 1 << 30), count)
+    return np.cumsum(-np.log1p(-u) / rate)
