@@ -351,7 +351,8 @@ def run_serve(args):
         res = [dwt.dwt_server_wait(srv, t, 3600.0) for t in tickets]
         wall = time.perf_counter() - t0
         srv.close()
-        assert all(x["status"] == 0 for x in res), [x["status"] for x in res if x["status"]][:5]
+        bad = [(r["p"], r["m"], r["s"], x["status"], x["message"]) for r, x in zip(reqs, res) if x["status"]]
+        assert not bad, bad[:8]
         lat = np.array([(x["t_done"] - x["t_submit"]) * 1e3 for x in res])
         svc = np.array([(x["t_done"] - x["t_admit"]) * 1e3 for x in res])
         plan = np.array([(x["t_plan"] - x["t_admit"]) * 1e3 for x in res])

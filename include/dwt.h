@@ -242,6 +242,7 @@ typedef struct {
     double var_trc[256];    /* cumulative, entries 0..s */
     double var_sup[256];
     double t_submit, t_admit, t_plan, t_done;   /* seconds since server creation */
+    char message[160];      /* error message when status != DWT_OK */
 } dwt_result;
 
 /* hbm_budget_bytes: device bytes the admitted requests may hold together

@@ -50,7 +50,7 @@ class dwt_result(ctypes.Structure):
     _fields_ = [("status", ctypes.c_int), ("s", ctypes.c_int), ("d_trc", ctypes.c_int), ("d_sup", ctypes.c_int),
                 ("var_trc", ctypes.c_double * 256), ("var_sup", ctypes.c_double * 256),
                 ("t_submit", ctypes.c_double), ("t_admit", ctypes.c_double), ("t_plan", ctypes.c_double),
-                ("t_done", ctypes.c_double)]
+                ("t_done", ctypes.c_double), ("message", ctypes.c_char * 160)]
 
 
 class DwtError(RuntimeError):
@@ -327,7 +327,7 @@ def _result(r):
     s = r.s
     return dict(status=r.status, d_trc=r.d_trc, d_sup=r.d_sup, var_trc=np.array(r.var_trc[:s + 1]),
                 var_sup=np.array(r.var_sup[:s + 1]), t_submit=r.t_submit, t_admit=r.t_admit, t_plan=r.t_plan,
-                t_done=r.t_done)
+                t_done=r.t_done, message=r.message.decode(errors="replace"))
 
 
 def dwt_server_poll(server, ticket):

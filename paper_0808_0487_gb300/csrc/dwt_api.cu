@@ -8,6 +8,7 @@
 #include <atomic>
 #include <map>
 #include <mutex>
+#include <unordered_set>
 
 #include "dwt_internal.cuh"
 
@@ -71,6 +72,21 @@ void launch_end(const char* fam, cudaStream_t st) {
             return;
         }
     }
+}
+
+// ---- per-kernel shared-memory limit ------------------------------------------------
+int smem_limit_max_ptr(const void* kern) {
+    static std::mutex mu;
+    static std::unordered_set<const void*> done;
+    std::lock_guard<std::mutex> lk(mu);
+    if (done.count(kern)) return DWT_OK;
+    int dev = 0, mx = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&mx, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute", __FILE__, __LINE__);
+    done.insert(kern);
+    return DWT_OK;
 }
 
 // ---- workspace ----------------------------------------------------------------

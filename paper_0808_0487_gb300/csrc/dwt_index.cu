@@ -555,7 +555,7 @@ static int eval_product_t(dwt_plan_s* Pl, const double* coef, T* f, int batch, l
         return DWT_EUNSUPPORTED;
     }
     auto kern = k_eval_product<P, T>;
-    if (smem > 48 * 1024) DWT_CK(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    if (int rc = smem_limit_max(kern)) return rc;
     {
         LaunchScope ls("eval_product", st);
         kern<<<grid_for(Pl->N), 256, smem, st>>>(Pl->d_C, Pl->d_col, Pl->m, Pl->s, Pl->N, coef, batch, f, ld);

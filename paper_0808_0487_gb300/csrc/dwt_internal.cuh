@@ -112,6 +112,15 @@ int run_eval_exp(dwt_plan_s* P, void* f, int batch, long long ld, dwt_dtype t, c
 int run_tc_transform(dwt_plan_s* P, const float* in, float* out, int batch, long long ld_in, long long ld_out,
                      int sgn, cudaStream_t st);
 
+// Raise a kernel's dynamic shared-memory limit to the device maximum, once per
+// kernel and thread-safely (the attribute belongs to the function, so
+// per-launch settings from concurrent host threads would race).
+int smem_limit_max_ptr(const void* kern);
+template <typename F>
+static inline int smem_limit_max(F* kern) {
+    return smem_limit_max_ptr(reinterpret_cast<const void*>(kern));
+}
+
 static inline long long ipow_ll(int p, int m) {
     long long v = 1;
     for (int i = 0; i < m; ++i) v *= p;

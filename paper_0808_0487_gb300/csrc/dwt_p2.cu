@@ -471,11 +471,8 @@ __global__ void __launch_bounds__(1 << (LT - 6)) k2_tile_tables(const float* __r
 // host side
 template <typename F>
 static int attr_smem(F* k, size_t bytes) {
-    if (bytes > 48 * 1024) {
-        cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
-        if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute", __FILE__, __LINE__);
-    }
-    return DWT_OK;
+    (void)bytes;
+    return smem_limit_max(k);
 }
 
 // digit split of the fast path: one low pass of L = m digits for 12 <= m <= 14;
@@ -624,6 +621,30 @@ static int p2_transform_t(dwt_plan_s* Pl, const T* in, T* out, int batch, long l
         a.scale = sc;
         a.do_scale = scale;
         rc = launch_hi_t<T, 14, false, false>(B, a, nf, 0, sgn < 0 ? "p2_hi_fwd" : "p2_hi_inv", st);
+        if (rc) return rc;
+    }
+    return DWT_OK;
+}
+
+// only the FP32 high pass (digits L .. m-1) over data in place; forward scales by 2^-m
+int p2_hi_only(dwt_plan_s* Pl, float* data, int batch, long long ld, int L, int sgn, cudaStream_t st) {
+    const int B = Pl->m - L;
+    HiArgs a{};
+    a.in = data;
+    a.out = data;
+    a.ld_in = ld;
+    a.ld_out = ld;
+    a.S = 1ll << L;
+    a.nlo = a.S >> (14 - B);
+    a.ntile = Pl->N >> 14;
+    a.scale = (float)(1.0 / (double)Pl->N);
+    a.do_scale = sgn < 0;
+    for (int f0 = 0; f0 < batch; f0 += 65535) {
+        HiArgs b = a;
+        b.in = data + (long long)f0 * ld;
+        b.out = data + (long long)f0 * ld;
+        int rc = launch_hi_t<float, 14, false, false>(B, b, std::min(65535, batch - f0), 0,
+                                                     sgn < 0 ? "p2_hi_fwd" : "p2_hi_inv", st);
         if (rc) return rc;
     }
     return DWT_OK;

@@ -14,6 +14,8 @@
 // stream-ordered, so requests in different slots overlap on the GPU and never
 // wait for each other's memory operations.  Results are kept by ticket until
 // polled; timestamps give queueing and service latency.
+#include <stdio.h>
+
 #include <chrono>
 #include <condition_variable>
 #include <deque>
@@ -78,6 +80,7 @@ static void run_request(dwt_server_s* S, Req& r, cudaStream_t st, double* var_h,
     int rc = dwt_plan_create(r.p, r.m, r.s, r.C.data(), 0, st, &plan);
     res.t_plan = S->now();
     if (rc != DWT_OK) {
+        snprintf(res.message, sizeof res.message, "plan: %s", dwt_last_error());
         if (plan) dwt_plan_destroy_async(plan, st);
         res.status = rc;
         return;
@@ -115,6 +118,7 @@ static void run_request(dwt_server_s* S, Req& r, cudaStream_t st, double* var_h,
         res.d_sup = dim_h[1];
     }
     res.status = rc;
+    if (rc) snprintf(res.message, sizeof res.message, "%s", dwt_last_error());
     dfree(f, st);
     dfree(c, st);
     dfree(coef, st);

@@ -410,11 +410,8 @@ static Tw make_tw(int p) {
 
 template <typename F>
 static int set_smem(F* kern, size_t bytes) {
-    if (bytes > 48 * 1024) {
-        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
-        if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute", __FILE__, __LINE__);
-    }
-    return DWT_OK;
+    (void)bytes;
+    return smem_limit_max(kern);
 }
 
 static PassArgs pass_args(const PassGeom& g, const void* in, void* out, long long ld_in, long long ld_out,

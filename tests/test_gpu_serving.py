@@ -94,3 +94,19 @@ def test_admission_limits(dwt):
             statuses.append(ex.status)
     assert dwt.DWT_EBUSY in statuses
     srv.close()
+
+
+def test_larger_requests_complete(dwt):
+    """One request of every (p, size class) of the serving mix, run concurrently."""
+    picked = {}
+    for r in S.serving_requests(600):
+        key = (r["p"], r["m"])
+        if key not in picked:
+            picked[key] = r
+    reqs = sorted(picked.values(), key=lambda r: r["p"] ** r["m"])
+    srv = dwt.dwt_server_create(0, slots=8)
+    tickets = [dwt.dwt_server_submit(srv, r["p"], r["m"], r["s"], r["C"], r["coef"]) for r in reqs]
+    res = [dwt.dwt_server_wait(srv, t) for t in tickets]
+    srv.close()
+    bad = [(r["p"], r["m"], r["s"], x["status"], x["message"]) for r, x in zip(reqs, res) if x["status"]]
+    assert not bad, bad
