@@ -244,6 +244,22 @@ def run_gpu(args):
     ms_i, _ = timed(inv, args.steps)
     peak, peak_kind = _peaks()
 
+    # the split-BF16 tensor-core forward (low 14 digits on tcgen05, the rest as
+    # FP32 butterflies) against the FP32 butterfly forward: time and deviation
+    c_tc = torch.empty_like(f)
+
+    def fwd_tc():
+        dwt.dwt_forward(plan, f, c_tc, B, N, N, dwt.DWT_F32, dwt.DWT_F32, algo=dwt.DWT_ALGO_TC_SPLIT_BF16,
+                        stream=stream)
+
+    ms_tc, _ = timed(fwd_tc, args.steps)
+    fwd()
+    fwd_tc()
+    torch.cuda.synchronize()
+    tc_rel = float((torch.linalg.vector_norm((c_tc - c).double()) / torch.linalg.vector_norm(c.double())).item())
+    tc_max = float(((c_tc - c).abs().max() / c.abs().max()).item())
+    del c_tc
+
     # per-kernel durations of the same step with events around every launch
     dwt.dwt_profile_reset()
     dwt.dwt_profile_enable(True)
@@ -312,6 +328,8 @@ def run_gpu(args):
             "inverse_points_per_s": B * N * args.steps * ws / (ms_i / 1e3),
             "forward_hbm_frac": (B * N * args.steps * 8 / (ms_f / 1e3) / 1e9) / peak,
             "inverse_hbm_frac": (B * N * args.steps * 8 / (ms_i / 1e3) / 1e9) / peak,
+            "forward_tc_points_per_s": B * N * args.steps * ws / (ms_tc / 1e3),
+            "forward_tc_vs_butterfly": {"rel_l2": tc_rel, "max_abs_over_max": tc_max},
             "step_hbm_frac_algorithmic": (B * N * args.steps * (8 + 6.0 / B) / (ms / 1e3) / 1e9) / peak,
             "kernel_ms": {k: v[1] / v[0] for k, v in fams.items()},
         }

@@ -166,8 +166,8 @@ struct Mptrs {
 
 // read k_j of every coset label (list) from the tables of coordinate j
 template <int P>
-__device__ __forceinline__ uint32_t recon_one(uint32_t& g, const uint8_t* __restrict__ Tj, const uint8_t* __restrict__ Dj,
-                                              const Mptrs& Mp, const uint32_t* __restrict__ Rj, int m) {
+__device__ __forceinline__ uint32_t recon_one(uint32_t& g, const uint8_t* Tj, const uint8_t* Dj, const Mptrs& Mp,
+                                              const uint32_t* __restrict__ Rj, int m) {
     const unsigned tau = Tj[g];
     const int d = Dj[g];
     if (d == 0) return 0;
@@ -402,12 +402,207 @@ static int coset_tables_p(dwt_plan_s* Pl, cudaStream_t st) {
     return DWT_OK;
 }
 
+// ---------------------------------------------------------------------------
+// The whole coset programme in one CTA, for small nets (N <= 2^16): the same
+// steps as above, separated by __syncthreads() instead of kernel launches, with
+// the working arrays of the backward sweep in shared memory (three N-byte
+// buffers).  A plan build is then a single launch on one SM, so many small
+// plans (the serving mix) build side by side.
+struct SmallDp {
+    long long N;
+    int m, s;
+    const uint32_t* R;       // [s][m]
+    uint8_t* T;              // [(s+1)][N]
+    uint8_t* D;              // [s][N]
+    uint8_t* M;              // [m][N] prefix minima of one coordinate (slot 0 unused)
+    uint32_t* G;             // [N]
+    unsigned long long* Pden;
+    uint8_t* cls;            // [N][2]
+    float* W;                // [N]
+    unsigned* flags;         // [0] max least-nu, [1] denominator overflow
+};
+
+template <int P>
+__global__ void __launch_bounds__(1024, 1) k_dp_small(SmallDp a) {
+    extern __shared__ uint8_t sbuf[];
+    const long long N = a.N;
+    const int m = a.m, s = a.s, t = threadIdx.x, nt = blockDim.x;
+    uint8_t* bx = sbuf;            // three rotating N-byte buffers
+    uint8_t* by = sbuf + N;
+    uint8_t* bz = sbuf + 2 * N;
+    // T_s
+    for (long long h = t; h < N; h += nt) {
+        const uint8_t v = h == 0 ? 0 : kInf;
+        by[h] = v;
+        a.T[(long long)s * N + h] = v;
+    }
+    __syncthreads();
+    uint8_t* Tn = by;   // T_{j+1}
+    for (int j = s - 1; j >= 0; --j) {
+        uint8_t* Tj = bx;
+        uint8_t* Ma = bz;
+        uint8_t* Mb = Tn;             // free once both copies are made
+        uint8_t* Dj = a.D + (long long)j * N;
+        for (long long h = t; h < N; h += nt) {
+            Tj[h] = Tn[h];
+            Ma[h] = Tn[h];
+            Dj[h] = 0;
+        }
+        __syncthreads();
+        for (int i = 0; i < m; ++i) {
+            const uint32_t r = a.R[j * m + i];
+            for (long long h = t; h < N; h += nt) {
+                unsigned e = kInf;
+#pragma unroll
+                for (int q = 1; q < P; ++q) {
+                    const unsigned v = Ma[dsub<P>((uint32_t)h, r, q, m)];
+                    e = v < e ? v : e;
+                }
+                const unsigned cur = Ma[h];
+                Mb[h] = (uint8_t)(e < cur ? e : cur);
+                unsigned cand = e == kInf ? kInf : e + (unsigned)(i + 1);
+                if (cand > kInf) cand = kInf;
+                if (cand < Tj[h]) {
+                    Tj[h] = (uint8_t)cand;
+                    Dj[h] = (uint8_t)(i + 1);
+                }
+            }
+            __syncthreads();
+            uint8_t* tmp = Ma;
+            Ma = Mb;
+            Mb = tmp;
+        }
+        for (long long h = t; h < N; h += nt) a.T[(long long)j * N + h] = Tj[h];
+        // rotate: T_j becomes T_{j+1} of the next coordinate
+        Tn = Tj;
+        bx = Ma;   // the two buffers not holding T_j
+        bz = Mb;
+        __syncthreads();
+    }
+    // saturation check on T_0
+    {
+        unsigned mx = 0;
+        for (long long h = t; h < N; h += nt) mx = max(mx, (unsigned)a.T[h]);
+        for (int o = 16; o > 0; o >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+        if ((t & 31) == 0) atomicMax(a.flags, mx);
+    }
+    __syncthreads();
+    if (*(volatile unsigned*)a.flags >= kInf) return;
+    // forward reconstruction over all labels
+    for (long long H = t; H < N; H += nt) {
+        a.G[H] = (uint32_t)H;
+        a.Pden[H] = 1ull;
+        a.cls[2 * H] = 0;
+        a.cls[2 * H + 1] = 0;
+    }
+    __syncthreads();
+    for (int j = 0; j < s; ++j) {
+        Mptrs mp;
+        mp.M[0] = a.T + (long long)(j + 1) * N;
+        for (int i = 1; i < m; ++i) {
+            const uint8_t* Mp = mp.M[i - 1];
+            uint8_t* Mi = a.M + (long long)i * N;
+            const uint32_t r = a.R[j * m + i - 1];
+            for (long long h = t; h < N; h += nt) {
+                unsigned v = Mp[h];
+#pragma unroll
+                for (int q = 1; q < P; ++q) {
+                    const unsigned w = Mp[dsub<P>((uint32_t)h, r, q, m)];
+                    v = w < v ? w : v;
+                }
+                Mi[h] = (uint8_t)v;
+            }
+            mp.M[i] = Mi;
+            __syncthreads();
+        }
+        const uint8_t* Tj = a.T + (long long)j * N;
+        const uint8_t* Dj = a.D + (long long)j * N;
+        const uint32_t* Rj = a.R + (long long)j * m;
+        for (long long H = t; H < N; H += nt) {
+            uint32_t g = a.G[H];
+            const uint32_t k = recon_one<P>(g, Tj, Dj, mp, Rj, m);
+            a.G[H] = g;
+            if (k) {
+                const unsigned long long q = (unsigned long long)k + 1ull, q2 = q * q;
+                const unsigned long long pd = a.Pden[H];
+                if (__umul64hi(pd, q2) != 0ull) atomicExch(a.flags + 1, 1u);
+                a.Pden[H] = pd * q2;
+                a.cls[2 * H] = (uint8_t)(j + 1);
+                a.cls[2 * H + 1] = (uint8_t)(a.cls[2 * H + 1] + 1);
+            }
+        }
+        __syncthreads();
+    }
+    for (long long H = t; H < N; H += nt) a.W[H] = __fdiv_rn(1.0f, __ull2float_rn(a.Pden[H]));
+}
+
+static const long long kSmallDpMax = 1ll << 16;
+
+template <int P>
+static int coset_tables_small(dwt_plan_s* Pl, cudaStream_t st) {
+    const long long N = Pl->N;
+    const int m = Pl->m, s = Pl->s;
+    if (host_rank(Pl) < m) {
+        set_error("rows of C_1..C_s span a space of dimension < m");
+        return DWT_ESPAN;
+    }
+    SmallDp a{};
+    a.N = N;
+    a.m = m;
+    a.s = s;
+    a.R = Pl->d_R;
+    uint8_t *T = nullptr, *D = nullptr, *M = nullptr;
+    uint32_t* G = nullptr;
+    unsigned long long* Pden = nullptr;
+    unsigned* flags = nullptr;
+    auto cleanup = [&]() {
+        dfree(T, st); dfree(D, st); dfree(M, st); dfree(G, st); dfree(Pden, st); dfree(flags, st);
+    };
+    if (dmalloc((void**)&T, (size_t)(s + 1) * N, st) || dmalloc((void**)&D, (size_t)s * N, st) ||
+        dmalloc((void**)&M, (size_t)m * N, st) || dmalloc((void**)&G, (size_t)N * 4, st) ||
+        dmalloc((void**)&Pden, (size_t)N * 8, st) || dmalloc((void**)&flags, 8, st) ||
+        dmalloc((void**)&Pl->d_W, (size_t)N * 4, st) || dmalloc((void**)&Pl->d_cls, (size_t)N * 2, st)) {
+        cleanup();
+        return DWT_ENOMEM;
+    }
+    DWT_CK(cudaMemsetAsync(flags, 0, 8, st));
+    a.T = T; a.D = D; a.M = M; a.G = G; a.Pden = Pden; a.cls = Pl->d_cls; a.W = Pl->d_W; a.flags = flags;
+    auto kern = k_dp_small<P>;
+    int rc = smem_limit_max(kern);
+    if (rc) { cleanup(); return rc; }
+    {
+        LaunchScope ls("dp_small", st);
+        kern<<<1, 1024, (size_t)3 * N, st>>>(a);
+    }
+    DWT_CK_LAUNCH("k_dp_small");
+    unsigned hf[2] = {0, 0};
+    DWT_CK(cudaMemcpyAsync(hf, flags, 8, cudaMemcpyDeviceToHost, st));
+    DWT_CK(cudaStreamSynchronize(st));
+    if (hf[0] >= kInf) {
+        cleanup();
+        set_error("a least nu over some coset reaches 255");
+        return DWT_EUNSUPPORTED;
+    }
+    if (Pl->flags & DWT_PLAN_KEEP_INDEX_MAP) {
+        Pl->d_T = T;
+        Pl->d_D = D;
+        T = D = nullptr;
+    }
+    cleanup();
+    if (hf[1]) {
+        set_error("a weight denominator prod (1+k_j)^2 exceeds 64 bits");
+        return DWT_EUNSUPPORTED;
+    }
+    return DWT_OK;
+}
+
 int build_coset_tables(dwt_plan_s* Pl, cudaStream_t st) {
+    const bool small = Pl->N <= kSmallDpMax;
     switch (Pl->p) {
-        case 2: return coset_tables_p<2>(Pl, st);
-        case 3: return coset_tables_p<3>(Pl, st);
-        case 5: return coset_tables_p<5>(Pl, st);
-        case 7: return coset_tables_p<7>(Pl, st);
+        case 2: return small ? coset_tables_small<2>(Pl, st) : coset_tables_p<2>(Pl, st);
+        case 3: return small ? coset_tables_small<3>(Pl, st) : coset_tables_p<3>(Pl, st);
+        case 5: return small ? coset_tables_small<5>(Pl, st) : coset_tables_p<5>(Pl, st);
+        case 7: return small ? coset_tables_small<7>(Pl, st) : coset_tables_p<7>(Pl, st);
         default: return DWT_EUNSUPPORTED;
     }
 }

@@ -116,3 +116,23 @@ def test_rank_deficient_plan(dwt, dev):
     with pytest.raises(dwt.DwtError):
         plan2 = dwt.dwt_plan_create(2, 4, 1, S.small_net(2, 4, 1), dwt.DWT_PLAN_TRANSFORM_ONLY)
         dwt.dwt_index_to_wavenumber(plan2, x, x, 1)
+
+
+# Nets with N <= 2^16 build their tables in one CTA, larger ones with one launch
+# per (coordinate, digit); these sizes sit on both sides of that boundary, with
+# the largest s the small path takes.
+@pytest.mark.parametrize("p,m,s", [(2, 16, 64), (2, 17, 6), (3, 10, 24), (5, 7, 5), (7, 5, 40), (2, 10, 2)])
+def test_tables_small_large_boundary(dwt, dev, orc, p, m, s):
+    C = S.small_net(p, m, s, index=m + s)
+    N = p ** m
+    plan = dwt.dwt_plan_create(p, m, s, C, dwt.DWT_PLAN_KEEP_INDEX_MAP)
+    assert plan.status == 0
+    W, cls = _read_tables(dwt, plan, N)
+    sel = S.sample_indices(300, N, index=m)
+    ref = orc.coset_leaders_dp(p, m, C, want_W64=False, Hsel=sel)
+    assert ref["status"] == 0
+    assert np.array_equal(W.view(np.uint32), ref["W32"].view(np.uint32))
+    assert np.array_equal(cls, ref["cls"])
+    k = torch.empty((300, s), dtype=torch.int32, device=dev)
+    dwt.dwt_index_to_wavenumber(plan, torch.tensor(sel.view(np.int32), device=dev), k, 300)
+    assert np.array_equal(k.cpu().numpy().view(np.uint32), ref["ksel"])
