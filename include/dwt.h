@@ -168,6 +168,27 @@ int dwt_interpolate(dwt_plan_t plan, const void *f, void *c, void *coef, int bat
                     double threshold, void *stream);
 
 /*
+ * dwt_interpolate on host-resident data: the same results as copying f to the
+ * device, calling dwt_interpolate and copying c, var and dim back, with the
+ * copies of one chunk of functions overlapped with the transforms of the next.
+ *   f: host, ld elements per function, type as for dwt_interpolate;
+ *   c: host output, ld elements per function (p = 2: float; p > 2: complex float);
+ *   var: optional host double [batch][2][s+1], or NULL;
+ *   dim: optional host int [batch][2], or NULL.
+ * Asynchronous like cudaMemcpyAsync: every copy and kernel is ordered on
+ * `stream` (two further streams of the plan carry the copies), so f, c, var
+ * and dim must stay valid until that stream has been synchronised.  Page-locked
+ * host buffers (cudaHostAlloc / cudaHostRegister) let the copies overlap with
+ * the computation; pageable buffers give the same results without overlap.
+ * The plan keeps three device slots of about 64 MiB of samples each (at least
+ * one function) from the first call until it is destroyed; calls on one plan
+ * must be issued from one stream or serialised by the caller.
+ * No counterpart in the paper: a transport of its interpolation step.
+ */
+int dwt_interpolate_host(dwt_plan_t plan, const void *f, void *c, int batch, long long ld, dwt_dtype f_t,
+                         dwt_weight weight, double *var, int *dim, double threshold, void *stream);
+
+/*
  * Effective dimension of given coefficients g (Sec. 4), the variance and
  * threshold part of dwt_interpolate alone.  coef: device, type DWT_F32
  * (p = 2) or DWT_C64, ld elements per function.  var/dim as above (device).

@@ -75,6 +75,7 @@ _SIGS = {
     "dwt_forward": (_I, [_VP, _VP, _VP, _I, _LL, _LL, _I, _I, _I, _VP]),
     "dwt_inverse": (_I, [_VP, _VP, _VP, _I, _LL, _LL, _I, _I, _I, _VP]),
     "dwt_interpolate": (_I, [_VP, _VP, _VP, _VP, _I, _LL, _I, _I, _I, _VP, _VP, ctypes.c_double, _VP]),
+    "dwt_interpolate_host": (_I, [_VP, _VP, _VP, _I, _LL, _I, _I, _VP, _VP, ctypes.c_double, _VP]),
     "dwt_effdim": (_I, [_VP, _VP, _I, _LL, _I, _VP, _VP, ctypes.c_double, _VP]),
     "dwt_effdim_static": (_I, [_VP, _VP, _I, _LL, _I, _VP, _VP, ctypes.c_double, _VP]),
     "dwt_eval_product": (_I, [_VP, _VP, _VP, _I, _LL, _I, _VP]),
@@ -235,6 +236,12 @@ def dwt_interpolate(plan, f, c, coef, batch, ld, f_t, weight, algo=DWT_ALGO_AUTO
                     threshold=0.99, stream=None):
     return _check(lib().dwt_interpolate(plan.handle, _ptr(f), _ptr(c), _ptr(coef), batch, ld, f_t, weight, algo,
                                         _ptr(var), _ptr(dim), threshold, _stream(stream)))
+
+
+def dwt_interpolate_host(plan, f, c, batch, ld, f_t, weight, var=None, dim=None, threshold=0.99, stream=None):
+    """dwt_interpolate on host buffers (f, c, var, dim host-resident; page-locked ones overlap copies)."""
+    return _check(lib().dwt_interpolate_host(plan.handle, _ptr(f), _ptr(c), batch, ld, f_t, weight, _ptr(var),
+                                             _ptr(dim), threshold, _stream(stream)))
 
 
 def dwt_effdim(plan, coef, batch, ld, t, var=None, dim=None, threshold=0.99, stream=None):

@@ -328,6 +328,7 @@ int dwt_plan_create(int p, int m, int s, const uint8_t* C, unsigned flags, void*
 int dwt_plan_destroy(dwt_plan_t P) {
     if (!P) return DWT_OK;
     cudaDeviceSynchronize();
+    host_stage_free(P, nullptr, true);
     cudaFree(P->d_R);
     cudaFree(P->d_col);
     cudaFree(P->d_C);
@@ -345,6 +346,7 @@ int dwt_plan_destroy(dwt_plan_t P) {
 int dwt_plan_destroy_async(dwt_plan_t P, void* stream) {
     if (!P) return DWT_OK;
     cudaStream_t st = (cudaStream_t)stream;
+    host_stage_free(P, st, false);
     dfree(P->d_R, st);
     dfree(P->d_col, st);
     dfree(P->d_C, st);
@@ -490,6 +492,28 @@ int dwt_interpolate(dwt_plan_t P, const void* f, void* c, void* coef, int batch,
     }
     if (batch == 0) return DWT_OK;
     return run_interpolate(P, f, c, coef, batch, ld, f_t, weight, var, dim, thr, (cudaStream_t)stream);
+}
+
+int dwt_interpolate_host(dwt_plan_t P, const void* f, void* c, int batch, long long ld, dwt_dtype f_t,
+                         dwt_weight weight, double* var, int* dim, double thr, void* stream) {
+    if (!P || batch < 0 || (batch > 0 && (!f || !c)) || ld < P->N || !(thr > 0.0 && thr <= 1.0)) {
+        set_error("dwt_interpolate_host: bad arguments");
+        return DWT_EINVAL;
+    }
+    if (weight != DWT_WEIGHT_NONE && weight != DWT_WEIGHT_INV_SQ_WAVENUMBER) {
+        set_error("unknown weight %d", (int)weight);
+        return DWT_EINVAL;
+    }
+    if (P->tables_status != DWT_OK) {
+        set_error("plan has no coset tables (status %d)", P->tables_status);
+        return P->tables_status > 0 ? P->tables_status : DWT_EUNSUPPORTED;
+    }
+    if (P->p == 2 ? f_t != DWT_F32 : (f_t != DWT_F32 && f_t != DWT_C64)) {
+        set_error("dwt_interpolate_host: p = 2 takes F32; p > 2 takes F32 (real) or C64");
+        return DWT_EUNSUPPORTED;
+    }
+    if (batch == 0) return DWT_OK;
+    return run_interpolate_host(P, f, c, batch, ld, f_t, weight, var, dim, thr, (cudaStream_t)stream);
 }
 
 int dwt_effdim(dwt_plan_t P, const void* coef, int batch, long long ld, dwt_dtype t, double* var, int* dim, double thr,

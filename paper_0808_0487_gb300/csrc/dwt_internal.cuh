@@ -60,6 +60,10 @@ struct PassPlan {
 
 }  // namespace dwt
 
+namespace dwt {
+struct HostStage;
+}
+
 struct dwt_plan_s {
     int p = 0, m = 0, s = 0;
     long long N = 0;
@@ -84,6 +88,8 @@ struct dwt_plan_s {
     size_t ws_bytes = 0;
     // pass decompositions by element size (4, 8, 16 bytes)
     dwt::PassPlan passes[3];
+    // device slots, streams and events of dwt_interpolate_host (first use)
+    dwt::HostStage* host = nullptr;
 };
 
 namespace dwt {
@@ -101,6 +107,11 @@ int run_interpolate(dwt_plan_s* P, const void* f, void* c, void* coef, int batch
                     dwt_weight weight, double* var, int* dim, double thr, cudaStream_t st);
 int run_effdim(dwt_plan_s* P, const void* coef, int batch, long long ld, dwt_dtype t, double* var, int* dim,
                double thr, cudaStream_t st);
+int run_interpolate_host(dwt_plan_s* P, const void* f_host, void* c_host, int batch, long long ld, dwt_dtype f_t,
+                         dwt_weight weight, double* var_host, int* dim_host, double thr, cudaStream_t st);
+// releases the plan's dwt_interpolate_host resources: after synchronising
+// (sync) or in the order of stream st
+void host_stage_free(dwt_plan_s* P, cudaStream_t st, bool sync);
 int run_points(dwt_plan_s* P, uint32_t* Y, long long ldY, cudaStream_t st);
 int run_k_to_h(dwt_plan_s* P, const uint32_t* k, uint32_t* H, long long cnt, cudaStream_t st);
 int run_h_to_k(dwt_plan_s* P, const uint32_t* H, uint32_t* k, long long cnt, cudaStream_t st);

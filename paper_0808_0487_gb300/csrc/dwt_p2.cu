@@ -106,6 +106,10 @@ __device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
     const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
     asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(sa), "l"(gmem) : "memory");
 }
+// bulk prefetch of [p, p + bytes) from global memory into L2 (bytes a multiple of 16)
+__device__ __forceinline__ void prefetch_l2(const void* p, unsigned bytes) {
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
+}
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
 
@@ -276,7 +280,6 @@ struct HiArgs {
     double* part;        // [fn][class][tile]
     long long ntile;
     int nb;
-    int wofs;            // byte offset of the weight stage in shared memory
 };
 
 template <int LT, int B> struct HiGeom {
@@ -301,8 +304,33 @@ template <int LT, int B> struct HiGeom {
     }
 };
 
+// Class sums of one register group (4 consecutive elements of a thread, one
+// 8-byte cls word: kt at byte 2u, ks at byte 2u + 1 for element u).  Element u
+// adds q[u] to the lane's max-support bin bt[32 kt_u] and support-size bin
+// bs[32 ks_u].  Elements go in pairs: the pair's four bins are loaded first and
+// stored last, so their shared-memory round trips overlap; if both elements of
+// the pair hit the same bin the second adds to the first's sum, so every bin
+// ends with exactly the element-order sum (bin + q_0) + q_1 ... of the
+// one-at-a-time form.
+__device__ __forceinline__ void bin_pair(float* bt, float* bs, unsigned w, float q0, float q1) {
+    const int kt0 = (int)(w & 0xffu), ks0 = (int)((w >> 8) & 0xffu);
+    const int kt1 = (int)((w >> 16) & 0xffu), ks1 = (int)(w >> 24);
+    const float xt0 = bt[32 * kt0], xt1 = bt[32 * kt1], xs0 = bs[32 * ks0], xs1 = bs[32 * ks1];
+    const float rt0 = xt0 + q0, rs0 = xs0 + q0;
+    const float rt1 = (kt1 == kt0 ? rt0 : xt1) + q1, rs1 = (ks1 == ks0 ? rs0 : xs1) + q1;
+    bt[32 * kt0] = rt0;
+    bs[32 * ks0] = rs0;
+    bt[32 * kt1] = rt1;
+    bs[32 * ks1] = rs1;
+}
+
+__device__ __forceinline__ void bin_group(float* bt, float* bs, uint2 c, const float (&q)[4]) {
+    bin_pair(bt, bs, c.x, q[0], q[1]);
+    bin_pair(bt, bs, c.y, q[2], q[3]);
+}
+
 template <typename T, int LT, int B, bool FUSED, bool HAS_COEF>
-__global__ void __launch_bounds__(1 << (LT - 6)) k2_hi(HiArgs a) {
+__global__ void __launch_bounds__(1 << (LT - 6), FUSED ? 4 : 1) k2_hi(HiArgs a) {
     static_assert(B >= 4 && B <= 10 && LT - B >= 2, "high-pass shape");
     using G = HiGeom<LT, B>;
     using V = typename P2<T>::t;
@@ -315,23 +343,17 @@ __global__ void __launch_bounds__(1 << (LT - 6)) k2_hi(HiArgs a) {
     const T* src = reinterpret_cast<const T*>(a.in) + fn * a.ld_in + base;
     T* dst = reinterpret_cast<T*>(a.out) + fn * a.ld_out + base;
     V v[32];
-    uint2 cl[FUSED ? 16 : 1];
     // layout A loads
 #pragma unroll
     for (int q = 0; q < 16; ++q) ld16(src + G::goff(4 * (t + NT * q), a.S), v + 2 * q);
     if constexpr (FUSED) {
-        // prefetch this tile's classes (registers) and weights (shared memory, async);
-        // tile-major order: group g of thread t at (g NT + t)
-        const uint2* cg = reinterpret_cast<const uint2*>(a.cls) + ((long long)tile << (LT - 2));
-#pragma unroll
-        for (int g = 0; g < 16; ++g) cl[g] = __ldcs(cg + g * NT + t);
-        if (a.W) {
-            const float* wg = a.W + ((long long)tile << LT);
-            unsigned char* sw = smraw + a.wofs;
-#pragma unroll
-            for (int i = 0; i < 16; ++i) cp_async16(sw + 16 * (t + NT * i), wg + 4 * (t + NT * i));
+        // this tile's weights (4 B per element) and classes (2 B) are contiguous
+        // in the tile-major tables: start moving them from HBM into L2 now, to be
+        // read after the forward stages
+        if (t == 0) {
+            if (a.W) prefetch_l2(a.W + ((long long)tile << LT), 4u << LT);
+            prefetch_l2(a.cls + ((long long)tile << (LT + 1)), 2u << LT);
         }
-        cp_async_commit();
     }
     bfly_range<2, 6>(v);   // e bits LT-4..LT-1 = row bits B-4..B-1
     // layout A in shared memory: pad(4(t + NT q)) = 4t + q 4NT + PADC (q >> QSH)
@@ -368,39 +390,55 @@ __global__ void __launch_bounds__(1 << (LT - 6)) k2_hi(HiArgs a) {
         const int nb2 = 2 * a.nb;
         const int lane = t & 31, w = t >> 5;
         if constexpr (B > 4) __syncthreads();
-        for (int i = t; i < (NT >> 5) * nb2 * 32; i += NT) bins[i] = 0.f;
-        cp_async_wait_all();
+        {
+            float4* b4 = reinterpret_cast<float4*>(bins);
+            for (int i = t; i < (NT >> 5) * nb2 * 8; i += NT) b4[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+        }
         __syncthreads();
-        float* mybins = bins + w * nb2 * 32 + lane;
-        const float4* sw4 = reinterpret_cast<const float4*>(smraw + a.wofs);
+        float* bt = bins + w * nb2 * 32 + lane;   // max-support classes of this lane
+        float* bs = bt + a.nb * 32;                 // support-size classes of this lane
         float* coef = HAS_COEF ? reinterpret_cast<float*>(a.coef) + fn * a.ld_out + base : nullptr;
         const bool has0 = base == 0 && t == 0;   // coset label H = 0 is register 0 of thread 0
+        // tile-major tables: register group g (4 elements) of thread t at g NT + t;
+        // the weights carry the factor 2^-m already (exact: a power of 2).  Groups
+        // are read two at a time, one pair ahead of the pair being binned.
+        const float4* wg = a.W ? reinterpret_cast<const float4*>(a.W) + ((long long)tile << (LT - 2)) + t : nullptr;
+        const uint2* cg = reinterpret_cast<const uint2*>(a.cls) + ((long long)tile << (LT - 2)) + t;
+        constexpr int CH = 2;
+        float4 wq[2][CH];
+        uint2 cq[2][CH];
+        auto fetch = [&](int c, int slot) {
 #pragma unroll
-        for (int g = 0; g < 16; ++g) {
-            // the tile-major weights carry the factor 2^-m already (exact: a power of 2)
-            float2 w01 = make_float2(a.scale, a.scale), w23 = w01;
-            if (a.W) {
-                const float4 x4 = sw4[g * NT + t];
-                w01 = make_float2(x4.x, x4.y);
-                w23 = make_float2(x4.z, x4.w);
+            for (int i = 0; i < CH; ++i) {
+                const int g = c * CH + i;
+                wq[slot][i] = wg ? __ldcs(wg + g * NT) : make_float4(a.scale, a.scale, a.scale, a.scale);
+                cq[slot][i] = __ldcs(cg + g * NT);
             }
-            V& v01 = v[2 * g];
-            V& v23 = v[2 * g + 1];
-            v01 = __fmul2_rn(v01, w01);
-            v23 = __fmul2_rn(v23, w23);
-            const float2 q01 = __fmul2_rn(v01, v01), q23 = __fmul2_rn(v23, v23);
+        };
+        fetch(0, 0);
 #pragma unroll
-            for (int u = 0; u < 4; ++u) {
-                const int j = 4 * g + u;
-                if constexpr (HAS_COEF) coef[G::goff(G::fused_e(t, j), a.S)] = comp(v[j >> 1], j & 1);
-                const unsigned word = u < 2 ? cl[g].x : cl[g].y;
-                const int kt = (word >> (16 * (u & 1))) & 0xff;
-                const int ks = (word >> (16 * (u & 1) + 8)) & 0xff;
-                float qv = u == 0 ? q01.x : u == 1 ? q01.y : u == 2 ? q23.x : q23.y;
-                if (j == 0 && has0) qv = 0.f;
-                mybins[kt * 32] += qv;
-                mybins[(a.nb + ks) * 32] += qv;
+        for (int c = 0; c < 16 / CH; ++c) {
+            if (c + 1 < 16 / CH) fetch(c + 1, (c + 1) & 1);
+#pragma unroll
+            for (int i = 0; i < CH; ++i) {
+                const int g = c * CH + i;
+                const float4 x4 = wq[c & 1][i];
+                V& v01 = v[2 * g];
+                V& v23 = v[2 * g + 1];
+                v01 = __fmul2_rn(v01, make_float2(x4.x, x4.y));
+                v23 = __fmul2_rn(v23, make_float2(x4.z, x4.w));
+                const float2 q01 = __fmul2_rn(v01, v01), q23 = __fmul2_rn(v23, v23);
+                if constexpr (HAS_COEF) {
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) {
+                        const int j = 4 * g + u;
+                        coef[G::goff(G::fused_e(t, j), a.S)] = comp(v[j >> 1], j & 1);
+                    }
+                }
+                const float q[4] = {(g == 0 && has0) ? 0.f : q01.x, q01.y, q23.x, q23.y};
+                bin_group(bt, bs, cq[c & 1][i], q);
             }
+            asm volatile("" ::: "memory");   // keep the next pair's loads behind this pair's bins
         }
         __syncthreads();
         // per-tile class sums, fixed order: lane l of warp w sums whole classes
@@ -415,7 +453,10 @@ __global__ void __launch_bounds__(1 << (LT - 6)) k2_hi(HiArgs a) {
             for (int b = lane; b < nb2; b += 32) {
                 float r[32];
 #pragma unroll
-                for (int k = 0; k < 32; ++k) r[k] = wb[b * 32 + ((k + lane) & 31)];
+                for (int i = 0; i < 8; ++i) {
+                    const float4 x = *reinterpret_cast<const float4*>(wb + b * 32 + 4 * ((i + lane) & 7));
+                    r[4 * i] = x.x; r[4 * i + 1] = x.y; r[4 * i + 2] = x.z; r[4 * i + 3] = x.w;
+                }
 #pragma unroll
                 for (int h = 16; h > 0; h >>= 1)
 #pragma unroll
@@ -553,11 +594,7 @@ static int launch_hi_one(HiArgs a, int nf, size_t bins_bytes, const char* fam, c
     using G = HiGeom<LT, B>;
     const size_t xbytes = (size_t)G::SMEM_ELEMS * sizeof(T);
     size_t smem = xbytes;
-    if (FUSED) {
-        const size_t u = (std::max(xbytes, bins_bytes) + 15) & ~(size_t)15;
-        a.wofs = (int)u;
-        smem = u + ((size_t)1 << LT) * sizeof(float);
-    }
+    if (FUSED) smem = (std::max(xbytes, bins_bytes) + 15) & ~(size_t)15;
     auto k = k2_hi<T, LT, B, FUSED, HAS_COEF>;
     int rc = attr_smem(k, smem);
     if (rc) return rc;
@@ -692,6 +729,18 @@ int p2_build_tiled_tables(dwt_plan_s* Pl, cudaStream_t st) {
     return DWT_OK;
 }
 
+// shared memory of the fused top pass: per-lane class bins of every warp and
+// the per-warp class sums; the tile exchange buffer aliases them
+static size_t fused_bins_bytes(int s) {
+    const size_t nw = ((size_t)1 << (kFusedLT - 6)) >> 5, nb2 = 2 * (size_t)(s + 1);
+    return (nw * nb2 * 32 + nw * nb2) * 4;
+}
+
+bool p2_interp_ok(int m, int s) {
+    const size_t xbytes = ((size_t)1 << kFusedLT) * 4 + 1024;
+    return m >= 16 && m <= 24 && std::max(fused_bins_bytes(s), xbytes) <= 227 * 1024;
+}
+
 // dwt_interpolate for p = 2, FP32, 16 <= m <= 24: forward low pass (f -> c),
 // fused top pass (c -> c), inverse low pass (c -> c), per function so that c
 // stays in L2 between the passes
@@ -703,11 +752,9 @@ int p2_interpolate(dwt_plan_s* Pl, const float* f, float* c, float* coef, int ba
     const int L = p2_low_digits(m);
     const int B = m - L;
     const int nb = Pl->s + 1, nb2 = 2 * nb;
-    const int nw = (1 << (LT - 6)) >> 5;
-    const size_t bins_bytes = ((size_t)nw * nb2 * 32 + (size_t)nw * nb2) * 4;
-    const size_t xbytes = ((size_t)1 << LT) * 4 + 1024;
-    if (std::max(bins_bytes, xbytes) + ((size_t)1 << LT) * 4 > 227 * 1024) {
-        set_error("s too large for the fused p = 2 pass");
+    const size_t bins_bytes = fused_bins_bytes(Pl->s);
+    if (!p2_interp_ok(m, Pl->s)) {
+        set_error("shape outside the fused p = 2 pass");
         return DWT_EUNSUPPORTED;
     }
     const long long ntile = N >> LT;

@@ -18,6 +18,7 @@
 namespace dwt {
 
 bool p2_fast_ok(int m);
+bool p2_interp_ok(int m, int s);
 int p2_transform(dwt_plan_s* Pl, const void* in, void* out, int batch, long long ld_in, long long ld_out,
                  dwt_dtype t, int sgn, cudaStream_t st);
 int p2_interpolate(dwt_plan_s* Pl, const float* f, float* c, float* coef, int batch, long long ld, const float* W,
@@ -628,7 +629,7 @@ static int interpolate_t(dwt_plan_s* Pl, const void* f, void* c, void* coef, int
 
 int run_interpolate(dwt_plan_s* Pl, const void* f, void* c, void* coef, int batch, long long ld, dwt_dtype f_t,
                     dwt_weight weight, double* var, int* dim, double thr, cudaStream_t st) {
-    if (Pl->p == 2 && Pl->m >= 16 && Pl->m <= 24 && aligned16(f, ld, 4) && aligned16(c, ld, 4)) {
+    if (Pl->p == 2 && p2_interp_ok(Pl->m, Pl->s) && aligned16(f, ld, 4) && aligned16(c, ld, 4)) {
         double* part = nullptr;
         long long ntile = 0;
         int rc = p2_interpolate(Pl, (const float*)f, (float*)c, (float*)coef, batch, ld,
