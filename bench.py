@@ -169,7 +169,12 @@ def run_reference(args):
 
 
 def cpu_baseline_sample():
-    """Oracle time for one function of the workload (about 10-20 s on one core)."""
+    """Oracle time on a bounded sample of the workload: one function on one thread,
+    then one function per thread on every host core this process may use (the
+    oracle's C routines release the interpreter lock, so the threads run in
+    parallel).  About 10-20 s in total."""
+    import concurrent.futures as cf
+
     import numpy as np
 
     import oracle
@@ -185,10 +190,94 @@ def cpu_baseline_sample():
     cls = np.zeros((N, 2), dtype=np.uint8)
     t0 = time.perf_counter()
     oracle.interpolate(p, m, f, W, cls, s)
-    t = time.perf_counter() - t0
-    return {"value": N / t, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": "1 of 32 functions (N=2^24), forward+weight+class sums+inverse in FP64, single thread; "
-                      "K(C) tables replaced by constants (plan time excluded on both arms)"}
+    t1 = time.perf_counter() - t0
+    threads = max(1, min(len(os.sched_getaffinity(0)), 32))
+    with cf.ThreadPoolExecutor(threads) as ex:
+        t0 = time.perf_counter()
+        list(ex.map(lambda _: oracle.interpolate(p, m, f, W, cls, s)[3], range(threads)))
+        tn = time.perf_counter() - t0
+    return {"value": threads * N / tn, "unit": UNIT, "cores": threads, "kind": "oracle",
+            "single_thread_value": N / t1,
+            "sample": "%d functions of the batch (N=2^24 each), one per thread, forward+weight+class sums+inverse "
+                      "in FP64; K(C) tables replaced by constants (plan time excluded on both arms)" % threads}
+
+
+# DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) of the
+# p = 2 interpolation kernels, read by ncu with --cache-control none on this
+# workload's launches (one function per launch, as in every step), together
+# with the SHA-256 of the kernel source they were taken from.  Any change to
+# that source makes the figures stale: they are then reported as null.
+MEASURED_TRAFFIC = {
+    "source": "paper_0808_0487_gb300/csrc/dwt_p2.cu",
+    "sha256": "07bd95fdc28fd34dc24fade2fae69abbbd6a95a200c8c2b053828652b97dbdee",
+    "bytes_per_launch": {"interp_top": 155.6e6, "interp_inv_fwd": 146.3e6},
+}
+
+
+def _traffic(family):
+    import hashlib
+    try:
+        src = open(os.path.join(ROOT, MEASURED_TRAFFIC["source"]), "rb").read()
+    except OSError:
+        return None
+    if hashlib.sha256(src).hexdigest() != MEASURED_TRAFFIC["sha256"]:
+        return None
+    return MEASURED_TRAFFIC["bytes_per_launch"].get(family)
+
+
+def run_other_configs(dwt, dev, stream, timed, steps):
+    """Throughput of the transforms at the other workload shapes: p = 2, m = 20,
+    s = 16 with 32 FP32 and 32 int32 functions (forward, inverse, round trip) and
+    p = 3, m = 13, s = 8 (real FP32 in, complex FP32 out; forward and inverse)."""
+    import torch
+
+    import synthetic as S
+    out = {}
+    w = S.workload_p2_m20()
+    p, m, s, B = w["p"], w["m"], w["s"], w["batch"]
+    N = p ** m
+    plan = dwt.dwt_plan_create(p, m, s, w["C"], dwt.DWT_PLAN_TRANSFORM_ONLY)
+    for name, dt, tt in (("f32", torch.float32, dwt.DWT_F32), ("i32", torch.int32, dwt.DWT_I32)):
+        x = torch.ones((B, N), dtype=dt, device=dev)
+        y = torch.empty_like(x)
+
+        def fw():
+            dwt.dwt_forward(plan, x, y, B, N, N, tt, tt, stream=stream)
+
+        def iv():
+            dwt.dwt_inverse(plan, y, x, B, N, N, tt, tt, stream=stream)
+
+        def rt():
+            fw()
+            iv()
+
+        r = {}
+        for k, fn in (("forward", fw), ("inverse", iv), ("round_trip", rt)):
+            ms, _ = timed(fn, steps)
+            r[k + "_points_per_s"] = B * N * steps / (ms / 1e3)
+        out["p2_m20_s16_b32_" + name] = r
+        del x, y
+    w = S.workload_p3_m13()
+    p, m, s = w["p"], w["m"], w["s"]
+    N = p ** m
+    ld = (N + 3) // 4 * 4
+    plan = dwt.dwt_plan_create(p, m, s, w["C"], dwt.DWT_PLAN_TRANSFORM_ONLY)
+    x = torch.ones((1, ld), dtype=torch.float32, device=dev)
+    y = torch.empty((1, ld), dtype=torch.complex64, device=dev)
+    z = torch.empty_like(y)
+
+    def fw3():
+        dwt.dwt_forward(plan, x, y, 1, ld, ld, dwt.DWT_F32, dwt.DWT_C64, stream=stream)
+
+    def iv3():
+        dwt.dwt_inverse(plan, y, z, 1, ld, ld, dwt.DWT_C64, dwt.DWT_C64, stream=stream)
+
+    r = {}
+    for k, fn in (("forward", fw3), ("inverse", iv3)):
+        ms, _ = timed(fn, steps)
+        r[k + "_points_per_s"] = N * steps / (ms / 1e3)
+    out["p3_m13_s8"] = r
+    return out
 
 
 def run_gpu(args):
@@ -308,9 +397,12 @@ def run_gpu(args):
         avg_s = tot / n / 1e3
         ach = bytes_per_point[dom] * points_per_launch.get(dom, N) / avg_s / 1e9
         roof = {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
-                "traffic": None, "kernel": dom, "peak_kind": peak_kind,
+                "traffic": _traffic(dom), "kernel": dom, "peak_kind": peak_kind,
                 "avg_launch_us": avg_s * 1e6, "launches": n,
                 "bytes_per_point": bytes_per_point[dom]}
+        if roof["traffic"]:
+            roof["dram_gbs"] = roof["traffic"] / avg_s / 1e9
+            roof["dram_frac"] = roof["dram_gbs"] / peak
     dwt.dwt_profile_reset()
 
     # end to end: pinned host f -> device, the step, c and the variances back
@@ -329,6 +421,8 @@ def run_gpu(args):
     K2 = max(1, min(args.steps, 5))
     ms_e2e, _ = timed(e2e_step, K2)
     e2e_value = B * N * K2 * ws / (ms_e2e / 1e3)
+
+    others = run_other_configs(dwt, dev, stream, timed, args.steps) if not args.no_others else None
 
     cpu = None
     if rank == 0 and not args.no_cpu:
@@ -357,6 +451,7 @@ def run_gpu(args):
             "forward_tc_vs_butterfly": {"rel_l2": tc_rel, "max_abs_over_max": tc_max},
             "step_hbm_frac_algorithmic": (B * N * args.steps * (8 + 6.0 / B) / (ms / 1e3) / 1e9) / peak,
             "kernel_ms": {k: v[1] / v[0] for k, v in fams.items()},
+            "other_workloads": others,
         }
         print(json.dumps(line), flush=True)
     if pg:
@@ -426,6 +521,7 @@ def main():
     ap.add_argument("--batch", type=int, default=32)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline leg")
+    ap.add_argument("--no-others", action="store_true", help="skip the p = 2, m = 20 and p = 3, m = 13 lines")
     ap.add_argument("--serve", action="store_true", help="run the serving workload instead")
     ap.add_argument("--requests", type=int, default=10000)
     ap.add_argument("--slots", type=int, default=8)

@@ -292,9 +292,16 @@ long long dwt_launch_count(void);
 /*
  * Optional per-kernel timing with CUDA events recorded on the launching stream
  * around every launch of this library.  dwt_profile_query synchronises on the
- * recorded events and returns, for kernel family "name" (see DESIGN notes in
- * the source: "pass_lo", "pass_hi", "pass_mid", ...), the number of launches
- * and their summed duration in milliseconds since the last reset.
+ * recorded events and returns, for kernel family "name", the number of
+ * launches and their summed duration in milliseconds since the last reset.
+ * Families: p = 2 register tiles "p2_lo_fwd", "p2_lo_inv", "p2_hi_fwd",
+ * "p2_hi_inv"; p = 2 interpolation "interp_fwd", "interp_top", "interp_inv",
+ * "interp_inv_fwd" (two low passes in one launch); tensor-core tiles
+ * "tc_lo14"; generic passes "pass_lo", "pass_mid", "pass_hi"; variance classes
+ * "effdim_bins", "effdim_classes", "effdim_finalize"; index maps "points",
+ * "k_to_h", "h2k_recon", "h2k_copy"; plan build "dp_init", "dp_step",
+ * "dp_check", "dp_prefix", "dp_recon", "dp_weights", "dp_small",
+ * "tile_tables"; test functions "eval_product", "eval_exp".
  */
 int dwt_profile_enable(int on);
 int dwt_profile_reset(void);
