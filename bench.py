@@ -368,6 +368,12 @@ def run_gpu(args):
                         stream=stream)
 
     ms_tc, _ = timed(fwd_tc, args.steps)
+
+    def step_tc():
+        dwt.dwt_interpolate(plan, f, c_tc, None, B, N, dwt.DWT_F32, dwt.DWT_WEIGHT_INV_SQ_WAVENUMBER,
+                            dwt.DWT_ALGO_TC_SPLIT_BF16, var=var, dim=dim, stream=stream)
+
+    ms_tci, _ = timed(step_tc, args.steps)
     fwd()
     fwd_tc()
     torch.cuda.synchronize()
@@ -449,6 +455,7 @@ def run_gpu(args):
             "inverse_hbm_frac": (B * N * args.steps * 8 / (ms_i / 1e3) / 1e9) / peak,
             "forward_tc_points_per_s": B * N * args.steps * ws / (ms_tc / 1e3),
             "forward_tc_vs_butterfly": {"rel_l2": tc_rel, "max_abs_over_max": tc_max},
+            "interpolate_tc_points_per_s": B * N * args.steps * ws / (ms_tci / 1e3),
             "step_hbm_frac_algorithmic": (B * N * args.steps * (8 + 6.0 / B) / (ms / 1e3) / 1e9) / peak,
             "kernel_ms": {k: v[1] / v[0] for k, v in fams.items()},
             "other_workloads": others,
@@ -495,7 +502,17 @@ def run_serve(args):
         svc = np.array([(x["t_done"] - x["t_admit"]) * 1e3 for x in res])
         plan = np.array([(x["t_plan"] - x["t_admit"]) * 1e3 for x in res])
         pts = float(sum(r["p"] ** r["m"] for r in reqs))
-        return {"label": label, "rate_req_s": rate, "wall_s": wall, "req_per_s": len(reqs) / wall,
+        # plan-build and service latency by net size (log2 N buckets)
+        lg = np.array([r["m"] * np.log2(r["p"]) for r in reqs])
+        by_size = []
+        for lo, hi in ((10, 13), (13, 16), (16, 19), (19, 23)):
+            sel = (lg >= lo - 0.01) & (lg < hi - 0.01)
+            if sel.any():
+                by_size.append({"log2N": [lo, hi], "requests": int(sel.sum()),
+                                "plan_p50_ms": float(np.percentile(plan[sel], 50)),
+                                "service_p50_ms": float(np.percentile(svc[sel], 50)),
+                                "service_p99_ms": float(np.percentile(svc[sel], 99))})
+        return {"label": label, "rate_req_s": rate, "wall_s": wall, "req_per_s": len(reqs) / wall, "by_size": by_size,
                 "points_per_s": pts / wall, "p50_ms": float(np.percentile(lat, 50)),
                 "p99_ms": float(np.percentile(lat, 99)), "service_p50_ms": float(np.percentile(svc, 50)),
                 "service_p99_ms": float(np.percentile(svc, 99)), "plan_p50_ms": float(np.percentile(plan, 50)),

@@ -486,12 +486,12 @@ int dwt_interpolate(dwt_plan_t P, const void* f, void* c, void* coef, int batch,
         set_error("dwt_interpolate: p = 2 takes F32; p > 2 takes F32 (real) or C64");
         return DWT_EUNSUPPORTED;
     }
-    if (algo != DWT_ALGO_AUTO && algo != DWT_ALGO_BUTTERFLY) {
-        set_error("dwt_interpolate runs the butterfly form");
-        return DWT_EUNSUPPORTED;
+    if (algo != DWT_ALGO_AUTO && algo != DWT_ALGO_BUTTERFLY && algo != DWT_ALGO_TC_SPLIT_BF16) {
+        set_error("unknown algo %d", (int)algo);
+        return DWT_EINVAL;
     }
     if (batch == 0) return DWT_OK;
-    return run_interpolate(P, f, c, coef, batch, ld, f_t, weight, var, dim, thr, (cudaStream_t)stream);
+    return run_interpolate(P, f, c, coef, batch, ld, f_t, weight, algo, var, dim, thr, (cudaStream_t)stream);
 }
 
 int dwt_interpolate_host(dwt_plan_t P, const void* f, void* c, int batch, long long ld, dwt_dtype f_t,

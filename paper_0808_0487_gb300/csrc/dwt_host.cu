@@ -137,7 +137,7 @@ int run_interpolate_host(dwt_plan_s* P, const void* f_host, void* c_host, int ba
         DWT_CK(cudaEventRecord(H->ev_in[b], H->s_in));
         // transform on the caller's stream
         DWT_CK(cudaStreamWaitEvent(st, H->ev_in[b], 0));
-        rc = run_interpolate(P, H->f[b], H->c[b], nullptr, nf, P->N, f_t, weight, H->var + (size_t)f0 * nb2,
+        rc = run_interpolate(P, H->f[b], H->c[b], nullptr, nf, P->N, f_t, weight, DWT_ALGO_AUTO, H->var + (size_t)f0 * nb2,
                              H->dim + (size_t)f0 * 2, thr, st);
         if (rc) return rc;
         DWT_CK(cudaEventRecord(H->ev_done[b], st));

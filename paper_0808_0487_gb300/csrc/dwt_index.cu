@@ -596,7 +596,18 @@ static int coset_tables_small(dwt_plan_s* Pl, cudaStream_t st) {
     return DWT_OK;
 }
 
+int coset_tables_tree2(dwt_plan_s* Pl, cudaStream_t st, bool* used);
+
 int build_coset_tables(dwt_plan_s* Pl, cudaStream_t st) {
+    if (Pl->p == 2 && !(Pl->flags & DWT_PLAN_KEEP_INDEX_MAP)) {
+        if (host_rank(Pl) < Pl->m) {
+            set_error("rows of C_1..C_s span a space of dimension < m");
+            return DWT_ESPAN;
+        }
+        bool used = false;
+        const int rc = coset_tables_tree2(Pl, st, &used);
+        if (used || rc) return rc;
+    }
     const bool small = Pl->N <= kSmallDpMax;
     switch (Pl->p) {
         case 2: return small ? coset_tables_small<2>(Pl, st) : coset_tables_p<2>(Pl, st);

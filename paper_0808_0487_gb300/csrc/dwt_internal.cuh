@@ -104,9 +104,20 @@ const PassPlan& pass_plan(dwt_plan_s* P, int elem_bytes);
 int run_transform(dwt_plan_s* P, const void* in, void* out, int batch, long long ld_in, long long ld_out,
                   dwt_dtype in_t, dwt_dtype out_t, int sgn, cudaStream_t st);
 int run_interpolate(dwt_plan_s* P, const void* f, void* c, void* coef, int batch, long long ld, dwt_dtype f_t,
-                    dwt_weight weight, double* var, int* dim, double thr, cudaStream_t st);
+                    dwt_weight weight, dwt_algo algo, double* var, int* dim, double thr, cudaStream_t st);
 int run_effdim(dwt_plan_s* P, const void* coef, int batch, long long ld, dwt_dtype t, double* var, int* dim,
                double thr, cudaStream_t st);
+// tensor-core low pass (p = 2, low 14 digits): one job of ntiles tiles of
+// 2^14 elements, tpf per function, result times scale
+struct TcJob {
+    const float* in;
+    float* out;
+    long long ld_in, ld_out, tpf, ntiles;
+    float scale;
+};
+int launch_tc_lo14(const TcJob& a, const TcJob* b, int* err, const char* fam, cudaStream_t st);
+bool tc_ok(int m);
+int tc_check(int* err, cudaStream_t st);
 int run_interpolate_host(dwt_plan_s* P, const void* f_host, void* c_host, int batch, long long ld, dwt_dtype f_t,
                          dwt_weight weight, double* var_host, int* dim_host, double thr, cudaStream_t st);
 // releases the plan's dwt_interpolate_host resources: after synchronising

@@ -745,7 +745,7 @@ bool p2_interp_ok(int m, int s) {
 // fused top pass (c -> c), inverse low pass (c -> c), per function so that c
 // stays in L2 between the passes
 int p2_interpolate(dwt_plan_s* Pl, const float* f, float* c, float* coef, int batch, long long ld, const float* W,
-                   double** part_out, long long* ntile_out, cudaStream_t st) {
+                   bool tc, double** part_out, long long* ntile_out, cudaStream_t st) {
     const int m = Pl->m;
     const long long N = Pl->N;
     constexpr int LT = kFusedLT;
@@ -764,14 +764,34 @@ int p2_interpolate(dwt_plan_s* Pl, const float* f, float* c, float* coef, int ba
     const long long fbytes = N * 4;
     int G = (int)std::max(1ll, kL2GroupP2 / fbytes);
     G = std::min(G, 65535);
+    // low passes: FP32 register tiles, or (tc) the split-BF16 tensor-core tiles
+    int* err = nullptr;
+    if (tc) {
+        if (L != 14 || !tc_ok(m)) {
+            set_error("the tensor-core interpolation covers 18 <= m <= 24");
+            return DWT_EUNSUPPORTED;
+        }
+        if ((rc = dmalloc((void**)&err, sizeof(int), st))) return rc;
+        DWT_CK(cudaMemsetAsync(err, 0, sizeof(int), st));
+    }
+    const long long tpf = N >> 14;
+    // job a (n0 functions) and optionally job b; a is the inverse pass of the
+    // final results when inv0 (stored with evict-first)
+    auto low = [&](const float* i0, float* o0, int n0, bool inv0, const float* i1, float* o1, int n1,
+                   const char* fam) {
+        if (tc) {
+            TcJob a{i0, o0, ld, ld, tpf, tpf * n0, 1.f};
+            TcJob b{i1, o1, ld, ld, tpf, tpf * n1, 1.f};
+            return launch_tc_lo14(a, i1 ? &b : nullptr, err, fam, st);
+        }
+        LoJob<float> a{i0, o0, ld, ld, n0, 1.f, 0, inv0 ? 1 : 0};
+        LoJob<float> b{i1, o1, ld, ld, n1, 1.f, 0, 0};
+        return launch_lo2<float>(L, a, i1 ? &b : nullptr, N, fam, st);
+    };
     // forward low pass of the first group; then per group: fused top pass, and one
     // launch holding this group's inverse low pass and the next group's forward
-    {
-        const int nf0 = std::min(G, batch);
-        LoJob<float> fw{f, c, ld, ld, nf0, 1.f, 0, 0};
-        rc = launch_lo2<float>(L, fw, nullptr, N, "interp_fwd", st);
-        if (rc) return rc;
-    }
+    rc = low(f, c, std::min(G, batch), false, nullptr, nullptr, 0, "interp_fwd");
+    if (rc) return rc;
     for (int f0 = 0; f0 < batch; f0 += G) {
         const int nf = std::min(G, batch - f0);
         const long long off = (long long)f0 * ld;
@@ -793,18 +813,16 @@ int p2_interpolate(dwt_plan_s* Pl, const float* f, float* c, float* coef, int ba
         rc = coef ? launch_hi_t<float, LT, true, true>(B, a, nf, bins_bytes, "interp_top", st)
                   : launch_hi_t<float, LT, true, false>(B, a, nf, bins_bytes, "interp_top", st);
         if (rc) return rc;
-        LoJob<float> inv{c + off, c + off, ld, ld, nf, 1.f, 0, 1};
         const int g1 = f0 + G;
         if (g1 < batch) {
-            const int nf1 = std::min(G, batch - g1);
             const long long off1 = (long long)g1 * ld;
-            LoJob<float> fw{f + off1, c + off1, ld, ld, nf1, 1.f, 0, 0};
-            rc = launch_lo2<float>(L, inv, &fw, N, "interp_inv_fwd", st);
+            rc = low(c + off, c + off, nf, true, f + off1, c + off1, std::min(G, batch - g1), "interp_inv_fwd");
         } else {
-            rc = launch_lo2<float>(L, inv, nullptr, N, "interp_inv", st);
+            rc = low(c + off, c + off, nf, true, nullptr, nullptr, 0, "interp_inv");
         }
         if (rc) return rc;
     }
+    if (tc && (rc = tc_check(err, st))) return rc;
     *part_out = part;
     *ntile_out = ntile;
     return DWT_OK;

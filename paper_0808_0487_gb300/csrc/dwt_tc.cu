@@ -13,13 +13,16 @@
 // tensor memory, which keeps about 16 bits of the mantissa (relative error of
 // the split <= 2^-17 per element and round).
 //
-// Per CTA (4 warps, one tile at a time): H_128 stays in shared memory as a
-// K-major 128B-swizzled BF16 operand; X_hi / X_lo are written there by the
-// threads; one elected thread issues tcgen05.mma (M = N = 128, K = 16 per
-// instruction) into a 256-column TMEM allocation (D1 at column 0, D2 at 128);
-// completion is signalled through an mbarrier; the warps read their 32 lanes
-// of the accumulator with tcgen05.ld.  Every mbarrier wait is bounded: past the
-// limit the kernel records an error and leaves, freeing its TMEM.
+// Per CTA (4 warps, persistent over tiles, two CTAs per SM): H_128 stays in
+// shared memory as a K-major 128B-swizzled BF16 operand, built once; X_hi /
+// X_lo are written there by the threads; one elected thread issues tcgen05.mma
+// (M = N = 128, K = 16 per instruction) into a 256-column TMEM allocation.
+// Round 1 takes both operands from shared memory; its result D1 is read back
+// (each thread one lane = one row), split, and written into tensor memory as
+// the A operand of round 2, so the second product reads only H from shared
+// memory.  The next tile is staged while round 2 runs.  Completion is
+// signalled through an mbarrier; every wait is bounded: past the limit the
+// kernel records an error and leaves, freeing its TMEM.
 #include <cuda_bf16.h>
 #include <stdint.h>
 
@@ -105,6 +108,38 @@ __device__ __forceinline__ void split_bf16(float x, unsigned short& hi, unsigned
     lo = __bfloat16_as_ushort(l);
 }
 
+// the same split for two values packed as one 32-bit column (element 2i in the
+// low half): hi and lo words
+__device__ __forceinline__ void split2(float a, float b, uint32_t& hi, uint32_t& lo) {
+    unsigned short ha, la, hb, lb;
+    split_bf16(a, ha, la);
+    split_bf16(b, hb, lb);
+    hi = ha | ((uint32_t)hb << 16);
+    lo = la | ((uint32_t)lb << 16);
+}
+
+__device__ __forceinline__ void tmem_st16(uint32_t taddr, const uint32_t* r) {
+    asm volatile(
+        "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16};" ::"r"(
+            taddr),
+        "r"(r[0]), "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]), "r"(r[7]), "r"(r[8]), "r"(r[9]),
+        "r"(r[10]), "r"(r[11]), "r"(r[12]), "r"(r[13]), "r"(r[14]), "r"(r[15])
+        : "memory");
+}
+
+// A operand from tensor memory (M = 128 rows on the lanes, K packed two BF16 per column)
+__device__ __forceinline__ void mma_bf16_ta(uint32_t dt, uint32_t at, uint64_t bd, uint32_t idesc, int acc) {
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+        " tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %3, p;\n}\n" ::"r"(dt),
+        "r"(at), "l"(bd), "r"(idesc), "r"(acc)
+        : "memory");
+}
+
+__device__ __forceinline__ void prefetch_l2_tc(const void* p, unsigned bytes) {
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
+}
+
 // shared-memory plan of the CTA (bytes, 1024-aligned operand blocks)
 constexpr int kOpBytes = 128 * 128 * 2;   // one 128 x 128 BF16 operand (two 64-wide K blocks)
 constexpr int kSmemH = 0;
@@ -112,20 +147,54 @@ constexpr int kSmemXhi = kOpBytes;
 constexpr int kSmemXlo = 2 * kOpBytes;
 constexpr int kSmemBar = 3 * kOpBytes;     // mbarrier (8 B) + TMEM address (4 B)
 constexpr int kSmemTotal = 3 * kOpBytes + 64 + 1024;   // + slack to align the base to 1024
+// tensor-memory plan (256 columns per CTA): accumulator D1 / D2, round-2 A operand hi / lo
+constexpr uint32_t kTmD = 0, kTmPhi = 128, kTmPlo = 192;
 
 // element (row, k) of a 128-row, 128-wide operand = two 64-wide swizzled blocks
 __device__ __forceinline__ uint32_t op_off(int row, int k) { return (uint32_t)((k >> 6) * (128 * 128)) + sw128(row, k & 63); }
 
+constexpr int kTcThreads = 256;   // two warps per 32-lane quarter of tensor memory
+
+// X (tile elements k + 128 n as rows n) -> hi / lo operands in shared memory;
+// all 16 loads of a thread are issued before the first split
+__device__ __forceinline__ void stage_x(unsigned char* sm, const float* src, int t) {
+    float4 x4[16];
+#pragma unroll
+    for (int q = 0; q < 16; ++q) x4[q] = __ldcs(reinterpret_cast<const float4*>(src + 4 * (t + kTcThreads * q)));
+#pragma unroll
+    for (int q = 0; q < 16; ++q) {
+        const int e = 4 * (t + kTcThreads * q);
+        const float4 x = x4[q];
+        uint32_t h01, l01, h23, l23;
+        split2(x.x, x.y, h01, l01);
+        split2(x.z, x.w, h23, l23);
+        const uint32_t o = op_off(e >> 7, e & 127);   // 4 consecutive k stay inside one 16-byte chunk
+        *reinterpret_cast<uint2*>(sm + kSmemXhi + o) = make_uint2(h01, h23);
+        *reinterpret_cast<uint2*>(sm + kSmemXlo + o) = make_uint2(l01, l23);
+    }
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
 // Transform of the low 14 digits of every 2^14-element tile of each function.
-// grid: (tiles, functions); 128 threads.  scale multiplies the result.
-__global__ void __launch_bounds__(128, 1) k_tc_lo14(const float* in, float* out, long long ld_in, long long ld_out,
-                                                    float scale, int* err) {
+// Persistent: CTA b takes tiles b, b + gridDim.x, ... of the nf x tpf tiles
+// (two CTAs per SM, 256 threads each; warps w and w + 4 share the 32 lanes
+// 32 (w mod 4) of tensor memory and take one half of the columns each).  Per tile:
+//   round 1: D1 = H X^T, A = H and B = X_hi, X_lo from shared memory;
+//   the threads read D1 (lane h = row h), split it and store the BF16 halves
+//   into tensor memory as the A operand of
+//   round 2: D2 = P H^T, A = P_hi, P_lo from tensor memory, B = H;
+// while round 2 runs the threads stage the next tile's X; then they read D2
+// and store it.  scale multiplies the result.
+__global__ void __launch_bounds__(kTcThreads, 2) k_tc_lo14(TcJob j0, TcJob j1, int* err) {
+    const long long ntiles = j0.ntiles + j1.ntiles;
     extern __shared__ __align__(1024) unsigned char smraw_unaligned[];
     unsigned char* sm = reinterpret_cast<unsigned char*>(((uintptr_t)smraw_unaligned + 1023) & ~(uintptr_t)1023);
     const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
     const uint32_t s_base = (uint32_t)__cvta_generic_to_shared(sm);
     uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(sm + kSmemBar + 8);
     const uint32_t bar_addr = s_base + kSmemBar;
+    long long tile = blockIdx.x;
+    if (tile >= ntiles) return;
 
     if (warp == 0) {
         const uint32_t slot = s_base + kSmemBar + 8;
@@ -136,116 +205,146 @@ __global__ void __launch_bounds__(128, 1) k_tc_lo14(const float* in, float* out,
         asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar_addr) : "memory");
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
-    // H_128 (symmetric, entries (-1)^popcount(i & j)) as the K-major operand
-    for (int idx = t; idx < 128 * 128; idx += 128) {
-        const int i = idx >> 7, j = idx & 127;
-        const unsigned short v = (__popc(i & j) & 1) ? 0xBF80u : 0x3F80u;   // -1.0 / +1.0 in BF16
-        *reinterpret_cast<unsigned short*>(sm + kSmemH + op_off(i, j)) = v;
+    // H_128 (symmetric, entries (-1)^popcount(i & j)) as a K-major operand, once per CTA
+    for (int idx = t; idx < 128 * 16; idx += kTcThreads) {
+        const int i = idx >> 4, j0 = (idx & 15) * 8;   // 8 consecutive k = one 16-byte chunk
+        uint32_t w[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const uint32_t a = (__popc(i & (j0 + 2 * u)) & 1) ? 0xBF80u : 0x3F80u;
+            const uint32_t b = (__popc(i & (j0 + 2 * u + 1)) & 1) ? 0xBF80u : 0x3F80u;
+            w[u] = a | (b << 16);
+        }
+        *reinterpret_cast<uint4*>(sm + kSmemH + op_off(i, j0)) = make_uint4(w[0], w[1], w[2], w[3]);
     }
-    // the tile: X[n][k] = element k + 128 n, split into hi / lo operands
-    const float* src = in + blockIdx.y * ld_in + ((long long)blockIdx.x << 14);
-    float* dst = out + blockIdx.y * ld_out + ((long long)blockIdx.x << 14);
-#pragma unroll 4
-    for (int q = 0; q < 32; ++q) {
-        const int e = 4 * (t + 128 * q);
-        const float4 x = __ldcs(reinterpret_cast<const float4*>(src + e));
-        const int n = e >> 7, k = e & 127;
-        unsigned short h0, h1, h2, h3, l0, l1, l2, l3;
-        split_bf16(x.x, h0, l0);
-        split_bf16(x.y, h1, l1);
-        split_bf16(x.z, h2, l2);
-        split_bf16(x.w, h3, l3);
-        const uint32_t o = op_off(n, k);   // 4 consecutive k stay inside one 16-byte chunk
-        *reinterpret_cast<uint2*>(sm + kSmemXhi + o) = make_uint2(h0 | ((uint32_t)h1 << 16), h2 | ((uint32_t)h3 << 16));
-        *reinterpret_cast<uint2*>(sm + kSmemXlo + o) = make_uint2(l0 | ((uint32_t)l1 << 16), l2 | ((uint32_t)l3 << 16));
-    }
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    auto src_of = [&](long long i) {
+        const TcJob& j = i < j0.ntiles ? j0 : j1;
+        const long long k = i < j0.ntiles ? i : i - j0.ntiles;
+        return j.in + (k / j.tpf) * j.ld_in + ((k % j.tpf) << 14);
+    };
+    // this CTA's first kPre tiles start moving into L2 at once; each iteration
+    // then asks for the tile kPre steps ahead
+    constexpr int kPre = 2;
+    if (t == 0)
+        for (int i = 1; i < kPre; ++i)
+            if (tile + (long long)i * gridDim.x < ntiles) prefetch_l2_tc(src_of(tile + (long long)i * gridDim.x), 1u << 16);
+    stage_x(sm, src_of(tile), t);
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const uint32_t tmem = *tmem_slot;
     constexpr uint32_t ID = idesc_bf16(128, 128);
+    const int h = 32 * (warp & 3) + lane, half = warp >> 2;
+    const uint32_t lane_base = tmem + ((uint32_t)(32 * (warp & 3)) << 16);
+    uint32_t phase = 0;
     bool ok = true;
 
-    // round 1: D1 = H * X^T over k (8 K-steps of 16), hi then lo
-    if (t == 0) {
-        for (int part = 0; part < 2; ++part) {
-            const uint32_t xb = s_base + (part ? kSmemXlo : kSmemXhi);
-            for (int ks = 0; ks < 8; ++ks) {
-                const uint32_t koff = (uint32_t)((ks >> 2) * (128 * 128) + (ks & 3) * 32);
-                mma_bf16(tmem, desc_sw128(s_base + kSmemH + koff), desc_sw128(xb + koff), ID, part | ks);
-            }
-        }
-        mma_commit(bar_addr);
-    }
-    ok = __syncthreads_and(mbar_wait(bar_addr, 0) ? 1 : 0) != 0;
-    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    // D1 row h = 32 warp + lane -> round-2 operand A[h][n] (K-major), hi / lo
-    const int h = 32 * warp + lane;
-    const uint32_t lane_base = tmem + ((uint32_t)(32 * warp) << 16);
-    if (ok) {
-#pragma unroll 1
-        for (int c = 0; c < 4; ++c) {
-            float v[32];
-            tmem_ld32(lane_base + 32 * c, v);
-#pragma unroll
-            for (int g = 0; g < 4; ++g) {   // 8 values = one 16-byte chunk
-                uint32_t hw[4], lw[4];
-#pragma unroll
-                for (int u = 0; u < 4; ++u) {
-                    unsigned short a0, a1, b0, b1;
-                    split_bf16(v[8 * g + 2 * u], a0, b0);
-                    split_bf16(v[8 * g + 2 * u + 1], a1, b1);
-                    hw[u] = a0 | ((uint32_t)a1 << 16);
-                    lw[u] = b0 | ((uint32_t)b1 << 16);
+    for (; tile < ntiles; tile += gridDim.x) {
+        const long long next = tile + gridDim.x;
+        if (t == 0 && tile + (long long)kPre * gridDim.x < ntiles)
+            prefetch_l2_tc(src_of(tile + (long long)kPre * gridDim.x), 1u << 16);
+        // round 1 (X staged and fenced by every thread before the barrier above)
+        if (t == 0) {
+            for (int part = 0; part < 2; ++part) {
+                const uint32_t xb = s_base + (part ? kSmemXlo : kSmemXhi);
+                for (int ks = 0; ks < 8; ++ks) {
+                    const uint32_t koff = (uint32_t)((ks >> 2) * (128 * 128) + (ks & 3) * 32);
+                    mma_bf16(tmem + kTmD, desc_sw128(s_base + kSmemH + koff), desc_sw128(xb + koff), ID, part | ks);
                 }
-                const uint32_t o = op_off(h, 32 * c + 8 * g);
-                *reinterpret_cast<uint4*>(sm + kSmemXhi + o) = make_uint4(hw[0], hw[1], hw[2], hw[3]);
-                *reinterpret_cast<uint4*>(sm + kSmemXlo + o) = make_uint4(lw[0], lw[1], lw[2], lw[3]);
             }
+            mma_commit(bar_addr);
         }
-    }
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-    __syncthreads();
-    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    // round 2: D2 = D1 * H over n, into TMEM columns 128..255
-    if (t == 0 && ok) {
-        for (int part = 0; part < 2; ++part) {
-            const uint32_t ab = s_base + (part ? kSmemXlo : kSmemXhi);
-            for (int ks = 0; ks < 8; ++ks) {
-                const uint32_t koff = (uint32_t)((ks >> 2) * (128 * 128) + (ks & 3) * 32);
-                mma_bf16(tmem + 128, desc_sw128(ab + koff), desc_sw128(s_base + kSmemH + koff), ID, part | ks);
-            }
-        }
-        mma_commit(bar_addr);
-    }
-    if (ok) ok = __syncthreads_and(mbar_wait(bar_addr, 1) ? 1 : 0) != 0;
-    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    if (ok) {
-        // D2[h][h'] -> out[h + 128 h']: lanes write consecutive h
+        ok = __syncthreads_and(mbar_wait(bar_addr, phase) ? 1 : 0) != 0;
+        phase ^= 1;
+        if (!ok) break;
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        // D1 row h, this warp's half of the columns -> P_hi / P_lo (two BF16 per
+        // column, element 2i low)
 #pragma unroll 1
-        for (int c = 0; c < 4; ++c) {
+        for (int c = 2 * half; c < 2 * half + 2; ++c) {
             float v[32];
-            tmem_ld32(lane_base + 128 + 32 * c, v);
+            tmem_ld32(lane_base + kTmD + 32 * c, v);
+            uint32_t hw[16], lw[16];
+#pragma unroll
+            for (int i = 0; i < 16; ++i) split2(v[2 * i], v[2 * i + 1], hw[i], lw[i]);
+            tmem_st16(lane_base + kTmPhi + 16 * c, hw);
+            tmem_st16(lane_base + kTmPlo + 16 * c, lw);
+        }
+        asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+        __syncthreads();
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        // round 2: D2 = P H^T over n, into the accumulator columns
+        if (t == 0) {
+            for (int part = 0; part < 2; ++part) {
+                const uint32_t pa = tmem + (part ? kTmPlo : kTmPhi);
+                for (int ks = 0; ks < 8; ++ks) {
+                    const uint32_t koff = (uint32_t)((ks >> 2) * (128 * 128) + (ks & 3) * 32);
+                    mma_bf16_ta(tmem + kTmD, pa + 8 * ks, desc_sw128(s_base + kSmemH + koff), ID, part | ks);
+                }
+            }
+            mma_commit(bar_addr);
+        }
+        // the next tile's X while round 2 runs (round 1 has finished reading X)
+        if (next < ntiles) stage_x(sm, src_of(next), t);
+        ok = __syncthreads_and(mbar_wait(bar_addr, phase) ? 1 : 0) != 0;
+        phase ^= 1;
+        if (!ok) break;
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        // D2[h][h'] -> out[h + 128 h']: lanes write consecutive h
+        const bool second = tile >= j0.ntiles;
+        const TcJob& jb = second ? j1 : j0;
+        const long long k = second ? tile - j0.ntiles : tile;
+        float* dst = jb.out + (k / jb.tpf) * jb.ld_out + ((k % jb.tpf) << 14);
+        const float scale = jb.scale;
+#pragma unroll 1
+        for (int c = 2 * half; c < 2 * half + 2; ++c) {
+            float v[32];
+            tmem_ld32(lane_base + kTmD + 32 * c, v);
 #pragma unroll
             for (int i = 0; i < 32; ++i) __stcg(dst + h + 128 * (32 * c + i), v[i] * scale);
         }
-    } else if (t == 0) {
-        atomicExch(err, 1);
+        // accumulator read out and next X staged before the next round 1
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+        __syncthreads();
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     }
+    if (!ok && t == 0) atomicExch(err, 1);
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
     if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 256;" ::"r"(tmem) : "memory");
 }
 
+// Tensor-core low pass over one job, or two independent jobs in one launch
+// (the first job's tiles first); err is the bounded-wait error flag.
+int launch_tc_lo14(const TcJob& a, const TcJob* b, int* err, const char* fam, cudaStream_t st) {
+    auto kern = k_tc_lo14;
+    int rc = smem_limit_max(kern);
+    if (rc) return rc;
+    int dev = 0, nsm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    TcJob jb{};
+    if (b) jb = *b;
+    const long long ntiles = a.ntiles + jb.ntiles;
+    if (ntiles == 0) return DWT_OK;
+    const unsigned grid = (unsigned)std::min<long long>(ntiles, 2ll * std::max(nsm, 1));
+    {
+        LaunchScope ls(fam, st);
+        kern<<<grid, kTcThreads, kSmemTotal, st>>>(a, jb, err);
+    }
+    DWT_CK_LAUNCH("k_tc_lo14");
+    return DWT_OK;
+}
+
 // dwt_forward / dwt_inverse with DWT_ALGO_TC_SPLIT_BF16 for p = 2, FP32:
 // the low 14 digits on the tensor cores; the digits above (m - 14 in 4..10)
-// with the FP32 high pass.
+// with the FP32 high pass, per group of functions whose data fits in L2 (about
+// 48 MB), so that the high pass reads what the tensor-core pass has just written.
 int run_tc_transform(dwt_plan_s* Pl, const float* in, float* out, int batch, long long ld_in, long long ld_out,
                      int sgn, cudaStream_t st) {
     const int m = Pl->m;
-    if (m < 14 || (m > 14 && (m - 14 < 4 || m - 14 > 10))) {
+    if (!tc_ok(m)) {
         set_error("the tensor-core form covers m = 14 and 18 <= m <= 24");
         return DWT_EUNSUPPORTED;
     }
@@ -256,25 +355,25 @@ int run_tc_transform(dwt_plan_s* Pl, const float* in, float* out, int batch, lon
     int* err = nullptr;
     int rc = dmalloc((void**)&err, sizeof(int), st);
     if (rc) return rc;
-    cudaMemsetAsync(err, 0, sizeof(int), st);
-    auto kern = k_tc_lo14;
-    rc = smem_limit_max(kern);
-    if (rc) return rc;
-    const long long N = Pl->N;
+    DWT_CK(cudaMemsetAsync(err, 0, sizeof(int), st));
+    const long long N = Pl->N, tpf = N >> 14;
     const float scale = (sgn < 0 && m == 14) ? (float)(1.0 / (double)N) : 1.f;
-    for (int f0 = 0; f0 < batch; f0 += 65535) {
-        const int nf = std::min(65535, batch - f0);
-        {
-            LaunchScope ls("tc_lo14", st);
-            kern<<<dim3((unsigned)(N >> 14), (unsigned)nf), 128, kSmemTotal, st>>>(
-                in + (long long)f0 * ld_in, out + (long long)f0 * ld_out, ld_in, ld_out, scale, err);
-        }
-        DWT_CK_LAUNCH("k_tc_lo14");
-        if (m > 14) {
-            rc = p2_hi_only(Pl, out + (long long)f0 * ld_out, nf, ld_out, 14, sgn, st);
-            if (rc) return rc;
-        }
+    const int G = (int)std::max(1ll, std::min(65535ll, (48ll << 20) / (N * 4)));
+    for (int f0 = 0; f0 < batch && !rc; f0 += G) {
+        const int nf = std::min(G, batch - f0);
+        TcJob a{in + (long long)f0 * ld_in, out + (long long)f0 * ld_out, ld_in, ld_out, tpf, tpf * nf, scale};
+        rc = launch_tc_lo14(a, nullptr, err, "tc_lo14", st);
+        if (!rc && m > 14) rc = p2_hi_only(Pl, out + (long long)f0 * ld_out, nf, ld_out, 14, sgn, st);
     }
+    if (!rc) rc = tc_check(err, st);
+    else dfree(err, st);
+    return rc;
+}
+
+bool tc_ok(int m) { return m == 14 || (m >= 18 && m <= 24); }
+
+// reads and releases the error flag of the tensor-core passes queued on st
+int tc_check(int* err, cudaStream_t st) {
     int herr = 0;
     DWT_CK(cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, st));
     DWT_CK(cudaStreamSynchronize(st));

@@ -22,7 +22,7 @@ bool p2_interp_ok(int m, int s);
 int p2_transform(dwt_plan_s* Pl, const void* in, void* out, int batch, long long ld_in, long long ld_out,
                  dwt_dtype t, int sgn, cudaStream_t st);
 int p2_interpolate(dwt_plan_s* Pl, const float* f, float* c, float* coef, int batch, long long ld, const float* W,
-                   double** part_out, long long* ntile_out, cudaStream_t st);
+                   bool tc, double** part_out, long long* ntile_out, cudaStream_t st);
 
 static bool aligned16(const void* p, long long ld, int elem) {
     return ((uintptr_t)p & 15) == 0 && ((ld * elem) & 15) == 0;
@@ -628,12 +628,18 @@ static int interpolate_t(dwt_plan_s* Pl, const void* f, void* c, void* coef, int
 }
 
 int run_interpolate(dwt_plan_s* Pl, const void* f, void* c, void* coef, int batch, long long ld, dwt_dtype f_t,
-                    dwt_weight weight, double* var, int* dim, double thr, cudaStream_t st) {
-    if (Pl->p == 2 && p2_interp_ok(Pl->m, Pl->s) && aligned16(f, ld, 4) && aligned16(c, ld, 4)) {
+                    dwt_weight weight, dwt_algo algo, double* var, int* dim, double thr, cudaStream_t st) {
+    const bool fast = Pl->p == 2 && p2_interp_ok(Pl->m, Pl->s) && aligned16(f, ld, 4) && aligned16(c, ld, 4);
+    if (algo == DWT_ALGO_TC_SPLIT_BF16 && !(fast && Pl->m >= 18)) {
+        set_error("the tensor-core interpolation needs p = 2, 18 <= m <= 24 and 16-byte aligned rows");
+        return DWT_EUNSUPPORTED;
+    }
+    if (fast) {
         double* part = nullptr;
         long long ntile = 0;
         int rc = p2_interpolate(Pl, (const float*)f, (float*)c, (float*)coef, batch, ld,
-                                weight == DWT_WEIGHT_INV_SQ_WAVENUMBER ? Pl->d_W : nullptr, &part, &ntile, st);
+                                weight == DWT_WEIGHT_INV_SQ_WAVENUMBER ? Pl->d_W : nullptr,
+                                algo == DWT_ALGO_TC_SPLIT_BF16, &part, &ntile, st);
         if (rc) return rc;
         return finalize(Pl, part, ntile, batch, thr, var, dim, st);
     }
