@@ -159,6 +159,12 @@ int dwt_inverse(dwt_plan_t plan, const void *in, void *out, int batch, long long
  *   var: optional device double [batch][2][s+1], or NULL;
  *   dim: optional device int [batch][2], or NULL;
  *   threshold: in (0, 1], 0.99 in the paper.
+ *   algo: DWT_ALGO_AUTO / DWT_ALGO_BUTTERFLY (FP32 stages), or
+ *      DWT_ALGO_TC_SPLIT_BF16 for p = 2, 18 <= m <= 24 and 16-byte aligned
+ *      rows: the low 14 digits of both transforms on the tensor cores (error
+ *      relative to the norm of f about 4e-6); this form checks its bounded
+ *      device waits before returning, so the call synchronises `stream`
+ *      (DWT_ETIMEOUT if a wait expired), DWT_EUNSUPPORTED for other shapes.
  * Variance sums use per-lane FP32 partials inside a tile, then FP64 in a
  * fixed order, so results do not depend on scheduling.  Needs plan tables
  * (DWT_ESPAN / DWT_EUNSUPPORTED otherwise).
