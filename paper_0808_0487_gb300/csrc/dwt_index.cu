@@ -597,15 +597,18 @@ static int coset_tables_small(dwt_plan_s* Pl, cudaStream_t st) {
 }
 
 int coset_tables_tree2(dwt_plan_s* Pl, cudaStream_t st, bool* used);
+int coset_tables_treep(dwt_plan_s* Pl, cudaStream_t st, bool* used);
 
 int build_coset_tables(dwt_plan_s* Pl, cudaStream_t st) {
-    if (Pl->p == 2 && !(Pl->flags & DWT_PLAN_KEEP_INDEX_MAP)) {
+    // the min-tree form (O(s N)) when every coordinate's rows are a basis; the
+    // per-digit programme otherwise, and when the index maps are kept
+    if (!(Pl->flags & DWT_PLAN_KEEP_INDEX_MAP)) {
         if (host_rank(Pl) < Pl->m) {
             set_error("rows of C_1..C_s span a space of dimension < m");
             return DWT_ESPAN;
         }
         bool used = false;
-        const int rc = coset_tables_tree2(Pl, st, &used);
+        const int rc = Pl->p == 2 ? coset_tables_tree2(Pl, st, &used) : coset_tables_treep(Pl, st, &used);
         if (used || rc) return rc;
     }
     const bool small = Pl->N <= kSmallDpMax;

@@ -136,3 +136,43 @@ def test_tables_small_large_boundary(dwt, dev, orc, p, m, s):
     k = torch.empty((300, s), dtype=torch.int32, device=dev)
     dwt.dwt_index_to_wavenumber(plan, torch.tensor(sel.view(np.int32), device=dev), k, 300)
     assert np.array_equal(k.cpu().numpy().view(np.uint32), ref["ksel"])
+
+
+# Plans without DWT_PLAN_KEEP_INDEX_MAP build K(C) with the min-tree form when
+# every C_j is nonsingular (one bottom-up and one top-down tree sweep per
+# coordinate, tiles of 2^13, 3^8, 5^5, 7^4 labels plus a coarse tree above
+# them); the tables must equal the oracle's bit for bit, on one tile, several
+# tiles, and with a coarse tree of several levels.
+@pytest.mark.parametrize("p,m,s", [(2, 9, 4), (2, 13, 9), (2, 14, 3), (2, 17, 20), (3, 8, 5), (3, 11, 9),
+                                   (3, 13, 3), (5, 5, 7), (5, 9, 3), (7, 4, 6), (7, 6, 10)])
+def test_tables_tree_form(dwt, dev, orc, p, m, s):
+    C = S.small_net(p, m, s, index=100 + m + s)
+    N = p ** m
+    dwt.dwt_profile_reset()
+    dwt.dwt_profile_enable(True)
+    plan = dwt.dwt_plan_create(p, m, s, C)
+    dwt.dwt_profile_enable(False)
+    n_up, _ = dwt.dwt_profile_query("tree_up")
+    dwt.dwt_profile_reset()
+    assert plan.status == 0
+    assert n_up == 2 * s   # the tree form ran (once per coordinate and sweep)
+    W, cls = _read_tables(dwt, plan, N)
+    ref = orc.coset_leaders_dp(p, m, C, want_W64=False)
+    assert ref["status"] == 0
+    assert np.array_equal(W.view(np.uint32), ref["W32"].view(np.uint32))
+    assert np.array_equal(cls, ref["cls"])
+
+
+def test_tables_tree_form_dense_fallback(dwt, dev, orc):
+    """A net with a singular C_j (rank of all rows still m) takes the per-digit
+    programme; tables still bit-exact."""
+    p, m, s = 2, 10, 3
+    C = S.small_net(p, m, s, index=7).copy()
+    C[1, 4, :] = C[1, 3, :]   # two equal rows: C_2 singular
+    N = p ** m
+    plan = dwt.dwt_plan_create(p, m, s, C)
+    assert plan.status == 0
+    W, cls = _read_tables(dwt, plan, N)
+    ref = orc.coset_leaders_dp(p, m, C, want_W64=False)
+    assert np.array_equal(W.view(np.uint32), ref["W32"].view(np.uint32))
+    assert np.array_equal(cls, ref["cls"])
