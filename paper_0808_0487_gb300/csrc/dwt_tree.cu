@@ -235,6 +235,136 @@ __global__ void k_tree_weights(const unsigned long long* __restrict__ Pden, floa
         W[H] = __fdiv_rn(1.0f, __ull2float_rn(Pden[H]));
 }
 
+// The whole construction for a net of N = 2^m <= 2^13 labels in one CTA: both
+// sweeps over all coordinates with the tree, the previous coordinate's table
+// and the maps in shared memory, and each thread carrying the reading state of
+// its labels H = t + 1024 q in registers.  One launch per plan.
+constexpr int kOneMax = 1 << kLB;
+constexpr int kOneQ = kOneMax / 1024;
+
+__global__ void __launch_bounds__(1024, 1) k_tree_one(const Map4* __restrict__ Imaps, const Map4* __restrict__ Qmaps,
+                                                      const uint32_t* __restrict__ R, int m, int s, uint8_t* TU,
+                                                      uint8_t* DU, uint8_t* cls, float* W, unsigned* flags) {
+    extern __shared__ __align__(16) unsigned char sm[];
+    uint32_t (*mq)[256] = reinterpret_cast<uint32_t (*)[256]>(sm);               // Q_j
+    uint32_t (*mi)[256] = reinterpret_cast<uint32_t (*)[256]>(sm + 4096);        // I_j
+    const int N = 1 << m;
+    uint16_t* A0 = reinterpret_cast<uint16_t*>(sm + 8192);
+    uint16_t* A1 = A0 + N;
+    uint8_t* lv = reinterpret_cast<uint8_t*>(A1 + N);                             // 2N bytes of levels
+    uint8_t* Tp = lv + 2 * N;                                                     // T of coordinate j+1
+    uint32_t* r = reinterpret_cast<uint32_t*>(Tp + ((N + 15) & ~15));
+    const int t = threadIdx.x;
+    auto build_levels = [&](int j) {
+        // leaves T'[U] = T_{j+1}[U_{j+1}(h(U))] and the levels above them
+        for (int U = t; U < N; U += blockDim.x) lv[U] = j == s - 1 ? (U == 0 ? 0 : kInfB) : Tp[apply4(mq, U)];
+        __syncthreads();
+        for (int i = 1; i <= m; ++i) {
+            const int n = N >> i;
+            const uint8_t* src = lv + loff(N, i - 1);
+            uint8_t* dst = lv + loff(N, i);
+            for (int v = t; v < n; v += blockDim.x) dst[v] = min(src[2 * v], src[2 * v + 1]);
+            __syncthreads();
+        }
+    };
+    // backward sweep
+    for (int j = s - 1; j >= 0; --j) {
+        if (j < s - 1)
+            for (int i = t; i < 1024; i += blockDim.x) mq[i >> 8][i & 255] = Qmaps[j].t[i >> 8][i & 255];
+        __syncthreads();
+        build_levels(j);
+        uint16_t* cur = A0;
+        uint16_t* nxt = A1;
+        if (t == 0) cur[0] = kInfB;
+        __syncthreads();
+        for (int i = m - 1; i >= 0; --i) {
+            const int n = N >> i;
+            const uint8_t* S = lv + loff(N, i);
+            for (int v = t; v < n; v += blockDim.x) {
+                const uint16_t par = cur[v >> 1];
+                const unsigned c = sat_add(S[v ^ 1], (unsigned)(i + 1));
+                nxt[v] = c <= (unsigned)(par & 255) ? (uint16_t)(c | ((unsigned)(i + 1) << 8)) : par;
+            }
+            __syncthreads();
+            uint16_t* tmp = cur;
+            cur = nxt;
+            nxt = tmp;
+        }
+        for (int U = t; U < N; U += blockDim.x) {
+            const unsigned tv = lv[U], a = cur[U];
+            const bool keep = tv <= (a & 255);
+            const uint8_t val = keep ? (uint8_t)tv : (uint8_t)(a & 255);
+            TU[(size_t)j * N + U] = val;
+            DU[(size_t)j * N + U] = keep ? 0 : (uint8_t)(a >> 8);
+            Tp[U] = val;
+        }
+        __syncthreads();
+    }
+    // least total over every coset must stay below the saturation value
+    {
+        unsigned mx = 0;
+        for (int U = t; U < N; U += blockDim.x) mx = max(mx, (unsigned)Tp[U]);
+        for (int o = 16; o > 0; o >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+        if ((t & 31) == 0) atomicMax(flags, mx);
+        __syncthreads();
+        if (*(volatile unsigned*)flags >= kInfB) return;
+    }
+    // forward reading, labels H = t + 1024 q held by this thread
+    uint32_t g[kOneQ];
+    unsigned long long pd[kOneQ];
+    uint8_t ct[kOneQ], cs[kOneQ];
+#pragma unroll
+    for (int q = 0; q < kOneQ; ++q) {
+        g[q] = (uint32_t)(t + 1024 * q);
+        pd[q] = 1ull;
+        ct[q] = cs[q] = 0;
+    }
+    bool over = false;
+    for (int j = 0; j < s; ++j) {
+        __syncthreads();   // previous coordinate done with the maps and levels
+        for (int i = t; i < 1024; i += blockDim.x) {
+            mi[i >> 8][i & 255] = Imaps[j].t[i >> 8][i & 255];
+            if (j < s - 1) mq[i >> 8][i & 255] = Qmaps[j].t[i >> 8][i & 255];
+        }
+        if (t < m) r[t] = R[(size_t)j * m + t];
+        if (j < s - 1)
+            for (int U = t; U < N; U += blockDim.x) Tp[U] = TU[(size_t)(j + 1) * N + U];
+        __syncthreads();
+        build_levels(j);
+#pragma unroll
+        for (int q = 0; q < kOneQ; ++q) {
+            if (t + 1024 * q >= N) continue;
+            uint32_t U = apply4(mi, g[q]);
+            const int tau = TU[(size_t)j * N + U], d = DU[(size_t)j * N + U];
+            if (!d) continue;
+            uint32_t k = 1u << (d - 1);
+            U ^= k;
+            g[q] ^= r[d - 1];
+            for (int i = d - 2; i >= 0; --i) {
+                if ((int)lv[loff(N, i) + (U >> i)] + d != tau) {
+                    U ^= 1u << i;
+                    g[q] ^= r[i];
+                    k |= 1u << i;
+                }
+            }
+            const unsigned long long qq = (unsigned long long)k + 1ull, q2 = qq * qq;
+            if (__umul64hi(pd[q], q2) != 0ull) over = true;
+            pd[q] *= q2;
+            ct[q] = (uint8_t)(j + 1);
+            ++cs[q];
+        }
+    }
+#pragma unroll
+    for (int q = 0; q < kOneQ; ++q) {
+        const int H = t + 1024 * q;
+        if (H >= N) continue;
+        W[H] = __fdiv_rn(1.0f, __ull2float_rn(pd[q]));
+        cls[2 * H] = ct[q];
+        cls[2 * H + 1] = cs[q];
+    }
+    if (over) atomicExch(flags + 1, 1u);
+}
+
 // inverse of the F_2 matrix with columns c[0 .. m-1] (bit a of c[i] = row a):
 // ci[a] = B^{-1} e_a as a bit vector; false if singular
 bool gf2_inverse(const uint32_t* c, int m, uint32_t* ci) {
@@ -266,13 +396,13 @@ bool gf2_inverse(const uint32_t* c, int m, uint32_t* ci) {
 }
 
 void make_map(const uint32_t* cols, int m, Map4& M) {
-    for (int b = 0; b < 4; ++b)
-        for (int x = 0; x < 256; ++x) {
-            uint32_t v = 0;
-            for (int l = 0; l < 8; ++l)
-                if (((x >> l) & 1) && 8 * b + l < m) v ^= cols[8 * b + l];
-            M.t[b][x] = v;
+    for (int b = 0; b < 4; ++b) {
+        M.t[b][0] = 0;
+        for (int x = 1; x < 256; ++x) {   // x = (x with its lowest set bit cleared) + that bit
+            const int l = __builtin_ctz((unsigned)x);
+            M.t[b][x] = M.t[b][x & (x - 1)] ^ (8 * b + l < m ? cols[8 * b + l] : 0u);
         }
+    }
 }
 
 uint32_t host_apply(const Map4& M, uint32_t x) {
@@ -280,6 +410,52 @@ uint32_t host_apply(const Map4& M, uint32_t x) {
 }
 
 unsigned grid_n(long long n) { return (unsigned)std::max(1ll, std::min((n + 255) / 256, 8ll * 152)); }
+
+// the one-CTA form for N <= 2^13
+int tree_one(dwt_plan_s* Pl, const std::vector<Map4>& Imap, const std::vector<Map4>& Qmap, cudaStream_t st) {
+    const long long N = Pl->N;
+    const int m = Pl->m, s = Pl->s;
+    uint8_t *TU = nullptr, *DU = nullptr;
+    Map4* dmaps = nullptr;
+    unsigned* flags = nullptr;
+    auto cleanup = [&]() {
+        dfree(TU, st); dfree(DU, st); dfree(dmaps, st); dfree(flags, st);
+    };
+    if (dmalloc((void**)&TU, (size_t)s * N, st) || dmalloc((void**)&DU, (size_t)s * N, st) ||
+        dmalloc((void**)&dmaps, sizeof(Map4) * 2 * s, st) || dmalloc((void**)&flags, 8, st) ||
+        dmalloc((void**)&Pl->d_W, (size_t)N * 4, st) || dmalloc((void**)&Pl->d_cls, (size_t)N * 2, st)) {
+        cleanup();
+        return DWT_ENOMEM;
+    }
+    std::vector<Map4> hm(2 * s);
+    for (int j = 0; j < s; ++j) {
+        hm[j] = Imap[j];
+        hm[s + j] = Qmap[j];
+    }
+    DWT_CK(cudaMemcpyAsync(dmaps, hm.data(), sizeof(Map4) * 2 * s, cudaMemcpyHostToDevice, st));
+    DWT_CK(cudaMemsetAsync(flags, 0, 8, st));
+    const size_t smem = 8192 + (size_t)4 * N + 2 * N + ((N + 15) & ~15ll) + 32 * 4;
+    int rc = smem_limit_max(k_tree_one);
+    if (rc) { cleanup(); return rc; }
+    {
+        LaunchScope ls("tree_one", st);
+        k_tree_one<<<1, 1024, smem, st>>>(dmaps, dmaps + s, Pl->d_R, m, s, TU, DU, Pl->d_cls, Pl->d_W, flags);
+    }
+    DWT_CK_LAUNCH("k_tree_one");
+    unsigned hf[2] = {0, 0};
+    DWT_CK(cudaMemcpyAsync(hf, flags, 8, cudaMemcpyDeviceToHost, st));
+    DWT_CK(cudaStreamSynchronize(st));
+    cleanup();
+    if (hf[0] >= kInfB) {
+        set_error("a least nu over some coset reaches 255");
+        return DWT_EUNSUPPORTED;
+    }
+    if (hf[1]) {
+        set_error("a weight denominator prod (1+k_j)^2 exceeds 64 bits");
+        return DWT_EUNSUPPORTED;
+    }
+    return DWT_OK;
+}
 
 }  // namespace
 
@@ -307,6 +483,7 @@ int coset_tables_tree2(dwt_plan_s* Pl, cudaStream_t st, bool* used) {
         make_map(qc.data(), m, Qmap[j]);
     }
     *used = true;
+    if (m <= kLB) return tree_one(Pl, Imap, Qmap, st);
     const int LB = std::min(m, kLB);
     const long long nLB = N >> LB;
     uint8_t *TU = nullptr, *DU = nullptr, *lev = nullptr;

@@ -278,6 +278,158 @@ __global__ void __launch_bounds__(kThreadsP) k_treep_recon(uint32_t* G, unsigned
     }
 }
 
+// The whole construction for a net of N = p^m <= one tile in one CTA (see the
+// p = 2 form): maps, levels and the previous coordinate's table in shared
+// memory, the reading state of labels H = t + 1024 q in registers.
+template <int P>
+__global__ void __launch_bounds__(1024, 1) k_treep_one(const MapP* __restrict__ Imaps, const MapP* __restrict__ Fmaps,
+                                                       const MapP* __restrict__ Qmaps, int m, int s, int ng,
+                                                       uint8_t* TU, uint8_t* DU, uint8_t* cls, float* W,
+                                                       unsigned* flags) {
+    using SH = TreeShape<P>;
+    constexpr int QN = (SH::TS + 1023) / 1024;
+    extern __shared__ __align__(16) unsigned char sm[];
+    unsigned long long (*mq)[256] = reinterpret_cast<unsigned long long (*)[256]>(sm);
+    unsigned long long (*mi)[256] = reinterpret_cast<unsigned long long (*)[256]>(sm + sizeof(MapP));
+    unsigned long long (*mf)[256] = reinterpret_cast<unsigned long long (*)[256]>(sm + 2 * sizeof(MapP));
+    long long* off = reinterpret_cast<long long*>(sm + 3 * sizeof(MapP));          // [32]
+    uint32_t* pw = reinterpret_cast<uint32_t*>(off + 32);                          // [32]
+    int N = 1;
+    for (int i = 0; i < m; ++i) N *= P;
+    uint16_t* A0 = reinterpret_cast<uint16_t*>(pw + 32);
+    uint16_t* A1 = A0 + N;
+    uint8_t* lv = reinterpret_cast<uint8_t*>(A1 + N);
+    uint8_t* Tp = lv + 2 * N;
+    const int t = threadIdx.x;
+    if (t == 0) {
+        long long n = N;
+        uint32_t w = 1;
+        for (int i = 0; i <= m; ++i) {
+            off[i] = loffP<P>(N, n);
+            pw[i] = w;
+            n /= P;
+            w *= P;
+        }
+    }
+    auto load = [&](unsigned long long (*dst)[256], const MapP* src) {
+        for (int i = t; i < ng * 256; i += blockDim.x) dst[i >> 8][i & 255] = src->t[i >> 8][i & 255];
+    };
+    auto build_levels = [&](int j) {
+        for (int U = t; U < N; U += blockDim.x)
+            lv[U] = j == s - 1 ? (U == 0 ? 0 : kInfP) : Tp[applyP<P>(mq, (uint32_t)U, ng, m)];
+        __syncthreads();
+        for (int i = 1; i <= m; ++i) {
+            const int np = N / (int)pw[i];
+            const uint8_t* src = lv + off[i - 1];
+            uint8_t* dst = lv + off[i];
+            for (int v = t; v < np; v += blockDim.x) {
+                unsigned x = src[P * v];
+#pragma unroll
+                for (int c = 1; c < P; ++c) x = min(x, (unsigned)src[P * v + c]);
+                dst[v] = (uint8_t)x;
+            }
+            __syncthreads();
+        }
+    };
+    for (int j = s - 1; j >= 0; --j) {
+        if (j < s - 1) load(mq, Qmaps + j);
+        __syncthreads();
+        build_levels(j);
+        uint16_t* cur = A0;
+        uint16_t* nxt = A1;
+        if (t == 0) cur[0] = kInfP;
+        __syncthreads();
+        int n = 1;
+        for (int i = m - 1; i >= 0; --i) {
+            const int ni = n * P;
+            const uint8_t* S = lv + off[i];
+            for (int v = t; v < ni; v += blockDim.x) {
+                const uint16_t par = cur[v / P];
+                const unsigned c = sat_addP(sib_min<P>(S, v), (unsigned)(i + 1));
+                nxt[v] = c <= (unsigned)(par & 255) ? (uint16_t)(c | ((unsigned)(i + 1) << 8)) : par;
+            }
+            __syncthreads();
+            uint16_t* tmp = cur;
+            cur = nxt;
+            nxt = tmp;
+            n = ni;
+        }
+        for (int U = t; U < N; U += blockDim.x) {
+            const unsigned tv = lv[U], a = cur[U];
+            const bool keep = tv <= (a & 255);
+            const uint8_t val = keep ? (uint8_t)tv : (uint8_t)(a & 255);
+            TU[(size_t)j * N + U] = val;
+            DU[(size_t)j * N + U] = keep ? 0 : (uint8_t)(a >> 8);
+            Tp[U] = val;
+        }
+        __syncthreads();
+    }
+    {
+        unsigned mx = 0;
+        for (int U = t; U < N; U += blockDim.x) mx = max(mx, (unsigned)Tp[U]);
+        for (int o = 16; o > 0; o >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+        if ((t & 31) == 0) atomicMax(flags, mx);
+        __syncthreads();
+        if (*(volatile unsigned*)flags >= kInfP) return;
+    }
+    uint32_t g[QN];
+    unsigned long long pd[QN];
+    uint8_t ct[QN], cs[QN];
+#pragma unroll
+    for (int q = 0; q < QN; ++q) {
+        g[q] = (uint32_t)(t + 1024 * q);
+        pd[q] = 1ull;
+        ct[q] = cs[q] = 0;
+    }
+    bool over = false;
+    for (int j = 0; j < s; ++j) {
+        __syncthreads();
+        load(mi, Imaps + j);
+        load(mf, Fmaps + j);
+        if (j < s - 1) {
+            load(mq, Qmaps + j);
+            for (int U = t; U < N; U += blockDim.x) Tp[U] = TU[(size_t)(j + 1) * N + U];
+        }
+        __syncthreads();
+        build_levels(j);
+#pragma unroll
+        for (int q = 0; q < QN; ++q) {
+            if (t + 1024 * q >= N) continue;
+            uint32_t U = applyP<P>(mi, g[q], ng, m);
+            const int tau = TU[(size_t)j * N + U], d = DU[(size_t)j * N + U];
+            if (!d) continue;
+            uint32_t k = 0;
+            for (int i = d - 1; i >= 0; --i) {
+                const uint32_t u = (U / pw[i]) % P;
+                int a = i == d - 1 ? 1 : 0;
+                uint32_t Un = U;
+                for (; a < P; ++a) {
+                    Un = U - u * pw[i] + ((u + P - (uint32_t)a) % P) * pw[i];
+                    if ((int)lv[off[i] + Un / pw[i]] + d == tau) break;
+                }
+                if (a == P) a = P - 1;   // unreachable for a consistent table
+                U = Un;
+                k += (uint32_t)a * pw[i];
+            }
+            g[q] = applyP<P>(mf, U, ng, m);
+            const unsigned long long qq = (unsigned long long)k + 1ull, q2 = qq * qq;
+            if (__umul64hi(pd[q], q2) != 0ull) over = true;
+            pd[q] *= q2;
+            ct[q] = (uint8_t)(j + 1);
+            ++cs[q];
+        }
+    }
+#pragma unroll
+    for (int q = 0; q < QN; ++q) {
+        const int H = t + 1024 * q;
+        if (H >= N) continue;
+        W[H] = __fdiv_rn(1.0f, __ull2float_rn(pd[q]));
+        cls[2 * H] = ct[q];
+        cls[2 * H + 1] = cs[q];
+    }
+    if (over) atomicExch(flags + 1, 1u);
+}
+
 __global__ void k_treep_max(const uint8_t* __restrict__ a, long long N, unsigned* out) {
     unsigned mx = 0;
     for (long long h = blockIdx.x * (long long)blockDim.x + threadIdx.x; h < N; h += (long long)gridDim.x * blockDim.x)
@@ -354,20 +506,21 @@ template <int P>
 void make_mapP(const std::vector<std::vector<int>>& cols, int m, MapP& M) {
     using SH = TreeShape<P>;
     const int ng = (m + SH::G - 1) / SH::G;
+    // packed multiples a * column i, a = 0 .. p-1
+    std::vector<unsigned long long> mult((size_t)m * P, 0ull);
+    for (int i = 0; i < m; ++i) {
+        const unsigned long long c = pack(cols[i]);
+        for (int a = 1; a < P; ++a) mult[(size_t)i * P + a] = padd<P>(mult[(size_t)i * P + a - 1], c);
+    }
     for (int g = 0; g < kMaxGroups; ++g)
         for (int x = 0; x < 256; ++x) {
             unsigned long long v = 0;
             if (g < ng && x < SH::PG) {
                 int y = x;
                 for (int l = 0; l < SH::G; ++l) {
-                    const int dgt = y % P;
+                    const int dgt = y % P, i = g * SH::G + l;
                     y /= P;
-                    const int i = g * SH::G + l;
-                    if (dgt && i < m) {
-                        std::vector<int> col(m);
-                        for (int a = 0; a < m; ++a) col[a] = cols[i][a] * dgt % P;
-                        v = padd<P>(v, pack(col));
-                    }
+                    if (dgt && i < m) v = padd<P>(v, mult[(size_t)i * P + dgt]);
                 }
             }
             M.t[g][x] = v;
@@ -387,12 +540,61 @@ unsigned long long host_applyP(const MapP& M, uint32_t x, int ng) {
 unsigned grid_np(long long n) { return (unsigned)std::max(1ll, std::min((n + 255) / 256, 8ll * 152)); }
 
 template <int P>
+int treep_one(dwt_plan_s* Pl, const std::vector<MapP>& Imap, const std::vector<MapP>& Fmap,
+              const std::vector<MapP>& Qmap, int ng, cudaStream_t st) {
+    const long long N = Pl->N;
+    const int m = Pl->m, s = Pl->s;
+    uint8_t *TU = nullptr, *DU = nullptr;
+    MapP* dmaps = nullptr;
+    unsigned* flags = nullptr;
+    auto cleanup = [&]() {
+        dfree(TU, st); dfree(DU, st); dfree(dmaps, st); dfree(flags, st);
+    };
+    if (dmalloc((void**)&TU, (size_t)s * N, st) || dmalloc((void**)&DU, (size_t)s * N, st) ||
+        dmalloc((void**)&dmaps, sizeof(MapP) * 3 * s, st) || dmalloc((void**)&flags, 8, st) ||
+        dmalloc((void**)&Pl->d_W, (size_t)N * 4, st) || dmalloc((void**)&Pl->d_cls, (size_t)N * 2, st)) {
+        cleanup();
+        return DWT_ENOMEM;
+    }
+    std::vector<MapP> hm(3 * s);
+    for (int j = 0; j < s; ++j) {
+        hm[j] = Imap[j];
+        hm[s + j] = Fmap[j];
+        hm[2 * s + j] = Qmap[j];
+    }
+    DWT_CK(cudaMemcpyAsync(dmaps, hm.data(), sizeof(MapP) * 3 * s, cudaMemcpyHostToDevice, st));
+    DWT_CK(cudaMemsetAsync(flags, 0, 8, st));
+    const size_t smem = 3 * sizeof(MapP) + 32 * 8 + 32 * 4 + (size_t)4 * N + 2 * N + N;
+    int rc = smem_limit_max(k_treep_one<P>);
+    if (rc) { cleanup(); return rc; }
+    {
+        LaunchScope ls("tree_one", st);
+        k_treep_one<P><<<1, 1024, smem, st>>>(dmaps, dmaps + s, dmaps + 2 * s, m, s, ng, TU, DU, Pl->d_cls, Pl->d_W,
+                                              flags);
+    }
+    DWT_CK_LAUNCH("k_treep_one");
+    unsigned hf[2] = {0, 0};
+    DWT_CK(cudaMemcpyAsync(hf, flags, 8, cudaMemcpyDeviceToHost, st));
+    DWT_CK(cudaStreamSynchronize(st));
+    cleanup();
+    if (hf[0] >= kInfP) {
+        set_error("a least nu over some coset reaches 255");
+        return DWT_EUNSUPPORTED;
+    }
+    if (hf[1]) {
+        set_error("a weight denominator prod (1+k_j)^2 exceeds 64 bits");
+        return DWT_EUNSUPPORTED;
+    }
+    return DWT_OK;
+}
+
+template <int P>
 int treep(dwt_plan_s* Pl, cudaStream_t st, bool* used) {
     using SH = TreeShape<P>;
     const long long N = Pl->N;
     const int m = Pl->m, s = Pl->s;
     *used = false;
-    if (m > 16 || m < SH::LB) return DWT_OK;
+    if (m > 16 || m < 1) return DWT_OK;
     const long long nLB = N / SH::TS;
     if (nLB > 16384) return DWT_OK;
     const int ng = (m + SH::G - 1) / SH::G;
@@ -417,6 +619,7 @@ int treep(dwt_plan_s* Pl, cudaStream_t st, bool* used) {
         make_mapP<P>(qc, m, Qmap[j]);
     }
     *used = true;
+    if (m <= SH::LB) return treep_one<P>(Pl, Imap, Fmap, Qmap, ng, st);
     uint8_t *TU = nullptr, *DU = nullptr, *lev = nullptr;
     uint16_t* Ac = nullptr;
     MapP* dmaps = nullptr;

@@ -141,10 +141,11 @@ def test_tables_small_large_boundary(dwt, dev, orc, p, m, s):
 # Plans without DWT_PLAN_KEEP_INDEX_MAP build K(C) with the min-tree form when
 # every C_j is nonsingular (one bottom-up and one top-down tree sweep per
 # coordinate, tiles of 2^13, 3^8, 5^5, 7^4 labels plus a coarse tree above
-# them); the tables must equal the oracle's bit for bit, on one tile, several
-# tiles, and with a coarse tree of several levels.
-@pytest.mark.parametrize("p,m,s", [(2, 9, 4), (2, 13, 9), (2, 14, 3), (2, 17, 20), (3, 8, 5), (3, 11, 9),
-                                   (3, 13, 3), (5, 5, 7), (5, 9, 3), (7, 4, 6), (7, 6, 10)])
+# them, or all in one CTA when the net is one tile); the tables must equal the
+# oracle's bit for bit, on one tile, several tiles, and with a coarse tree of
+# several levels.
+@pytest.mark.parametrize("p,m,s", [(2, 1, 3), (2, 9, 4), (2, 13, 9), (2, 14, 3), (2, 17, 20), (3, 2, 4), (3, 8, 5),
+                                   (3, 11, 9), (3, 13, 3), (5, 5, 7), (5, 9, 3), (7, 4, 6), (7, 6, 10), (2, 12, 64)])
 def test_tables_tree_form(dwt, dev, orc, p, m, s):
     C = S.small_net(p, m, s, index=100 + m + s)
     N = p ** m
@@ -153,9 +154,11 @@ def test_tables_tree_form(dwt, dev, orc, p, m, s):
     plan = dwt.dwt_plan_create(p, m, s, C)
     dwt.dwt_profile_enable(False)
     n_up, _ = dwt.dwt_profile_query("tree_up")
+    n_one, _ = dwt.dwt_profile_query("tree_one")
     dwt.dwt_profile_reset()
     assert plan.status == 0
-    assert n_up == 2 * s   # the tree form ran (once per coordinate and sweep)
+    # the tree form ran: one CTA for a single tile, else one up-sweep launch per coordinate and sweep
+    assert (n_one, n_up) == ((1, 0) if N <= {2: 8192, 3: 6561, 5: 3125, 7: 2401}[p] else (0, 2 * s))
     W, cls = _read_tables(dwt, plan, N)
     ref = orc.coset_leaders_dp(p, m, C, want_W64=False)
     assert ref["status"] == 0
