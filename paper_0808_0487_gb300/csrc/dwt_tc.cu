@@ -25,6 +25,7 @@
 // kernel records an error and leaves, freeing its TMEM.
 #include <cuda_bf16.h>
 #include <stdint.h>
+#include <string.h>
 
 #include <algorithm>
 
@@ -111,11 +112,18 @@ __device__ __forceinline__ void split_bf16(float x, unsigned short& hi, unsigned
 // the same split for two values packed as one 32-bit column (element 2i in the
 // low half): hi and lo words
 __device__ __forceinline__ void split2(float a, float b, uint32_t& hi, uint32_t& lo) {
-    unsigned short ha, la, hb, lb;
-    split_bf16(a, ha, la);
-    split_bf16(b, hb, lb);
-    hi = ha | ((uint32_t)hb << 16);
-    lo = la | ((uint32_t)lb << 16);
+    const __nv_bfloat162 h = __floats2bfloat162_rn(a, b);   // .x = bf16(a) in the low half
+    const float2 hf = __bfloat1622float2(h);
+    unsigned long long ab, hh, d;
+    const float2 abf = make_float2(a, b);
+    memcpy(&ab, &abf, 8);
+    memcpy(&hh, &hf, 8);
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(ab), "l"(hh));
+    float2 df;
+    memcpy(&df, &d, 8);
+    const __nv_bfloat162 l = __floats2bfloat162_rn(df.x, df.y);
+    memcpy(&hi, &h, 4);
+    memcpy(&lo, &l, 4);
 }
 
 __device__ __forceinline__ void tmem_st16(uint32_t taddr, const uint32_t* r) {
@@ -147,8 +155,9 @@ constexpr int kSmemXhi = kOpBytes;
 constexpr int kSmemXlo = 2 * kOpBytes;
 constexpr int kSmemBar = 3 * kOpBytes;     // mbarrier (8 B) + TMEM address (4 B)
 constexpr int kSmemTotal = 3 * kOpBytes + 64 + 1024;   // + slack to align the base to 1024
-// tensor-memory plan (256 columns per CTA): accumulator D1 / D2, round-2 A operand hi / lo
-constexpr uint32_t kTmD = 0, kTmPhi = 128, kTmPlo = 192;
+// tensor-memory plan (256 columns per CTA): two 128-column halves, one holding
+// a tile's accumulator (D1, then D2), the other its round-2 A operand (P_hi in
+// the first 64 columns, P_lo in the next 64); the roles swap from tile to tile
 
 // element (row, k) of a 128-row, 128-wide operand = two 64-wide swizzled blocks
 __device__ __forceinline__ uint32_t op_off(int row, int k) { return (uint32_t)((k >> 6) * (128 * 128)) + sw128(row, k & 63); }
@@ -158,19 +167,27 @@ constexpr int kTcThreads = 256;   // two warps per 32-lane quarter of tensor mem
 // X (tile elements k + 128 n as rows n) -> hi / lo operands in shared memory;
 // all 16 loads of a thread are issued before the first split
 __device__ __forceinline__ void stage_x(unsigned char* sm, const float* src, int t) {
+    // thread t takes 8 consecutive elements per step (one 16-byte chunk of
+    // each operand): e = 8 (t + 256 q), q < 8
     float4 x4[16];
 #pragma unroll
-    for (int q = 0; q < 16; ++q) x4[q] = __ldcs(reinterpret_cast<const float4*>(src + 4 * (t + kTcThreads * q)));
+    for (int q = 0; q < 8; ++q) {
+        const float4* p = reinterpret_cast<const float4*>(src + 8 * (t + kTcThreads * q));
+        x4[2 * q] = __ldcs(p);
+        x4[2 * q + 1] = __ldcs(p + 1);
+    }
 #pragma unroll
-    for (int q = 0; q < 16; ++q) {
-        const int e = 4 * (t + kTcThreads * q);
-        const float4 x = x4[q];
-        uint32_t h01, l01, h23, l23;
-        split2(x.x, x.y, h01, l01);
-        split2(x.z, x.w, h23, l23);
-        const uint32_t o = op_off(e >> 7, e & 127);   // 4 consecutive k stay inside one 16-byte chunk
-        *reinterpret_cast<uint2*>(sm + kSmemXhi + o) = make_uint2(h01, h23);
-        *reinterpret_cast<uint2*>(sm + kSmemXlo + o) = make_uint2(l01, l23);
+    for (int q = 0; q < 8; ++q) {
+        const int e = 8 * (t + kTcThreads * q);
+        const float4 x = x4[2 * q], y = x4[2 * q + 1];
+        uint4 hw, lw;
+        split2(x.x, x.y, hw.x, lw.x);
+        split2(x.z, x.w, hw.y, lw.y);
+        split2(y.x, y.y, hw.z, lw.z);
+        split2(y.z, y.w, hw.w, lw.w);
+        const uint32_t o = op_off(e >> 7, e & 127);
+        *reinterpret_cast<uint4*>(sm + kSmemXhi + o) = hw;
+        *reinterpret_cast<uint4*>(sm + kSmemXlo + o) = lw;
     }
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
 }
@@ -238,60 +255,69 @@ __global__ void __launch_bounds__(kTcThreads, 2) k_tc_lo14(TcJob j0, TcJob j1, i
     const uint32_t lane_base = tmem + ((uint32_t)(32 * (warp & 3)) << 16);
     uint32_t phase = 0;
     bool ok = true;
-
-    for (; tile < ntiles; tile += gridDim.x) {
-        const long long next = tile + gridDim.x;
-        if (t == 0 && tile + (long long)kPre * gridDim.x < ntiles)
-            prefetch_l2_tc(src_of(tile + (long long)kPre * gridDim.x), 1u << 16);
-        // round 1 (X staged and fenced by every thread before the barrier above)
+    // The two 128-column halves of the allocation alternate: tile k accumulates
+    // D1 and D2 in half R = k & 1 and keeps its round-2 operand P in the other
+    // half, where tile k+1's D1 goes once round 2 of tile k has read P.  So the
+    // next tile's round 1 is issued as soon as round 2 finishes, and runs while
+    // the threads store this tile's D2.
+    auto issue_round1 = [&](uint32_t dcol) {
         if (t == 0) {
             for (int part = 0; part < 2; ++part) {
                 const uint32_t xb = s_base + (part ? kSmemXlo : kSmemXhi);
                 for (int ks = 0; ks < 8; ++ks) {
                     const uint32_t koff = (uint32_t)((ks >> 2) * (128 * 128) + (ks & 3) * 32);
-                    mma_bf16(tmem + kTmD, desc_sw128(s_base + kSmemH + koff), desc_sw128(xb + koff), ID, part | ks);
+                    mma_bf16(tmem + dcol, desc_sw128(s_base + kSmemH + koff), desc_sw128(xb + koff), ID, part | ks);
                 }
             }
             mma_commit(bar_addr);
         }
-        ok = __syncthreads_and(mbar_wait(bar_addr, phase) ? 1 : 0) != 0;
-        phase ^= 1;
-        if (!ok) break;
+    };
+    issue_round1(0);   // X of the first tile staged and fenced before the barrier above
+    ok = __syncthreads_and(mbar_wait(bar_addr, phase) ? 1 : 0) != 0;
+    phase ^= 1;
+    for (int it = 0; ok && tile < ntiles; ++it, tile += gridDim.x) {
+        const long long next = tile + gridDim.x;
+        const uint32_t R = (it & 1) ? 128u : 0u, Ro = 128u - R;
+        if (t == 0 && tile + (long long)kPre * gridDim.x < ntiles)
+            prefetch_l2_tc(src_of(tile + (long long)kPre * gridDim.x), 1u << 16);
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        // D1 row h, this warp's half of the columns -> P_hi / P_lo (two BF16 per
-        // column, element 2i low)
+        // round 1 of this tile has finished: D1 row h, this warp's half of the
+        // columns -> P_hi / P_lo in the other half (two BF16 per column, element 2i low)
 #pragma unroll 1
         for (int c = 2 * half; c < 2 * half + 2; ++c) {
             float v[32];
-            tmem_ld32(lane_base + kTmD + 32 * c, v);
+            tmem_ld32(lane_base + R + 32 * c, v);
             uint32_t hw[16], lw[16];
 #pragma unroll
             for (int i = 0; i < 16; ++i) split2(v[2 * i], v[2 * i + 1], hw[i], lw[i]);
-            tmem_st16(lane_base + kTmPhi + 16 * c, hw);
-            tmem_st16(lane_base + kTmPlo + 16 * c, lw);
+            tmem_st16(lane_base + Ro + 16 * c, hw);
+            tmem_st16(lane_base + Ro + 64 + 16 * c, lw);
         }
         asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
         asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
         __syncthreads();
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        // round 2: D2 = P H^T over n, into the accumulator columns
+        // round 2: D2 = P H^T over n, into half R
         if (t == 0) {
             for (int part = 0; part < 2; ++part) {
-                const uint32_t pa = tmem + (part ? kTmPlo : kTmPhi);
+                const uint32_t pa = tmem + Ro + (part ? 64u : 0u);
                 for (int ks = 0; ks < 8; ++ks) {
                     const uint32_t koff = (uint32_t)((ks >> 2) * (128 * 128) + (ks & 3) * 32);
-                    mma_bf16_ta(tmem + kTmD, pa + 8 * ks, desc_sw128(s_base + kSmemH + koff), ID, part | ks);
+                    mma_bf16_ta(tmem + R, pa + 8 * ks, desc_sw128(s_base + kSmemH + koff), ID, part | ks);
                 }
             }
             mma_commit(bar_addr);
         }
         // the next tile's X while round 2 runs (round 1 has finished reading X)
         if (next < ntiles) stage_x(sm, src_of(next), t);
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
         ok = __syncthreads_and(mbar_wait(bar_addr, phase) ? 1 : 0) != 0;
         phase ^= 1;
         if (!ok) break;
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        // D2[h][h'] -> out[h + 128 h']: lanes write consecutive h
+        // round 2 has read P: the next tile's round 1 into half Ro, then this
+        // tile's D2[h][h'] -> out[h + 128 h'] (lanes write consecutive h)
+        if (next < ntiles) issue_round1(Ro);
         const bool second = tile >= j0.ntiles;
         const TcJob& jb = second ? j1 : j0;
         const long long k = second ? tile - j0.ntiles : tile;
@@ -300,14 +326,22 @@ __global__ void __launch_bounds__(kTcThreads, 2) k_tc_lo14(TcJob j0, TcJob j1, i
 #pragma unroll 1
         for (int c = 2 * half; c < 2 * half + 2; ++c) {
             float v[32];
-            tmem_ld32(lane_base + kTmD + 32 * c, v);
+            tmem_ld32(lane_base + R + 32 * c, v);
+            if (scale == 1.f) {
 #pragma unroll
-            for (int i = 0; i < 32; ++i) __stcg(dst + h + 128 * (32 * c + i), v[i] * scale);
+                for (int i = 0; i < 32; ++i) __stcg(dst + h + 128 * (32 * c + i), v[i]);
+            } else {
+#pragma unroll
+                for (int i = 0; i < 32; ++i) __stcg(dst + h + 128 * (32 * c + i), v[i] * scale);
+            }
         }
-        // accumulator read out and next X staged before the next round 1
+        // every thread's D2 reads are done before the next tile writes its P
+        // into half R; the next round 1 must have finished before its D1 is read
         asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-        __syncthreads();
-        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        if (next < ntiles) {
+            ok = __syncthreads_and(mbar_wait(bar_addr, phase) ? 1 : 0) != 0;
+            phase ^= 1;
+        }
     }
     if (!ok && t == 0) atomicExch(err, 1);
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
