@@ -38,6 +38,28 @@ def _dist():
     return ws, rank, local
 
 
+def max_over_ranks(ms, pg, device):
+    """The slowest rank's time: every rank returns the maximum (replicas finish
+    when the last one does).  pg is torch.distributed or None."""
+    if pg is None:
+        return ms
+    import torch
+    t = torch.tensor([float(ms)], dtype=torch.float64, device=device)
+    pg.all_reduce(t, op=pg.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(units_per_rank, world_size, max_ms):
+    """Units processed by all ranks per second of the slowest rank's time."""
+    return units_per_rank * world_size / (max_ms / 1e3)
+
+
+def rank_requests(count, rank):
+    """The serving requests of one rank: disjoint request ids per rank."""
+    import synthetic as S
+    return S.serving_requests(count, first=rank * count)
+
+
 class ClockSampler:
     """nvidia-smi clocks and throttle reasons sampled during the timed region."""
     Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
@@ -335,18 +357,13 @@ def run_gpu(args):
         launches = dwt.dwt_launch_count() - l0
         if pg:
             pg.barrier()
-        ms = e0.elapsed_time(e1)
-        if pg:
-            t = torch.tensor([ms], device=dev)
-            pg.all_reduce(t, op=pg.ReduceOp.MAX)
-            ms = float(t.item())
+        ms = max_over_ranks(e0.elapsed_time(e1), pg, dev)
         return ms, launches
 
     with ClockSampler(local) as clk:
         ms, launches = timed(step, args.steps)
     clocks = clk.summary()
-    pts = B * N * args.steps * ws
-    value = pts / (ms / 1e3)
+    value = whole_job_rate(B * N * args.steps, ws, ms)
 
     # forward / inverse alone (extra context)
     def fwd():
@@ -477,7 +494,7 @@ def run_serve(args):
     import torch
     torch.cuda.set_device(local)
     dwt.lib()
-    reqs = S.serving_requests(args.requests, first=rank * args.requests)
+    reqs = rank_requests(args.requests, rank)
     warm = S.serving_requests(16, first=10 ** 6)
 
     def run(rate, label):
