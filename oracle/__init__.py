@@ -57,6 +57,11 @@ def lib():
                                  _f64p, _f64p, _ip, _ip]
         L.orc_eval_product.argtypes = [ctypes.c_int] * 3 + [_u32p, _f64p, _f64p]
         L.orc_eval_exp.argtypes = [ctypes.c_int] * 3 + [_u32p, _f64p]
+        L.orc_kprime.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_uint32]
+        L.orc_kprime.restype = ctypes.c_double
+        L.orc_rprime.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_uint32]
+        L.orc_rprime.restype = ctypes.c_double
+        L.orc_kernel_data.argtypes = [ctypes.c_int] * 3 + [_u32p, ctypes.c_double, _f64p, _f64p, _f64p, _f64p]
         _lib = L
     return _lib
 
@@ -253,6 +258,58 @@ def interpolate(p, m, f, W, cls, s, thr=0.99):
     c = fiwt(p, m, g)
     vt, vs, dt, ds = effdim(g, cls, s, thr)
     return c, g, vt, vs, dt, ds
+
+
+# --- the kernel spline (Sec. 3.1) and its ANOVA variances (Sec. 4) ---------------
+def kprime(p, m, alpha, Y):
+    """K'(x, 0) at x = Y / p^m (short form of Sec. 4)."""
+    return lib().orc_kprime(p, m, alpha, int(Y))
+
+
+def rprime(p, m, alpha, Y):
+    """R'(x, 0) at x = Y / p^m (short form of Sec. 4)."""
+    return lib().orc_rprime(p, m, alpha, int(Y))
+
+
+def kernel_data(p, m, Y, alpha, gamma):
+    """(K[N], R[s][N], E[s][N]): the kernel data K(x_n, 0), the truncated products
+    R_d(x_n, 0), d = 1..s, and the degree-j parts E_j(x_n, 0) = sum_{|u|=j} gamma_u^2 R_u."""
+    Y = np.ascontiguousarray(Y, dtype=np.uint32)
+    s, N = Y.shape
+    gamma = np.ascontiguousarray(gamma, dtype=np.float64)
+    K = np.empty(N)
+    R = np.empty((s, N))
+    E = np.empty((s, N))
+    lib().orc_kernel_data(p, m, s, _p(Y, _u32p), alpha, _p(gamma, _f64p), _p(K, _f64p), _p(R, _f64p), _p(E, _f64p))
+    return K, R, E
+
+
+def spline(p, m, Y, f, alpha, gamma, thr=0.99):
+    """The kernel spline of f on the net and the variances of its ANOVA effects.
+
+    K~ = DWT of the kernel data; c~ = f~ / (p^m K~) (eq. splinecoef); c = FIWT(c~)
+    (Algorithm 2); sigma^2_trc(d) = p^{2m} sum_H |c~|^2 (R~_d - [H = 0]) and
+    sigma^2_sup(d) = p^{2m} sum_H |c~|^2 sum_{j <= d} E~_j, d = 0..s (eq. sig2sfu
+    summed over u, the constant effect u = {} left out), then d_trc, d_sup.
+    Returns a dict with Ktil, W (= 1 / (p^m K~)), ctil, c, var_trc, var_sup, d_trc, d_sup."""
+    N = p ** m
+    s = Y.shape[0]
+    K, R, E = kernel_data(p, m, Y, alpha, gamma)
+    Kt = fwt(p, m, K)
+    W = 1.0 / (N * Kt.real)
+    ft = fwt(p, m, f)
+    ct = ft * W
+    c = fiwt(p, m, ct)
+    a = np.abs(ct) ** 2
+    vt = np.zeros(s + 1)
+    vs = np.zeros(s + 1)
+    for d in range(1, s + 1):
+        Rt = fwt(p, m, R[d - 1]).real
+        Rt[0] -= 1.0
+        vt[d] = N * N * float(np.dot(a, Rt))
+        vs[d] = vs[d - 1] + N * N * float(np.dot(a, fwt(p, m, E[d - 1]).real))
+    dt, ds = effdim_threshold(vt, vs, thr)
+    return dict(Ktil=Kt, W=W, ctil=ct, c=c, var_trc=vt, var_sup=vs, d_trc=dt, d_sup=ds)
 
 
 # --- synthetic test functions ------------------------------------------------

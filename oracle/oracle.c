@@ -699,3 +699,66 @@ void orc_eval_exp(int p, int m, int s, const uint32_t *Y, double *f)
         f[n] = exp(a);
     }
 }
+
+/* ------------------------------------------------------------------------ */
+/* The kernel spline of Sec. 3.1 and its ANOVA variances (Sec. 4).          */
+
+/* position i >= 1 of the first nonzero base-p digit of x = Y / p^m (0 if x = 0) */
+static int first_digit_pos(int p, int m, uint32_t Y)
+{
+    if (Y == 0) return 0;
+    int t = 0;                         /* Y in [p^t, p^(t+1)) */
+    for (uint64_t q = (uint64_t)Y; q >= (uint64_t)p; q /= (uint64_t)p) ++t;
+    return m - t;
+}
+
+/* Univariate kernel K'(x, 0) in its short form (Sec. 4): 1 at x = 0, else
+ * 1 - p^{i(1-alpha)} (p^alpha - 1)/(p - 1), i the first nonzero digit of x.  */
+double orc_kprime(int p, int m, double alpha, uint32_t Y)
+{
+    int i = first_digit_pos(p, m, Y);
+    if (i == 0) return 1.0;
+    return 1.0 - pow((double)p, i * (1.0 - alpha)) * (pow((double)p, alpha) - 1.0) / (p - 1.0);
+}
+
+/* Univariate kernel R'(x, 0) = int K'(t, x) K'(t, 0) dt in its short form (Sec. 4):
+ * (p^a - p)^2 / ((p-1)(p^{2a} - p)) [1 - p^{i(1-2a)} (p^{2a} - 1)/(p - 1)], the
+ * bracket being 1 at x = 0.                                                 */
+double orc_rprime(int p, int m, double alpha, uint32_t Y)
+{
+    double pa = pow((double)p, alpha), p2a = pow((double)p, 2.0 * alpha);
+    double c = (pa - p) * (pa - p) / ((p - 1.0) * (p2a - p));
+    int i = first_digit_pos(p, m, Y);
+    if (i == 0) return c;
+    return c * (1.0 - pow((double)p, i * (1.0 - 2.0 * alpha)) * (p2a - 1.0) / (p - 1.0));
+}
+
+/* Kernel data at the net points (Sec. 3.1 and 4), Y[j][n] the point digits:
+ *   K[n]      = prod_j (1 + gamma_j K'(x_{j,n}, 0)),
+ *   R[d-1][n] = prod_{j <= d} (1 + gamma_j^2 R'(x_{j,n}, 0)),       d = 1..s,
+ *   E[j-1][n] = sum_{|u| = j} prod_{i in u} gamma_i^2 R'(x_{i,n}, 0), j = 1..s,
+ * the last by the recurrence of elementary symmetric polynomials, one
+ * coordinate at a time.  Any of K, R, E may be NULL.                        */
+void orc_kernel_data(int p, int m, int s, const uint32_t *Y, double alpha, const double *gamma,
+                     double *K, double *R, double *E)
+{
+    uint64_t N = ipow_u64(p, m);
+    double *e = (double *)malloc(((size_t)s + 1) * sizeof(double));
+    for (uint64_t n = 0; n < N; ++n) {
+        double kv = 1.0, rv = 1.0;
+        e[0] = 1.0;
+        for (int j = 1; j <= s; ++j) e[j] = 0.0;
+        for (int j = 0; j < s; ++j) {
+            uint32_t y = Y[(size_t)j * N + n];
+            kv *= 1.0 + gamma[j] * orc_kprime(p, m, alpha, y);
+            double a = gamma[j] * gamma[j] * orc_rprime(p, m, alpha, y);
+            rv *= 1.0 + a;
+            if (R) R[(size_t)j * N + n] = rv;
+            for (int q = j + 1; q >= 1; --q) e[q] += a * e[q - 1];
+        }
+        if (K) K[n] = kv;
+        if (E)
+            for (int q = 1; q <= s; ++q) E[(size_t)(q - 1) * N + n] = e[q];
+    }
+    free(e);
+}
