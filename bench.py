@@ -279,6 +279,26 @@ def run_other_configs(dwt, dev, stream, timed, steps):
             r[k + "_points_per_s"] = B * N * steps / (ms / 1e3)
         out["p2_m20_s16_b32_" + name] = r
         del x, y
+    # the kernel spline of Sec. 3.1 with its ANOVA variances (FP64) on the same
+    # net: forward, weight 1 / (p^m K~), inverse and the 2s variance sums
+    w2 = S.workload_p2_m20()
+    plan2 = dwt.dwt_plan_create(2, 20, 16, w2["C"], dwt.DWT_PLAN_TRANSFORM_ONLY)
+    N2 = 1 << 20
+    dwt.dwt_spline_prepare(plan2, 2.0, [0.9 / (j + 1) ** 1.2 for j in range(16)])
+    fs = torch.empty((32, N2), dtype=torch.float64, device=dev)
+    dwt.dwt_eval_product(plan2, torch.tensor(w2["coef"], dtype=torch.float64, device=dev), fs, 32, N2, dwt.DWT_F64)
+    cs = torch.empty_like(fs)
+    vts = torch.empty((32, 17), dtype=torch.float64, device=dev)
+    vss = torch.empty_like(vts)
+    dims = torch.empty((32, 2), dtype=torch.int32, device=dev)
+
+    def spl():
+        dwt.dwt_spline(plan2, fs, cs, 32, N2, vts, vss, dims, stream=stream)
+
+    ms_s, _ = timed(spl, steps)
+    out["spline_p2_m20_s16_b32"] = {"points_per_s": 32 * N2 * steps / (ms_s / 1e3), "dtype": "f64",
+                                    "alpha": 2.0, "gamma": "0.9 / j^1.2"}
+    del fs, cs
     w = S.workload_p3_m13()
     p, m, s = w["p"], w["m"], w["s"]
     N = p ** m

@@ -195,6 +195,41 @@ int dwt_interpolate_host(dwt_plan_t plan, const void *f, void *c, int batch, lon
                          dwt_weight weight, double *var, int *dim, double threshold, void *stream);
 
 /*
+ * The kernel spline of Sec. 3.1 and the variances of its ANOVA effects
+ * (Sec. 4), in FP64.  The kernel is K(x, y) = prod_j (1 + gamma_j K'(x_j (-) y_j, 0))
+ * with the univariate K' of Sec. 4 (Walsh coefficients proportional to
+ * p^{-alpha a} for wavenumbers with top digit a), evaluated by its short form.
+ *
+ * dwt_spline_prepare(plan, alpha, gamma, stream): alpha > 1; gamma: host
+ * double [s], entries >= 0 (the paper takes gamma_j = beta j^q).  Builds in
+ * the plan the kernel data at the net points and its DWT K~, the spline weight
+ * W_K = 1 / (p^m K~) (eq. splinecoef), and the DWTs of R_d = prod_{j<=d}
+ * (1 + gamma_j^2 R') and of the degree-j parts E_j of R_s (the tables of the
+ * truncation and superposition variances): (1 + 2s) N doubles, s <= 64.  Works
+ * on any plan (the coset tables are not used).  Replaces earlier tables; runs
+ * in the order of `stream`.
+ *
+ * dwt_spline(plan, f, c, batch, ld, var_trc, var_sup, dim, threshold, stream):
+ *   f: device double [batch][ld], the function at the net points;
+ *   c: device output [batch][ld] of the spline coefficients c_n
+ *      (sum_v c_v K(x_n (-) x_v, 0) = f(x_n)): double for p = 2, complex double
+ *      (interleaved) for p > 2, whose imaginary parts are rounding; or NULL;
+ *   var_trc, var_sup: optional device double [batch][s+1]:
+ *      var_trc[d] = sum over nonempty u within 1..d of sigma^2((Sf)_u),
+ *      var_sup[d] = sum over 0 < |u| <= d of sigma^2((Sf)_u)   (eq. sig2sfu);
+ *   dim: optional device int [batch][2], d_trc and d_sup at `threshold`.
+ * c~ = f~ W_K divides by K~, which is small at high H: the coefficients are as
+ * well conditioned as that quotient (relative error about
+ * 1e-16 max|K(x_n, 0)| / min|K~|).  DWT_EINVAL without dwt_spline_prepare.
+ * No counterpart in the paper for the superposition route: the degree-j
+ * tables come from the elementary symmetric polynomials of the per-coordinate
+ * terms instead of the interpolation in beta^2 of Sec. 4 (same quantities).
+ */
+int dwt_spline_prepare(dwt_plan_t plan, double alpha, const double *gamma, void *stream);
+int dwt_spline(dwt_plan_t plan, const double *f, void *c, int batch, long long ld, double *var_trc,
+               double *var_sup, int *dim, double threshold, void *stream);
+
+/*
  * Effective dimension of given coefficients g (Sec. 4), the variance and
  * threshold part of dwt_interpolate alone.  coef: device, type DWT_F32
  * (p = 2) or DWT_C64, ld elements per function.  var/dim as above (device).

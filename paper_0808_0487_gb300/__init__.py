@@ -76,6 +76,8 @@ _SIGS = {
     "dwt_inverse": (_I, [_VP, _VP, _VP, _I, _LL, _LL, _I, _I, _I, _VP]),
     "dwt_interpolate": (_I, [_VP, _VP, _VP, _VP, _I, _LL, _I, _I, _I, _VP, _VP, ctypes.c_double, _VP]),
     "dwt_interpolate_host": (_I, [_VP, _VP, _VP, _I, _LL, _I, _I, _VP, _VP, ctypes.c_double, _VP]),
+    "dwt_spline_prepare": (_I, [_VP, ctypes.c_double, _VP, _VP]),
+    "dwt_spline": (_I, [_VP, _VP, _VP, _I, _LL, _VP, _VP, _VP, ctypes.c_double, _VP]),
     "dwt_effdim": (_I, [_VP, _VP, _I, _LL, _I, _VP, _VP, ctypes.c_double, _VP]),
     "dwt_effdim_static": (_I, [_VP, _VP, _I, _LL, _I, _VP, _VP, ctypes.c_double, _VP]),
     "dwt_eval_product": (_I, [_VP, _VP, _VP, _I, _LL, _I, _VP]),
@@ -242,6 +244,18 @@ def dwt_interpolate_host(plan, f, c, batch, ld, f_t, weight, var=None, dim=None,
     """dwt_interpolate on host buffers (f, c, var, dim host-resident; page-locked ones overlap copies)."""
     return _check(lib().dwt_interpolate_host(plan.handle, _ptr(f), _ptr(c), batch, ld, f_t, weight, _ptr(var),
                                              _ptr(dim), threshold, _stream(stream)))
+
+
+def dwt_spline_prepare(plan, alpha, gamma, stream=None):
+    """Kernel-spline tables for (alpha, gamma[s]) (Sec. 3.1, Sec. 4); gamma is a host sequence."""
+    g = np.ascontiguousarray(gamma, dtype=np.float64)
+    return _check(lib().dwt_spline_prepare(plan.handle, float(alpha), g.ctypes.data, _stream(stream)))
+
+
+def dwt_spline(plan, f, c, batch, ld, var_trc=None, var_sup=None, dim=None, threshold=0.99, stream=None):
+    """Spline coefficients c_n of f (FP64) and the ANOVA variances of the spline."""
+    return _check(lib().dwt_spline(plan.handle, _ptr(f), _ptr(c), batch, ld, _ptr(var_trc), _ptr(var_sup),
+                                   _ptr(dim), threshold, _stream(stream)))
 
 
 def dwt_effdim(plan, coef, batch, ld, t, var=None, dim=None, threshold=0.99, stream=None):

@@ -10,6 +10,8 @@
 #include <mutex>
 #include <unordered_set>
 
+#include <cmath>
+
 #include "dwt_internal.cuh"
 
 namespace dwt {
@@ -329,6 +331,7 @@ int dwt_plan_destroy(dwt_plan_t P) {
     if (!P) return DWT_OK;
     cudaDeviceSynchronize();
     host_stage_free(P, nullptr, true);
+    spline_free(P, nullptr, true);
     cudaFree(P->d_R);
     cudaFree(P->d_col);
     cudaFree(P->d_C);
@@ -347,6 +350,7 @@ int dwt_plan_destroy_async(dwt_plan_t P, void* stream) {
     if (!P) return DWT_OK;
     cudaStream_t st = (cudaStream_t)stream;
     host_stage_free(P, st, false);
+    spline_free(P, st, false);
     dfree(P->d_R, st);
     dfree(P->d_col, st);
     dfree(P->d_C, st);
@@ -514,6 +518,29 @@ int dwt_interpolate_host(dwt_plan_t P, const void* f, void* c, int batch, long l
     }
     if (batch == 0) return DWT_OK;
     return run_interpolate_host(P, f, c, batch, ld, f_t, weight, var, dim, thr, (cudaStream_t)stream);
+}
+
+int dwt_spline_prepare(dwt_plan_t P, double alpha, const double* gamma, void* stream) {
+    if (!P || !gamma || !(alpha > 1.0) || !std::isfinite(alpha)) {
+        set_error("dwt_spline_prepare: bad arguments (alpha > 1 and gamma[s] required)");
+        return DWT_EINVAL;
+    }
+    for (int j = 0; j < P->s; ++j)
+        if (!(gamma[j] >= 0.0) || !std::isfinite(gamma[j])) {
+            set_error("dwt_spline_prepare: gamma[%d] must be finite and >= 0", j);
+            return DWT_EINVAL;
+        }
+    return run_spline_prepare(P, alpha, gamma, (cudaStream_t)stream);
+}
+
+int dwt_spline(dwt_plan_t P, const double* f, void* c, int batch, long long ld, double* var_trc, double* var_sup,
+               int* dim, double thr, void* stream) {
+    if (!P || batch < 0 || (batch > 0 && !f) || ld < P->N || !(thr > 0.0 && thr <= 1.0)) {
+        set_error("dwt_spline: bad arguments");
+        return DWT_EINVAL;
+    }
+    if (batch == 0) return DWT_OK;
+    return run_spline(P, f, c, batch, ld, var_trc, var_sup, dim, thr, (cudaStream_t)stream);
 }
 
 int dwt_effdim(dwt_plan_t P, const void* coef, int batch, long long ld, dwt_dtype t, double* var, int* dim, double thr,

@@ -90,6 +90,9 @@ struct dwt_plan_s {
     dwt::PassPlan passes[3];
     // device slots, streams and events of dwt_interpolate_host (first use)
     dwt::HostStage* host = nullptr;
+    // kernel spline tables (dwt_spline_prepare): W_K [N], then R~_d - [H=0] and E~_j, [2s][N], FP64
+    double* d_splW = nullptr;
+    double* d_splT = nullptr;
 };
 
 namespace dwt {
@@ -123,6 +126,10 @@ int run_interpolate_host(dwt_plan_s* P, const void* f_host, void* c_host, int ba
 // releases the plan's dwt_interpolate_host resources: after synchronising
 // (sync) or in the order of stream st
 void host_stage_free(dwt_plan_s* P, cudaStream_t st, bool sync);
+int run_spline_prepare(dwt_plan_s* P, double alpha, const double* gamma, cudaStream_t st);
+int run_spline(dwt_plan_s* P, const double* f, void* c, int batch, long long ld, double* var_trc, double* var_sup,
+               int* dim, double thr, cudaStream_t st);
+void spline_free(dwt_plan_s* P, cudaStream_t st, bool sync);
 int run_points(dwt_plan_s* P, uint32_t* Y, long long ldY, cudaStream_t st);
 int run_k_to_h(dwt_plan_s* P, const uint32_t* k, uint32_t* H, long long cnt, cudaStream_t st);
 int run_h_to_k(dwt_plan_s* P, const uint32_t* H, uint32_t* k, long long cnt, cudaStream_t st);

@@ -1,0 +1,313 @@
+// dwt_spline.cu -- the kernel spline of Sec. 3.1 and the variances of its
+// ANOVA effects (Sec. 4), in FP64.
+//
+// The reproducing kernel K(x, y) = prod_j (1 + gamma_j K'(x_j (-) y_j, 0)) has
+// Walsh coefficients supported on all wavenumbers, and its data at the net
+// points aliases them onto the cosets: K~(H) = DWT of (K(x_n, 0))_n.  The
+// interpolation conditions f(x_n) = sum_v c_v K(x_n (-) x_v, 0) are diagonal
+// in the Walsh basis (eq. splinecoef): c~(H) = f~(H) / (p^m K~(H)), and
+// c = FIWT(c~) (Algorithm 2).  With R'(x, 0) = int K'(t, x) K'(t, 0) dt and
+// R_d = prod_{j <= d} (1 + gamma_j^2 R'), eq. sig2sfu summed over the nonempty
+// u within 1..d gives
+//     sigma^2_trc(d) = p^{2m} sum_H |c~(H)|^2 (R~_d(H) - [H = 0]),
+// and over |u| = j the degree-j part E_j = sum_{|u| = j} gamma_u^2 R_u of
+// R_s = prod_j (1 + gamma_j^2 R'), built point by point with the recurrence
+// of elementary symmetric polynomials, gives
+//     sigma^2_sup(d) = p^{2m} sum_H |c~(H)|^2 sum_{j <= d} E~_j(H).
+// The constant effect (u = {}, the squared mean) is not a variance and is
+// left out; the K' and R' values come from their short forms (Sec. 4).
+//
+// dwt_spline_prepare builds, once per (alpha, gamma), the kernel data at the
+// net points, its 1 + 2s DWTs, and keeps W_K = 1 / (p^m K~) and the 2s
+// variance tables (real parts: the kernels are real and symmetric, so their
+// DWTs are real up to rounding).  dwt_spline then transforms each function,
+// multiplies by W_K, transforms back, and contracts |c~|^2 with the tables in
+// a fixed summation order.
+#include <math.h>
+
+#include <algorithm>
+#include <vector>
+
+#include "dwt_internal.cuh"
+
+namespace dwt {
+
+namespace {
+
+constexpr int kSplineMaxS = 64;
+constexpr int kDotTile = 4096;   // labels per block of the variance contraction
+
+// kernel data at point n: K, R_1..R_s, E_1..E_s (rows of `out`, ld N)
+__global__ void k_spline_data(const uint32_t* __restrict__ Y, long long N, int s, int p, int m,
+                              const double* __restrict__ kp, const double* __restrict__ rp,
+                              const double* __restrict__ gam, double* out) {
+    double e[kSplineMaxS + 1];
+    for (long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x; n < N; n += (long long)gridDim.x * blockDim.x) {
+        double kv = 1.0, rv = 1.0;
+        e[0] = 1.0;
+        for (int q = 1; q <= s; ++q) e[q] = 0.0;
+        for (int j = 0; j < s; ++j) {
+            uint32_t y = Y[(long long)j * N + n];
+            int i = 0;   // position of the first nonzero base-p digit of x = y / p^m
+            if (y) {
+                int t = 0;
+                while (y >= (uint32_t)p) {
+                    y /= (uint32_t)p;
+                    ++t;
+                }
+                i = m - t;
+            }
+            kv *= 1.0 + gam[j] * kp[i];
+            const double a = gam[j] * gam[j] * rp[i];
+            rv *= 1.0 + a;
+            out[(long long)(1 + j) * N + n] = rv;
+            for (int q = j + 1; q >= 1; --q) e[q] += a * e[q - 1];
+        }
+        out[n] = kv;
+        for (int q = 1; q <= s; ++q) out[(long long)(s + q) * N + n] = e[q];
+    }
+}
+
+// real parts of the 1 + 2s transforms (interleaved complex when cplx) ->
+// W_K = 1 / (N Re K~) and the tables, with R~_d(0) - 1
+__global__ void k_spline_tables(const double* __restrict__ tr, int cplx, long long N, int s, double* W,
+                                double* tab) {
+    const long long total = (long long)(1 + 2 * s) * N;
+    for (long long x = blockIdx.x * (long long)blockDim.x + threadIdx.x; x < total;
+         x += (long long)gridDim.x * blockDim.x) {
+        const long long row = x / N, H = x - row * N;
+        const double v = cplx ? tr[2 * x] : tr[x];
+        if (row == 0) {
+            W[H] = 1.0 / ((double)N * v);
+        } else {
+            tab[x - N] = (row <= s && H == 0) ? v - 1.0 : v;
+        }
+    }
+}
+
+// c~ = f~ W_K in place ([batch][N], real or interleaved complex)
+__global__ void k_spline_scale(double* ft, int cplx, long long N, long long total, const double* __restrict__ W) {
+    for (long long x = blockIdx.x * (long long)blockDim.x + threadIdx.x; x < total;
+         x += (long long)gridDim.x * blockDim.x) {
+        const double w = W[x % N];
+        if (cplx) {
+            ft[2 * x] *= w;
+            ft[2 * x + 1] *= w;
+        } else {
+            ft[x] *= w;
+        }
+    }
+}
+
+// partial sums of |c~(H)|^2 T_t(H) over one tile of labels, for all 2s tables:
+// part[(b * 2s + t) * ntile + tile]; per thread in label order, then a fixed tree
+__global__ void __launch_bounds__(256) k_spline_dots(const double* __restrict__ ct, int cplx, long long N, int nt,
+                                                     const double* __restrict__ tab, double* part, long long ntile) {
+    __shared__ double red[256];
+    const long long tile = blockIdx.x, b = blockIdx.y;
+    const long long h0 = tile * kDotTile;
+    const int t = threadIdx.x;
+    constexpr int PER = kDotTile / 256;
+    double a[PER];
+#pragma unroll
+    for (int q = 0; q < PER; ++q) {
+        const long long H = h0 + t + 256 * q;
+        double v = 0.0;
+        if (H < N) {
+            const long long x = b * N + H;
+            v = cplx ? ct[2 * x] * ct[2 * x] + ct[2 * x + 1] * ct[2 * x + 1] : ct[x] * ct[x];
+        }
+        a[q] = v;
+    }
+    for (int tb = 0; tb < nt; ++tb) {
+        const double* T = tab + (long long)tb * N;
+        double acc = 0.0;
+#pragma unroll
+        for (int q = 0; q < PER; ++q) {
+            const long long H = h0 + t + 256 * q;
+            if (H < N) acc += a[q] * T[H];
+        }
+        red[t] = acc;
+        __syncthreads();
+        for (int w = 128; w > 0; w >>= 1) {
+            if (t < w) red[t] += red[t + w];
+            __syncthreads();
+        }
+        if (t == 0) part[(b * nt + tb) * ntile + tile] = red[0];
+        __syncthreads();
+    }
+}
+
+// sums over tiles in tile order, then the cumulative variances and dimensions
+// (least d with variance >= thr * total, 0 when the total is 0)
+__global__ void k_spline_finalize(const double* __restrict__ part, long long ntile, int s, int batch, double N2,
+                                  double thr, double* var_trc, double* var_sup, int* dim) {
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= batch) return;
+    const int nt = 2 * s;
+    double vt[kSplineMaxS + 1], vs[kSplineMaxS + 1];
+    vt[0] = vs[0] = 0.0;
+    for (int d = 1; d <= s; ++d) {
+        double x = 0.0, y = 0.0;
+        const double* pr = part + ((long long)b * nt + (d - 1)) * ntile;
+        const double* pe = part + ((long long)b * nt + (s + d - 1)) * ntile;
+        for (long long i = 0; i < ntile; ++i) {
+            x += pr[i];
+            y += pe[i];
+        }
+        vt[d] = N2 * x;
+        vs[d] = vs[d - 1] + N2 * y;
+    }
+    for (int d = 0; d <= s; ++d) {
+        if (var_trc) var_trc[(long long)b * (s + 1) + d] = vt[d];
+        if (var_sup) var_sup[(long long)b * (s + 1) + d] = vs[d];
+    }
+    if (dim) {
+        const double tot = vt[s];
+        int dt = 0, ds = 0;
+        if (tot > 0.0) {
+            dt = ds = s;
+            for (int d = s; d >= 0; --d) {
+                if (vt[d] >= thr * tot) dt = d;
+                if (vs[d] >= thr * tot) ds = d;
+            }
+        }
+        dim[2 * b] = dt;
+        dim[2 * b + 1] = ds;
+    }
+}
+
+unsigned grid_sp(long long n) { return (unsigned)std::max(1ll, std::min((n + 255) / 256, 8ll * 152)); }
+
+}  // namespace
+
+void spline_free(dwt_plan_s* P, cudaStream_t st, bool sync) {
+    if (sync) {
+        cudaFree(P->d_splW);
+        cudaFree(P->d_splT);
+    } else {
+        dfree(P->d_splW, st);
+        dfree(P->d_splT, st);
+    }
+    P->d_splW = nullptr;
+    P->d_splT = nullptr;
+}
+
+int run_spline_prepare(dwt_plan_s* P, double alpha, const double* gamma, cudaStream_t st) {
+    const long long N = P->N;
+    const int s = P->s, p = P->p, m = P->m;
+    if (s > kSplineMaxS) {
+        set_error("the kernel spline supports s <= %d", kSplineMaxS);
+        return DWT_EUNSUPPORTED;
+    }
+    // K'(x, 0) and R'(x, 0) by the position i (1..m) of the first nonzero digit; i = 0 for x = 0
+    std::vector<double> hv(3 * (m + 1) + s);
+    const double pa = std::pow((double)p, alpha), p2a = std::pow((double)p, 2.0 * alpha);
+    const double rc = (pa - p) * (pa - p) / ((p - 1.0) * (p2a - p));
+    for (int i = 0; i <= m; ++i) {
+        hv[i] = i == 0 ? 1.0 : 1.0 - std::pow((double)p, i * (1.0 - alpha)) * (pa - 1.0) / (p - 1.0);
+        hv[m + 1 + i] = i == 0 ? rc : rc * (1.0 - std::pow((double)p, i * (1.0 - 2.0 * alpha)) * (p2a - 1.0) / (p - 1.0));
+    }
+    for (int j = 0; j < s; ++j) hv[2 * (m + 1) + j] = gamma[j];
+    const int rows = 1 + 2 * s;
+    const bool cplx = p != 2;
+    uint32_t* Y = nullptr;
+    double *dv = nullptr, *data = nullptr, *tr = nullptr;
+    auto cleanup = [&]() {
+        dfree(Y, st);
+        dfree(dv, st);
+        dfree(data, st);
+        if (tr != data) dfree(tr, st);
+    };
+    if (dmalloc((void**)&Y, (size_t)s * N * 4, st) || dmalloc((void**)&dv, hv.size() * 8, st) ||
+        dmalloc((void**)&data, (size_t)rows * N * 8, st)) {
+        cleanup();
+        return DWT_ENOMEM;
+    }
+    tr = data;
+    if (cplx && dmalloc((void**)&tr, (size_t)rows * N * 16, st)) {
+        tr = data;
+        cleanup();
+        return DWT_ENOMEM;
+    }
+    DWT_CK(cudaMemcpyAsync(dv, hv.data(), hv.size() * 8, cudaMemcpyHostToDevice, st));
+    int rc2 = run_points(P, Y, N, st);
+    if (rc2) { cleanup(); return rc2; }
+    {
+        LaunchScope ls("spline_data", st);
+        k_spline_data<<<grid_sp(N), 128, 0, st>>>(Y, N, s, p, m, dv, dv + m + 1, dv + 2 * (m + 1), data);
+    }
+    DWT_CK_LAUNCH("k_spline_data");
+    rc2 = run_transform(P, data, tr, rows, N, N, DWT_F64, cplx ? DWT_C128 : DWT_F64, -1, st);
+    if (rc2) { cleanup(); return rc2; }
+    spline_free(P, st, false);
+    if (dmalloc((void**)&P->d_splW, (size_t)N * 8, st) || dmalloc((void**)&P->d_splT, (size_t)2 * s * N * 8, st)) {
+        spline_free(P, st, false);
+        cleanup();
+        return DWT_ENOMEM;
+    }
+    {
+        LaunchScope ls("spline_tables", st);
+        k_spline_tables<<<grid_sp((long long)rows * N), 256, 0, st>>>(tr, cplx ? 1 : 0, N, s, P->d_splW, P->d_splT);
+    }
+    DWT_CK_LAUNCH("k_spline_tables");
+    cleanup();
+    return DWT_OK;
+}
+
+int run_spline(dwt_plan_s* P, const double* f, void* c, int batch, long long ld, double* var_trc, double* var_sup,
+               int* dim, double thr, cudaStream_t st) {
+    if (!P->d_splW) {
+        set_error("dwt_spline: no kernel tables (call dwt_spline_prepare first)");
+        return DWT_EINVAL;
+    }
+    const long long N = P->N;
+    const int s = P->s;
+    const bool cplx = P->p != 2;
+    const size_t eb = cplx ? 16 : 8;
+    double* ft = nullptr;
+    double* part = nullptr;
+    const long long ntile = (N + kDotTile - 1) / kDotTile;
+    const bool want_var = var_trc || var_sup || dim;
+    if (dmalloc((void**)&ft, (size_t)batch * N * eb, st) ||
+        (want_var && dmalloc((void**)&part, (size_t)batch * 2 * s * ntile * 8, st))) {
+        dfree(ft, st);
+        return DWT_ENOMEM;
+    }
+    auto cleanup = [&]() {
+        dfree(ft, st);
+        dfree(part, st);
+    };
+    int rc = run_transform(P, f, ft, batch, ld, N, DWT_F64, cplx ? DWT_C128 : DWT_F64, -1, st);
+    if (rc) { cleanup(); return rc; }
+    {
+        LaunchScope ls("spline_scale", st);
+        k_spline_scale<<<grid_sp((long long)batch * N), 256, 0, st>>>(ft, cplx ? 1 : 0, N, (long long)batch * N,
+                                                                     P->d_splW);
+    }
+    DWT_CK_LAUNCH("k_spline_scale");
+    if (want_var) {
+        for (int b0 = 0; b0 < batch; b0 += 65535) {
+            const int nb = std::min(65535, batch - b0);
+            LaunchScope ls("spline_dots", st);
+            k_spline_dots<<<dim3((unsigned)ntile, (unsigned)nb), 256, 0, st>>>(
+                ft + (size_t)b0 * N * (eb / 8), cplx ? 1 : 0, N, 2 * s, P->d_splT, part + (size_t)b0 * 2 * s * ntile,
+                ntile);
+        }
+        DWT_CK_LAUNCH("k_spline_dots");
+    }
+    if (c) {
+        rc = run_transform(P, ft, c, batch, N, ld, cplx ? DWT_C128 : DWT_F64, cplx ? DWT_C128 : DWT_F64, +1, st);
+        if (rc) { cleanup(); return rc; }
+    }
+    if (want_var) {
+        LaunchScope ls("spline_finalize", st);
+        k_spline_finalize<<<(batch + 127) / 128, 128, 0, st>>>(part, ntile, s, batch, (double)N * (double)N, thr,
+                                                               var_trc, var_sup, dim);
+    }
+    DWT_CK_LAUNCH("k_spline_finalize");
+    cleanup();
+    return DWT_OK;
+}
+
+}  // namespace dwt

@@ -1,0 +1,61 @@
+"""GPU parity of the kernel spline (Sec. 3.1) and its ANOVA variances (Sec. 4)
+against the FP64 oracle.  Both sides divide f~ by p^m K~; the rounding of K~
+(about 1e-16 of the largest kernel datum) is amplified where K~ is small, so
+the tolerance on c is that ratio, measured on the oracle's K~."""
+import numpy as np
+import pytest
+import torch
+
+import synthetic as S
+from conftest import rel_l2
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.mark.parametrize("p,m,s,alpha,B,pad", [(2, 10, 4, 2.0, 1, 0), (2, 14, 6, 2.0, 2, 4), (3, 7, 3, 2.0, 1, 0),
+                                              (5, 5, 4, 2.5, 2, 3), (2, 16, 8, 1.7, 3, 0), (7, 4, 3, 2.0, 1, 1)])
+def test_spline_matches_oracle(dwt, dev, orc, p, m, s, alpha, B, pad):
+    N = p ** m
+    ld = N + pad
+    C = S.small_net(p, m, s, index=200 + m)
+    Y = orc.net_points(p, m, C)
+    gamma = 0.9 / np.arange(1, s + 1) ** 1.2
+    coefs = S.uniform(S.stream_seed(60, S.P_COEFFS, m), B * s).reshape(B, s)
+    fs = np.stack([orc.eval_product(p, m, Y, coefs[b]) for b in range(B)])
+    refs = [orc.spline(p, m, Y, fs[b], alpha, gamma) for b in range(B)]
+    K, _, _ = orc.kernel_data(p, m, Y, alpha, gamma)
+    cond = np.abs(K).max() / np.abs(refs[0]["Ktil"].real).min()
+    tol_c = max(1e-11, 1e-15 * cond * 50)
+
+    plan = dwt.dwt_plan_create(p, m, s, C, dwt.DWT_PLAN_TRANSFORM_ONLY)
+    dwt.dwt_spline_prepare(plan, alpha, gamma)
+    f = torch.zeros((B, ld), dtype=torch.float64, device=dev)
+    f[:, :N] = torch.from_numpy(fs)
+    cdt = torch.float64 if p == 2 else torch.complex128
+    c = torch.zeros((B, ld), dtype=cdt, device=dev)
+    vt = torch.empty((B, s + 1), dtype=torch.float64, device=dev)
+    vs = torch.empty((B, s + 1), dtype=torch.float64, device=dev)
+    dim = torch.empty((B, 2), dtype=torch.int32, device=dev)
+    dwt.dwt_spline(plan, f, c, B, ld, vt, vs, dim)
+    cg = c.cpu().numpy()[:, :N]
+    vtg, vsg, dg = vt.cpu().numpy(), vs.cpu().numpy(), dim.cpu().numpy()
+    for b in range(B):
+        r = refs[b]
+        assert rel_l2(cg[b].real, r["c"].real) < tol_c
+        tot = r["var_trc"][-1]
+        assert np.all(np.abs(vtg[b] - r["var_trc"]) <= 1e-9 * tot)
+        assert np.all(np.abs(vsg[b] - r["var_sup"]) <= 1e-9 * tot)
+        for dgot, dref, v in ((dg[b, 0], r["d_trc"], r["var_trc"]), (dg[b, 1], r["d_sup"], r["var_sup"])):
+            if dgot != dref:
+                lo, hi = sorted((dgot, dref))
+                assert all(abs(v[d] / tot - 0.99) < 1e-8 for d in range(lo, hi))
+
+
+def test_spline_needs_prepare(dwt, dev):
+    p, m, s = 2, 8, 3
+    plan = dwt.dwt_plan_create(p, m, s, S.small_net(p, m, s, index=1), dwt.DWT_PLAN_TRANSFORM_ONLY)
+    f = torch.zeros(2 ** m, dtype=torch.float64, device=dev)
+    with pytest.raises(dwt.DwtError):
+        dwt.dwt_spline(plan, f, f.clone(), 1, 2 ** m)
+    with pytest.raises(dwt.DwtError):
+        dwt.dwt_spline_prepare(plan, 1.0, np.ones(s))   # alpha must exceed 1
