@@ -177,7 +177,7 @@ void orc_dwt_direct(int p, int m, const double *fre, const double *fim,
                     const uint32_t *Hsel, long nsel, double *ore, double *oim)
 {
     uint64_t N = ipow_u64(p, m);
-    double cw[8], sw[8];
+    double cw[32], sw[32];
     unit_roots(p, cw, sw);
     long nout = Hsel ? nsel : (long)N;
     for (long t = 0; t < nout; ++t) {
@@ -227,7 +227,7 @@ void orc_dwt_walsh_def(int p, int m, int s, const uint32_t *Y, const double *fre
                        const uint32_t *k, long cnt, double *ore, double *oim)
 {
     uint64_t N = ipow_u64(p, m);
-    double cw[8], sw[8];
+    double cw[32], sw[32];
     unit_roots(p, cw, sw);
     int yd[32], kd[32];
     for (long t = 0; t < cnt; ++t) {
@@ -257,9 +257,9 @@ static void digit_dft(int p, int m, int r, int sgn, double *re, double *im)
 {
     uint64_t N = ipow_u64(p, m);
     uint64_t stride = ipow_u64(p, r);
-    double cw[8], sw[8];
+    double cw[32], sw[32];
     unit_roots(p, cw, sw);
-    double xr[8], xi[8];
+    double xr[32], xi[32];
     for (uint64_t base = 0; base < N; base += stride * (uint64_t)p) {
         for (uint64_t off = 0; off < stride; ++off) {
             uint64_t i0 = base + off;

@@ -617,6 +617,8 @@ int build_coset_tables(dwt_plan_s* Pl, cudaStream_t st) {
         case 3: return small ? coset_tables_small<3>(Pl, st) : coset_tables_p<3>(Pl, st);
         case 5: return small ? coset_tables_small<5>(Pl, st) : coset_tables_p<5>(Pl, st);
         case 7: return small ? coset_tables_small<7>(Pl, st) : coset_tables_p<7>(Pl, st);
+        case 11: return small ? coset_tables_small<11>(Pl, st) : coset_tables_p<11>(Pl, st);
+        case 13: return small ? coset_tables_small<13>(Pl, st) : coset_tables_p<13>(Pl, st);
         default: return DWT_EUNSUPPORTED;
     }
 }
@@ -659,6 +661,8 @@ int run_h_to_k(dwt_plan_s* Pl, const uint32_t* H, uint32_t* k, long long cnt, cu
         case 3: return h_to_k_p<3>(Pl, H, k, cnt, st);
         case 5: return h_to_k_p<5>(Pl, H, k, cnt, st);
         case 7: return h_to_k_p<7>(Pl, H, k, cnt, st);
+        case 11: return h_to_k_p<11>(Pl, H, k, cnt, st);
+        case 13: return h_to_k_p<13>(Pl, H, k, cnt, st);
         default: return DWT_EUNSUPPORTED;
     }
 }
@@ -672,6 +676,8 @@ int run_points(dwt_plan_s* Pl, uint32_t* Y, long long ldY, cudaStream_t st) {
             case 3: k_points<3><<<grid, 256, 0, st>>>(Pl->d_C, Pl->d_col, Pl->m, Pl->N, Y, ldY); break;
             case 5: k_points<5><<<grid, 256, 0, st>>>(Pl->d_C, Pl->d_col, Pl->m, Pl->N, Y, ldY); break;
             case 7: k_points<7><<<grid, 256, 0, st>>>(Pl->d_C, Pl->d_col, Pl->m, Pl->N, Y, ldY); break;
+            case 11: k_points<11><<<grid, 256, 0, st>>>(Pl->d_C, Pl->d_col, Pl->m, Pl->N, Y, ldY); break;
+            case 13: k_points<13><<<grid, 256, 0, st>>>(Pl->d_C, Pl->d_col, Pl->m, Pl->N, Y, ldY); break;
         }
     }
     DWT_CK_LAUNCH("k_points");
@@ -687,6 +693,8 @@ int run_k_to_h(dwt_plan_s* Pl, const uint32_t* k, uint32_t* H, long long cnt, cu
             case 3: k_k_to_h<3><<<g, 256, 0, st>>>(Pl->d_C, Pl->d_R, Pl->m, Pl->s, k, H, cnt); break;
             case 5: k_k_to_h<5><<<g, 256, 0, st>>>(Pl->d_C, Pl->d_R, Pl->m, Pl->s, k, H, cnt); break;
             case 7: k_k_to_h<7><<<g, 256, 0, st>>>(Pl->d_C, Pl->d_R, Pl->m, Pl->s, k, H, cnt); break;
+            case 11: k_k_to_h<11><<<g, 256, 0, st>>>(Pl->d_C, Pl->d_R, Pl->m, Pl->s, k, H, cnt); break;
+            case 13: k_k_to_h<13><<<g, 256, 0, st>>>(Pl->d_C, Pl->d_R, Pl->m, Pl->s, k, H, cnt); break;
         }
     }
     DWT_CK_LAUNCH("k_k_to_h");

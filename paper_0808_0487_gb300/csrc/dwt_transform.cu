@@ -31,8 +31,8 @@ static bool aligned16(const void* p, long long ld, int elem) {
 // ---------------------------------------------------------------------------
 // element helpers
 struct Tw {
-    float c[8], s[8];     // cos, sin of 2 pi e / p
-    double cd[8], sd[8];
+    float c[16], s[16];   // cos, sin of 2 pi e / p, e < p <= 13
+    double cd[16], sd[16];
 };
 
 template <typename T> struct IsCplx : std::false_type {};
@@ -398,7 +398,7 @@ __global__ void k_effdim_finalize(const double* __restrict__ csum, int nb, doubl
 // host side
 static Tw make_tw(int p) {
     Tw t;
-    for (int e = 0; e < 8; ++e) {
+    for (int e = 0; e < 16; ++e) {
         double ang = e < p ? 2.0 * 3.14159265358979323846 * e / p : 0.0;
         t.cd[e] = cos(ang);
         t.sd[e] = sin(ang);
@@ -523,6 +523,8 @@ int run_transform(dwt_plan_s* Pl, const void* in, void* out, int batch, long lon
         case 3: return transform_p<3>(Pl, in, out, batch, ld_in, ld_out, in_t, out_t, sgn, st);
         case 5: return transform_p<5>(Pl, in, out, batch, ld_in, ld_out, in_t, out_t, sgn, st);
         case 7: return transform_p<7>(Pl, in, out, batch, ld_in, ld_out, in_t, out_t, sgn, st);
+        case 11: return transform_p<11>(Pl, in, out, batch, ld_in, ld_out, in_t, out_t, sgn, st);
+        case 13: return transform_p<13>(Pl, in, out, batch, ld_in, ld_out, in_t, out_t, sgn, st);
         default: set_error("unsupported p"); return DWT_EUNSUPPORTED;
     }
 }
@@ -654,6 +656,12 @@ int run_interpolate(dwt_plan_s* Pl, const void* f, void* c, void* coef, int batc
         case 7:
             return f_t == DWT_F32 ? interpolate_t<7, float2, float>(Pl, f, c, coef, batch, ld, weight, var, dim, thr, st)
                                   : interpolate_t<7, float2, float2>(Pl, f, c, coef, batch, ld, weight, var, dim, thr, st);
+        case 11:
+            return f_t == DWT_F32 ? interpolate_t<11, float2, float>(Pl, f, c, coef, batch, ld, weight, var, dim, thr, st)
+                                  : interpolate_t<11, float2, float2>(Pl, f, c, coef, batch, ld, weight, var, dim, thr, st);
+        case 13:
+            return f_t == DWT_F32 ? interpolate_t<13, float2, float>(Pl, f, c, coef, batch, ld, weight, var, dim, thr, st)
+                                  : interpolate_t<13, float2, float2>(Pl, f, c, coef, batch, ld, weight, var, dim, thr, st);
         default: set_error("unsupported p"); return DWT_EUNSUPPORTED;
     }
 }

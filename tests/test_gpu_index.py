@@ -25,7 +25,7 @@ def _read_tables(dwt, plan, N):
     return W, cls
 
 
-NETS = [("pr1", 2, 12, 4), ("p3", 3, 6, 4), ("p5", 5, 4, 3), ("p7", 7, 3, 3)]
+NETS = [("pr1", 2, 12, 4), ("p3", 3, 6, 4), ("p5", 5, 4, 3), ("p7", 7, 3, 3), ("p11", 11, 3, 3), ("p13", 13, 3, 2)]
 
 
 def _net(name, p, m, s):
@@ -73,7 +73,8 @@ def test_tables_bit_exact(dwt, dev, orc, name, p, m, s):
     assert np.array_equal(cls, ref["cls"])
 
 
-@pytest.mark.parametrize("p,m,s,idx", [(2, 3, 3, 1), (2, 4, 2, 2), (3, 2, 3, 1), (5, 1, 3, 2), (3, 3, 2, 3), (2, 2, 4, 1)])
+@pytest.mark.parametrize("p,m,s,idx", [(2, 3, 3, 1), (2, 4, 2, 2), (3, 2, 3, 1), (5, 1, 3, 2), (3, 3, 2, 3), (2, 2, 4, 1),
+                                       (11, 1, 3, 1), (13, 1, 2, 2)])
 def test_dense_nets_vs_bruteforce(dwt, dev, orc, p, m, s, idx):
     C = S.dense_matrices(p, m, s, index=idx)
     st, kmap = orc.coset_leaders_bruteforce(p, m, C)

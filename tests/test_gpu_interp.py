@@ -76,9 +76,14 @@ def test_interpolate_m20_batch(dwt, dev, orc):
         _check_dims(dg[b], dt, ds, vt, vs)
 
 
-def test_interpolate_p3_m13(dwt, dev, orc):
-    w = S.workload_p3_m13()
-    p, m, s, C = w["p"], w["m"], w["s"], w["C"]
+@pytest.mark.parametrize("which", ["p3_m13", "p11_m4", "p13_m4"])
+def test_interpolate_p_odd(dwt, dev, orc, which):
+    if which == "p3_m13":
+        w = S.workload_p3_m13()
+        p, m, s, C = w["p"], w["m"], w["s"], w["C"]
+    else:
+        p, m, s = (11, 4, 5) if which == "p11_m4" else (13, 4, 3)
+        C = S.small_net(p, m, s, index=90 + p)
     N = p ** m
     plan = dwt.dwt_plan_create(p, m, s, C)
     f = orc.eval_exp(p, m, orc.net_points(p, m, C))
@@ -98,7 +103,7 @@ def test_interpolate_p3_m13(dwt, dev, orc):
     _check_dims(_np(dim)[0], dt, ds, vt, vs)
 
 
-@pytest.mark.parametrize("p,m,s", [(2, 12, 4), (5, 5, 3), (7, 4, 6)])
+@pytest.mark.parametrize("p,m,s", [(2, 12, 4), (5, 5, 3), (7, 4, 6), (11, 3, 4), (13, 3, 3)])
 def test_effdim_standalone(dwt, dev, orc, p, m, s):
     C = S.workload_pr1()["C"] if p == 2 else S.small_net(p, m, s, index=5)
     N = p ** m

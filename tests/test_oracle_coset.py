@@ -19,7 +19,8 @@ def _nu(kv, p):
     return sum(_nu1(int(k), p) for k in kv)
 
 
-TINY = [(2, 3, 3), (2, 4, 2), (3, 2, 3), (3, 2, 2), (2, 2, 4), (5, 1, 3), (3, 3, 2), (5, 2, 2), (2, 3, 4)]
+TINY = [(2, 3, 3), (2, 4, 2), (3, 2, 3), (3, 2, 2), (2, 2, 4), (5, 1, 3), (3, 3, 2), (5, 2, 2), (2, 3, 4),
+        (11, 1, 3), (13, 1, 2), (7, 2, 2)]
 
 
 @pytest.mark.parametrize("p,m,s", TINY)

@@ -15,7 +15,7 @@ def _data(p, m, idx=0, cplx=False):
     return v[:N] + 1j * v[N:] if cplx else v[:N]
 
 
-@pytest.mark.parametrize("p,m", [(2, 9), (3, 5), (5, 3), (2, 1), (3, 1)])
+@pytest.mark.parametrize("p,m", [(2, 9), (3, 5), (5, 3), (2, 1), (3, 1), (11, 2), (13, 2), (11, 1)])
 def test_fwt_matches_direct_sum(orc, p, m):
     f = _data(p, m, cplx=p > 2)
     a = orc.fwt(p, m, f)
@@ -32,7 +32,7 @@ def test_p2_is_sylvester_hadamard(orc, m):
     assert np.abs(orc.fwt(2, m, f) - ref).max() < 1e-14
 
 
-@pytest.mark.parametrize("p,m", [(3, 6), (5, 4), (3, 2)])
+@pytest.mark.parametrize("p,m", [(3, 6), (5, 4), (3, 2), (11, 3), (13, 2)])
 def test_p_odd_is_multidimensional_dft(orc, p, m):
     """F_p^{(x)m} with omega^{-nh}: numpy's forward FFT over an m-axis p x ... x p array."""
     f = _data(p, m, 2, cplx=True)
@@ -40,7 +40,7 @@ def test_p_odd_is_multidimensional_dft(orc, p, m):
     assert np.abs(orc.fwt(p, m, f) - ref).max() < 1e-14
 
 
-@pytest.mark.parametrize("p,m", [(2, 12), (3, 7), (5, 5)])
+@pytest.mark.parametrize("p,m", [(2, 12), (3, 7), (5, 5), (11, 3), (13, 3)])
 def test_inverse_is_identity_and_lemma(orc, p, m):
     """Lemma 3.1 / Alg. 2: c_n = sum_H c~(H) omega^{n.h}; forward then inverse is the identity."""
     f = _data(p, m, 3, cplx=p > 2)
