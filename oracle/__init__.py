@@ -62,6 +62,8 @@ def lib():
         L.orc_rprime.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_uint32]
         L.orc_rprime.restype = ctypes.c_double
         L.orc_kernel_data.argtypes = [ctypes.c_int] * 3 + [_u32p, ctypes.c_double, _f64p, _f64p, _f64p, _f64p]
+        L.orc_kernel_shift_data.argtypes = [ctypes.c_int] * 3 + [_u32p, _u32p, ctypes.c_int, ctypes.c_double, _f64p,
+                                                                  _f64p]
         _lib = L
     return _lib
 
@@ -310,6 +312,23 @@ def spline(p, m, Y, f, alpha, gamma, thr=0.99):
         vs[d] = vs[d - 1] + N * N * float(np.dot(a, fwt(p, m, E[d - 1]).real))
     dt, ds = effdim_threshold(vt, vs, thr)
     return dict(Ktil=Kt, W=W, ctil=ct, c=c, var_trc=vt, var_sup=vs, d_trc=dt, d_sup=ds)
+
+
+def spline_values_shifted(p, m, Y, c, delta, M, alpha, gamma):
+    """Values of the spline Sf(x) = sum_v c_v K(x (-) x_v, 0) at the shifted points
+    x_n (+) delta, n = 0..N-1, delta_j = delta[j] / p^M (M >= m digits).  As a
+    function of n this is a convolution over the net: its DWT is
+    p^m c~(H) k~(H), k~ the DWT of the shifted kernel data K(x_w (+) delta, 0);
+    FIWT (Algorithm 2) gives the values."""
+    Y = np.ascontiguousarray(Y, dtype=np.uint32)
+    s, N = Y.shape
+    D = np.ascontiguousarray(delta, dtype=np.uint32)
+    g = np.ascontiguousarray(gamma, dtype=np.float64)
+    Kd = np.empty(N)
+    lib().orc_kernel_shift_data(p, m, s, _p(Y, _u32p), _p(D, _u32p), M, alpha, _p(g, _f64p), _p(Kd, _f64p))
+    kt = fwt(p, m, Kd)
+    ct = fwt(p, m, c)
+    return fiwt(p, m, N * ct * kt)
 
 
 # --- synthetic test functions ------------------------------------------------

@@ -762,3 +762,27 @@ void orc_kernel_data(int p, int m, int s, const uint32_t *Y, double alpha, const
     }
     free(e);
 }
+
+/* Kernel data at digitally shifted points (Sec. 3.1 and 5.1): for w = 0..N-1,
+ * Kd[w] = prod_j (1 + gamma_j K'(x_{j,w} (+) delta_j, 0)), where x_{j,w} = Y/p^m has
+ * m digits, delta_j = D[j] / p^M has M >= m digits, and (+) adds digits mod p.  */
+void orc_kernel_shift_data(int p, int m, int s, const uint32_t *Y, const uint32_t *D, int M, double alpha,
+                           const double *gamma, double *Kd)
+{
+    uint64_t N = ipow_u64(p, m);
+    uint64_t up = ipow_u64(p, M - m);
+    for (uint64_t w = 0; w < N; ++w) {
+        double kv = 1.0;
+        for (int j = 0; j < s; ++j) {
+            uint64_t a = (uint64_t)Y[(size_t)j * N + w] * up, b = D[j], y = 0, pw = 1;
+            for (int c = 0; c < M; ++c) {            /* digit-wise sum mod p of the M-digit numerators */
+                y += ((a % (uint64_t)p + b % (uint64_t)p) % (uint64_t)p) * pw;
+                a /= (uint64_t)p;
+                b /= (uint64_t)p;
+                pw *= (uint64_t)p;
+            }
+            kv *= 1.0 + gamma[j] * orc_kprime(p, M, alpha, (uint32_t)y);
+        }
+        Kd[w] = kv;
+    }
+}

@@ -109,3 +109,36 @@ def test_variances_equal_double_sums(orc, p, m, s, alpha):
     assert np.allclose(r["var_sup"], vs, rtol=1e-9, atol=1e-12 * tot)
     dt, ds = orc.effdim_threshold(np.array(vt), np.array(vs))
     assert (r["d_trc"], r["d_sup"]) == (dt, ds)
+
+
+def _dadd(a, b, p, M):
+    return sum(((((a // p ** i) % p) + ((b // p ** i) % p)) % p) * p ** i for i in range(M))
+
+
+@pytest.mark.parametrize("p,m,s,M", [(2, 5, 3, 6), (2, 4, 2, 7), (3, 3, 2, 4), (5, 2, 3, 3), (2, 5, 3, 5)])
+def test_spline_values_at_shifted_points(orc, p, m, s, M):
+    """Sf(x_n (+) delta) by the DWT route against the direct sum over the net, with
+    K(x (-) x_v, 0) from the short form on M digits; delta with M digits (for
+    p = 2, M = m + 1 is the second half of a 2^(m+1)-point net)."""
+    C = S.small_net(p, m, s, index=120 + m)
+    Y = orc.net_points(p, m, C)
+    gamma = 0.7 / np.arange(1, s + 1)
+    alpha = 2.0
+    f = orc.eval_product(p, m, Y, 0.4 + 0.1 * np.arange(s))
+    c = orc.spline(p, m, Y, f, alpha, gamma)["c"].real
+    delta = S.integers(S.stream_seed(61, S.P_SAMPLE, m), s, 0, p ** M - 1).astype(np.uint32)
+    got = orc.spline_values_shifted(p, m, Y, c, delta, M, alpha, gamma)
+    N = p ** m
+    up = p ** (M - m)
+    ref = np.zeros(N)
+    for n in range(N):
+        for v in range(N):
+            k = 1.0
+            for j in range(s):
+                xs = _dadd(int(Y[j, n]) * up, int(delta[j]), p, M)
+                k *= 1.0 + gamma[j] * orc.kprime(p, M, alpha, _dsub(xs, int(Y[j, v]) * up, p, M))
+            ref[n] += c[v] * k
+    assert np.allclose(got.real, ref, rtol=1e-10, atol=1e-12 * np.abs(ref).max())
+    assert np.abs(got.imag).max() < 1e-10 * np.abs(ref).max()
+    if np.all(delta == 0):
+        assert np.allclose(got.real, f, rtol=1e-10)   # interpolation at the net itself
