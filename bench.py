@@ -296,9 +296,20 @@ def run_other_configs(dwt, dev, stream, timed, steps):
         dwt.dwt_spline(plan2, fs, cs, 32, N2, vts, vss, dims, stream=stream)
 
     ms_s, _ = timed(spl, steps)
+    # values at the net shifted by one point of the finer net (the hold-out half
+    # of a 2N-point net) and the squared error against the function there
+    delta = [int(S.integers(S.stream_seed(2, S.P_SAMPLE, j), 1, 0, (1 << 21) - 1)[0]) | 1 for j in range(16)]
+    vals = torch.empty_like(fs)
+    sse = torch.empty(32, dtype=torch.float64, device=dev)
+
+    def hold():
+        dwt.dwt_spline_values_shifted(plan2, cs, delta, 21, vals, 32, N2, fs, sse, stream=stream)
+
+    ms_h, _ = timed(hold, steps)
     out["spline_p2_m20_s16_b32"] = {"points_per_s": 32 * N2 * steps / (ms_s / 1e3), "dtype": "f64",
-                                    "alpha": 2.0, "gamma": "0.9 / j^1.2"}
-    del fs, cs
+                                    "alpha": 2.0, "gamma": "0.9 / j^1.2",
+                                    "holdout_points_per_s": 32 * N2 * steps / (ms_h / 1e3)}
+    del fs, cs, vals
     w = S.workload_p3_m13()
     p, m, s = w["p"], w["m"], w["s"]
     N = p ** m

@@ -230,6 +230,26 @@ int dwt_spline(dwt_plan_t plan, const double *f, void *c, int batch, long long l
                double *var_sup, int *dim, double threshold, void *stream);
 
 /*
+ * Values of the spline Sf(x) = sum_v c_v K(x (-) x_v, 0) at the digitally
+ * shifted points x_n (+) delta, n = 0..N-1 (Sec. 3.1; for p = 2 and
+ * delta = x_N of a 2N-point net whose halves are nets these are the hold-out
+ * points of the cost function of Sec. 5.1).  As a function of n the values are
+ * a convolution over the net, so their DWT is p^m c~ k~ with k~ the DWT of the
+ * shifted kernel data K(x_w (+) delta, 0): O(N log N) per function.
+ *   c: device spline coefficients [batch][ld] from dwt_spline (double for
+ *      p = 2, complex double for p > 2);
+ *   delta: host uint32 [s], delta_j = delta[j] / p^M, with m <= M and
+ *      p^M <= 2^32 (M = m + 1 for the second half of a 2N-point net);
+ *   values: device output [batch][ld], same type as c;
+ *   f_shift, sse: optional; with both, sse[b] (device double [batch]) =
+ *      sum_n (f_shift[b][n] - Re values[b][n])^2, f_shift device double [batch][ld]
+ *      (the function at the shifted points): the cost of eq. splineCostFunc.
+ * Uses the kernel of the last dwt_spline_prepare (DWT_EINVAL without one).
+ */
+int dwt_spline_values_shifted(dwt_plan_t plan, const void *c, const uint32_t *delta, int M, void *values,
+                              int batch, long long ld, const double *f_shift, double *sse, void *stream);
+
+/*
  * Effective dimension of given coefficients g (Sec. 4), the variance and
  * threshold part of dwt_interpolate alone.  coef: device, type DWT_F32
  * (p = 2) or DWT_C64, ld elements per function.  var/dim as above (device).

@@ -78,6 +78,7 @@ _SIGS = {
     "dwt_interpolate_host": (_I, [_VP, _VP, _VP, _I, _LL, _I, _I, _VP, _VP, ctypes.c_double, _VP]),
     "dwt_spline_prepare": (_I, [_VP, ctypes.c_double, _VP, _VP]),
     "dwt_spline": (_I, [_VP, _VP, _VP, _I, _LL, _VP, _VP, _VP, ctypes.c_double, _VP]),
+    "dwt_spline_values_shifted": (_I, [_VP, _VP, _VP, _I, _VP, _I, _LL, _VP, _VP, _VP]),
     "dwt_effdim": (_I, [_VP, _VP, _I, _LL, _I, _VP, _VP, ctypes.c_double, _VP]),
     "dwt_effdim_static": (_I, [_VP, _VP, _I, _LL, _I, _VP, _VP, ctypes.c_double, _VP]),
     "dwt_eval_product": (_I, [_VP, _VP, _VP, _I, _LL, _I, _VP]),
@@ -256,6 +257,13 @@ def dwt_spline(plan, f, c, batch, ld, var_trc=None, var_sup=None, dim=None, thre
     """Spline coefficients c_n of f (FP64) and the ANOVA variances of the spline."""
     return _check(lib().dwt_spline(plan.handle, _ptr(f), _ptr(c), batch, ld, _ptr(var_trc), _ptr(var_sup),
                                    _ptr(dim), threshold, _stream(stream)))
+
+
+def dwt_spline_values_shifted(plan, c, delta, M, values, batch, ld, f_shift=None, sse=None, stream=None):
+    """Spline values at the net shifted by delta (host uint32 [s], M digits); optional hold-out error."""
+    d = np.ascontiguousarray(delta, dtype=np.uint32)
+    return _check(lib().dwt_spline_values_shifted(plan.handle, _ptr(c), d.ctypes.data, int(M), _ptr(values), batch, ld,
+                                                  _ptr(f_shift), _ptr(sse), _stream(stream)))
 
 
 def dwt_effdim(plan, coef, batch, ld, t, var=None, dim=None, threshold=0.99, stream=None):

@@ -533,6 +533,16 @@ int dwt_spline_prepare(dwt_plan_t P, double alpha, const double* gamma, void* st
     return run_spline_prepare(P, alpha, gamma, (cudaStream_t)stream);
 }
 
+int dwt_spline_values_shifted(dwt_plan_t P, const void* c, const uint32_t* delta, int M, void* values, int batch,
+                              long long ld, const double* f_shift, double* sse, void* stream) {
+    if (!P || !delta || batch < 0 || (batch > 0 && (!c || !values)) || ld < P->N) {
+        set_error("dwt_spline_values_shifted: bad arguments");
+        return DWT_EINVAL;
+    }
+    if (batch == 0) return DWT_OK;
+    return run_spline_shifted(P, c, delta, M, values, batch, ld, f_shift, sse, (cudaStream_t)stream);
+}
+
 int dwt_spline(dwt_plan_t P, const double* f, void* c, int batch, long long ld, double* var_trc, double* var_sup,
                int* dim, double thr, void* stream) {
     if (!P || batch < 0 || (batch > 0 && !f) || ld < P->N || !(thr > 0.0 && thr <= 1.0)) {

@@ -93,6 +93,8 @@ struct dwt_plan_s {
     // kernel spline tables (dwt_spline_prepare): W_K [N], then R~_d - [H=0] and E~_j, [2s][N], FP64
     double* d_splW = nullptr;
     double* d_splT = nullptr;
+    double spl_alpha = 0.0;           // the kernel's parameters, kept for evaluations
+    std::vector<double> spl_gamma;
 };
 
 namespace dwt {
@@ -130,6 +132,8 @@ int run_spline_prepare(dwt_plan_s* P, double alpha, const double* gamma, cudaStr
 int run_spline(dwt_plan_s* P, const double* f, void* c, int batch, long long ld, double* var_trc, double* var_sup,
                int* dim, double thr, cudaStream_t st);
 void spline_free(dwt_plan_s* P, cudaStream_t st, bool sync);
+int run_spline_shifted(dwt_plan_s* P, const void* c, const uint32_t* delta, int M, void* values, int batch,
+                       long long ld, const double* f_shift, double* sse, cudaStream_t st);
 int run_points(dwt_plan_s* P, uint32_t* Y, long long ldY, cudaStream_t st);
 int run_k_to_h(dwt_plan_s* P, const uint32_t* k, uint32_t* H, long long cnt, cudaStream_t st);
 int run_h_to_k(dwt_plan_s* P, const uint32_t* H, uint32_t* k, long long cnt, cudaStream_t st);

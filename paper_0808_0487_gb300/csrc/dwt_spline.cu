@@ -177,6 +177,93 @@ __global__ void k_spline_finalize(const double* __restrict__ part, long long nti
     }
 }
 
+// kernel data at the shifted points: Kd[w] = prod_j (1 + gamma_j K'(x_{j,w} (+) delta_j, 0)),
+// x_{j,w} with m digits, delta_j = D[j] / p^M with M digits; kpM[i] = K' for a first
+// nonzero digit at position i of M (kpM[0] = 1)
+__global__ void k_spline_shift_data(const uint32_t* __restrict__ Y, long long N, int s, int p, int m, int M,
+                                    const uint32_t* __restrict__ D, const double* __restrict__ kpM,
+                                    const double* __restrict__ gam, double* Kd) {
+    unsigned long long up = 1;
+    for (int i = m; i < M; ++i) up *= (unsigned long long)p;
+    for (long long w = blockIdx.x * (long long)blockDim.x + threadIdx.x; w < N; w += (long long)gridDim.x * blockDim.x) {
+        double kv = 1.0;
+        for (int j = 0; j < s; ++j) {
+            unsigned long long a = (unsigned long long)Y[(long long)j * N + w] * up, b = D[j], y;
+            if (p == 2) {
+                y = a ^ b;
+            } else {
+                y = 0;
+                unsigned long long pw = 1;
+                for (int c = 0; c < M; ++c) {
+                    y += ((a % p + b % p) % p) * pw;
+                    a /= p;
+                    b /= p;
+                    pw *= p;
+                }
+            }
+            int i = 0;
+            if (y) {
+                int t = 0;
+                while (y >= (unsigned long long)p) {
+                    y /= p;
+                    ++t;
+                }
+                i = M - t;
+            }
+            kv *= 1.0 + gam[j] * kpM[i];
+        }
+        Kd[w] = kv;
+    }
+}
+
+// g~ = N c~ k~ in place in c~ (real, or interleaved complex with k~ complex)
+__global__ void k_spline_conv(double* ct, const double* __restrict__ kt, int cplx, long long N, long long total) {
+    const double n = (double)N;
+    for (long long x = blockIdx.x * (long long)blockDim.x + threadIdx.x; x < total;
+         x += (long long)gridDim.x * blockDim.x) {
+        const long long H = x % N;
+        if (cplx) {
+            const double ar = ct[2 * x], ai = ct[2 * x + 1], br = kt[2 * H], bi = kt[2 * H + 1];
+            ct[2 * x] = n * (ar * br - ai * bi);
+            ct[2 * x + 1] = n * (ar * bi + ai * br);
+        } else {
+            ct[x] *= n * kt[H];
+        }
+    }
+}
+
+// per-block partial sums of (f - Re v)^2 over a tile of points; part[b * ntile + tile]
+__global__ void __launch_bounds__(256) k_spline_sse(const double* __restrict__ f, const double* __restrict__ v,
+                                                    int cplx, long long N, long long ld, double* part,
+                                                    long long ntile) {
+    __shared__ double red[256];
+    const long long tile = blockIdx.x, b = blockIdx.y;
+    double acc = 0.0;
+    for (int q = 0; q < kDotTile / 256; ++q) {
+        const long long n = tile * kDotTile + threadIdx.x + 256 * q;
+        if (n < N) {
+            const long long x = b * ld + n;
+            const double d = f[x] - (cplx ? v[2 * x] : v[x]);
+            acc += d * d;
+        }
+    }
+    red[threadIdx.x] = acc;
+    __syncthreads();
+    for (int w = 128; w > 0; w >>= 1) {
+        if (threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) part[b * ntile + tile] = red[0];
+}
+
+__global__ void k_spline_sse_final(const double* __restrict__ part, long long ntile, int batch, double* sse) {
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= batch) return;
+    double x = 0.0;
+    for (long long i = 0; i < ntile; ++i) x += part[(long long)b * ntile + i];
+    sse[b] = x;
+}
+
 unsigned grid_sp(long long n) { return (unsigned)std::max(1ll, std::min((n + 255) / 256, 8ll * 152)); }
 
 }  // namespace
@@ -241,6 +328,8 @@ int run_spline_prepare(dwt_plan_s* P, double alpha, const double* gamma, cudaStr
     rc2 = run_transform(P, data, tr, rows, N, N, DWT_F64, cplx ? DWT_C128 : DWT_F64, -1, st);
     if (rc2) { cleanup(); return rc2; }
     spline_free(P, st, false);
+    P->spl_alpha = alpha;
+    P->spl_gamma.assign(gamma, gamma + s);
     if (dmalloc((void**)&P->d_splW, (size_t)N * 8, st) || dmalloc((void**)&P->d_splT, (size_t)2 * s * N * 8, st)) {
         spline_free(P, st, false);
         cleanup();
@@ -251,6 +340,80 @@ int run_spline_prepare(dwt_plan_s* P, double alpha, const double* gamma, cudaStr
         k_spline_tables<<<grid_sp((long long)rows * N), 256, 0, st>>>(tr, cplx ? 1 : 0, N, s, P->d_splW, P->d_splT);
     }
     DWT_CK_LAUNCH("k_spline_tables");
+    cleanup();
+    return DWT_OK;
+}
+
+int run_spline_shifted(dwt_plan_s* P, const void* c, const uint32_t* delta, int M, void* values, int batch,
+                       long long ld, const double* f_shift, double* sse, cudaStream_t st) {
+    if (!P->d_splW) {
+        set_error("dwt_spline_values_shifted: no kernel tables (call dwt_spline_prepare first)");
+        return DWT_EINVAL;
+    }
+    const long long N = P->N;
+    const int s = P->s, p = P->p, m = P->m;
+    if (M < m || (double)M * std::log2((double)p) > 32.0) {
+        set_error("dwt_spline_values_shifted: need m <= M and p^M <= 2^32");
+        return DWT_EINVAL;
+    }
+    const bool cplx = p != 2;
+    const size_t eb = cplx ? 16 : 8;
+    // K'(y, 0) on M digits by the first nonzero digit, and the kernel weights
+    const double alpha = P->spl_alpha;
+    const double pa = std::pow((double)p, alpha);
+    std::vector<double> hv((size_t)M + 1 + s);
+    for (int i = 0; i <= M; ++i)
+        hv[i] = i == 0 ? 1.0 : 1.0 - std::pow((double)p, i * (1.0 - alpha)) * (pa - 1.0) / (p - 1.0);
+    for (int j = 0; j < s; ++j) hv[M + 1 + j] = P->spl_gamma[j];
+    uint32_t *Y = nullptr, *dD = nullptr;
+    double *dv = nullptr, *kd = nullptr, *kt = nullptr, *ct = nullptr, *part = nullptr;
+    auto cleanup = [&]() {
+        dfree(Y, st); dfree(dD, st); dfree(dv, st); dfree(kd, st); dfree(kt, st); dfree(ct, st); dfree(part, st);
+    };
+    const long long ntile = (N + kDotTile - 1) / kDotTile;
+    if (dmalloc((void**)&Y, (size_t)s * N * 4, st) || dmalloc((void**)&dD, (size_t)s * 4, st) ||
+        dmalloc((void**)&dv, hv.size() * 8, st) || dmalloc((void**)&kd, (size_t)N * 8, st) ||
+        dmalloc((void**)&kt, (size_t)N * eb, st) || dmalloc((void**)&ct, (size_t)batch * N * eb, st) ||
+        (sse && f_shift && dmalloc((void**)&part, (size_t)batch * ntile * 8, st))) {
+        cleanup();
+        return DWT_ENOMEM;
+    }
+    DWT_CK(cudaMemcpyAsync(dv, hv.data(), hv.size() * 8, cudaMemcpyHostToDevice, st));
+    DWT_CK(cudaMemcpyAsync(dD, delta, (size_t)s * 4, cudaMemcpyHostToDevice, st));
+    int rc = run_points(P, Y, N, st);
+    if (rc) { cleanup(); return rc; }
+    {
+        LaunchScope ls("spline_shift_data", st);
+        k_spline_shift_data<<<grid_sp(N), 128, 0, st>>>(Y, N, s, p, m, M, dD, dv, dv + M + 1, kd);
+    }
+    DWT_CK_LAUNCH("k_spline_shift_data");
+    const dwt_dtype ct_t = cplx ? DWT_C128 : DWT_F64;
+    if ((rc = run_transform(P, kd, kt, 1, N, N, DWT_F64, ct_t, -1, st)) ||
+        (rc = run_transform(P, c, ct, batch, ld, N, ct_t, ct_t, -1, st))) {
+        cleanup();
+        return rc;
+    }
+    {
+        LaunchScope ls("spline_conv", st);
+        k_spline_conv<<<grid_sp((long long)batch * N), 256, 0, st>>>(ct, kt, cplx ? 1 : 0, N, (long long)batch * N);
+    }
+    DWT_CK_LAUNCH("k_spline_conv");
+    if ((rc = run_transform(P, ct, values, batch, N, ld, ct_t, ct_t, +1, st))) {
+        cleanup();
+        return rc;
+    }
+    if (sse && f_shift) {
+        for (int b0 = 0; b0 < batch; b0 += 65535) {
+            const int nb = std::min(65535, batch - b0);
+            LaunchScope ls("spline_sse", st);
+            k_spline_sse<<<dim3((unsigned)ntile, (unsigned)nb), 256, 0, st>>>(
+                f_shift + (size_t)b0 * ld, reinterpret_cast<const double*>(values) + (size_t)b0 * ld * (eb / 8),
+                cplx ? 1 : 0, N, ld, part + (size_t)b0 * ntile, ntile);
+        }
+        LaunchScope ls("spline_sse", st);
+        k_spline_sse_final<<<(batch + 127) / 128, 128, 0, st>>>(part, ntile, batch, sse);
+    }
+    DWT_CK_LAUNCH("k_spline_sse");
     cleanup();
     return DWT_OK;
 }

@@ -59,3 +59,38 @@ def test_spline_needs_prepare(dwt, dev):
         dwt.dwt_spline(plan, f, f.clone(), 1, 2 ** m)
     with pytest.raises(dwt.DwtError):
         dwt.dwt_spline_prepare(plan, 1.0, np.ones(s))   # alpha must exceed 1
+
+
+@pytest.mark.parametrize("p,m,s,M,B", [(2, 10, 4, 11, 2), (2, 14, 5, 15, 1), (3, 6, 3, 7, 1), (5, 4, 3, 6, 2),
+                                       (2, 12, 3, 12, 1)])
+def test_spline_values_shifted(dwt, dev, orc, p, m, s, M, B):
+    """Values at x_n (+) delta and the hold-out squared error, against the oracle's DWT
+    route (itself pinned by the direct kernel sum)."""
+    N = p ** m
+    C = S.small_net(p, m, s, index=210 + m)
+    Y = orc.net_points(p, m, C)
+    gamma = 0.8 / np.arange(1, s + 1)
+    alpha = 2.0
+    coefs = S.uniform(S.stream_seed(62, S.P_COEFFS, m), B * s).reshape(B, s)
+    fs = np.stack([orc.eval_product(p, m, Y, coefs[b]) for b in range(B)])
+    delta = S.integers(S.stream_seed(63, S.P_SAMPLE, m), s, 0, p ** M - 1).astype(np.uint32)
+    K, _, _ = orc.kernel_data(p, m, Y, alpha, gamma)
+    plan = dwt.dwt_plan_create(p, m, s, C, dwt.DWT_PLAN_TRANSFORM_ONLY)
+    dwt.dwt_spline_prepare(plan, alpha, gamma)
+    cdt = torch.float64 if p == 2 else torch.complex128
+    f = torch.from_numpy(fs).to(dev)
+    c = torch.empty((B, N), dtype=cdt, device=dev)
+    dwt.dwt_spline(plan, f, c, B, N)
+    vals = torch.empty_like(c)
+    fshift = torch.from_numpy(fs[::-1].copy()).to(dev)   # any data at the shifted points
+    sse = torch.empty(B, dtype=torch.float64, device=dev)
+    dwt.dwt_spline_values_shifted(plan, c, delta, M, vals, B, N, fshift, sse)
+    vg = vals.cpu().numpy()
+    ref0 = orc.spline(p, m, Y, fs[0], alpha, gamma)
+    tol = max(1e-10, 1e-15 * 50 * np.abs(K).max() / np.abs(ref0["Ktil"].real).min())
+    for b in range(B):
+        cref = orc.spline(p, m, Y, fs[b], alpha, gamma)["c"].real
+        ref = orc.spline_values_shifted(p, m, Y, cref, delta, M, alpha, gamma).real
+        assert rel_l2(vg[b].real, ref) < tol
+        err = float(((fs[::-1][b] - ref) ** 2).sum())
+        assert sse.cpu().numpy()[b] == pytest.approx(err, rel=max(1e-8, 10 * tol), abs=1e-14)
