@@ -296,6 +296,14 @@ def run_other_configs(dwt, dev, stream, timed, steps):
         dwt.dwt_spline(plan2, fs, cs, 32, N2, vts, vss, dims, stream=stream)
 
     ms_s, _ = timed(spl, steps)
+    # the variance contraction reads |c~|^2 and the 2s tables once per function
+    dwt.dwt_profile_reset()
+    dwt.dwt_profile_enable(True)
+    timed(spl, 1)
+    dwt.dwt_profile_enable(False)
+    nd, td = dwt.dwt_profile_query("spline_dots")
+    dwt.dwt_profile_reset()
+    dots_gbs = (2 * 16 + 1) * N2 * 8 * 32 / (td / max(nd, 1) / 1e3) / 1e9 if nd else None
     # values at the net shifted by one point of the finer net (the hold-out half
     # of a 2N-point net) and the squared error against the function there
     delta = [int(S.integers(S.stream_seed(2, S.P_SAMPLE, j), 1, 0, (1 << 21) - 1)[0]) | 1 for j in range(16)]
@@ -308,7 +316,9 @@ def run_other_configs(dwt, dev, stream, timed, steps):
     ms_h, _ = timed(hold, steps)
     out["spline_p2_m20_s16_b32"] = {"points_per_s": 32 * N2 * steps / (ms_s / 1e3), "dtype": "f64",
                                     "alpha": 2.0, "gamma": "0.9 / j^1.2",
-                                    "holdout_points_per_s": 32 * N2 * steps / (ms_h / 1e3)}
+                                    "holdout_points_per_s": 32 * N2 * steps / (ms_h / 1e3),
+                                    "dots_kernel": {"achieved_gbs": dots_gbs, "bytes_per_point": (2 * 16 + 1) * 8,
+                                                    "frac": dots_gbs / _peaks()[0] if dots_gbs else None}}
     del fs, cs, vals
     w = S.workload_p3_m13()
     p, m, s = w["p"], w["m"], w["s"]

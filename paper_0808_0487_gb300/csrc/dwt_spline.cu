@@ -100,11 +100,14 @@ __global__ void k_spline_scale(double* ft, int cplx, long long N, long long tota
 }
 
 // partial sums of |c~(H)|^2 T_t(H) over one tile of labels, for all 2s tables:
-// part[(b * 2s + t) * ntile + tile]; per thread in label order, then a fixed tree
+// part[(b * 2s + t) * ntile + tile]; per thread in label order, then a fixed
+// tree.  Consecutive blocks take the same tile for consecutive functions, so a
+// tile's table rows come from HBM once and from L2 for the other functions.
 __global__ void __launch_bounds__(256) k_spline_dots(const double* __restrict__ ct, int cplx, long long N, int nt,
-                                                     const double* __restrict__ tab, double* part, long long ntile) {
+                                                     const double* __restrict__ tab, double* part, long long ntile,
+                                                     long long tile0) {
     __shared__ double red[256];
-    const long long tile = blockIdx.x, b = blockIdx.y;
+    const long long tile = tile0 + blockIdx.y, b = blockIdx.x;
     const long long h0 = tile * kDotTile;
     const int t = threadIdx.x;
     constexpr int PER = kDotTile / 256;
@@ -452,10 +455,12 @@ int run_spline(dwt_plan_s* P, const double* f, void* c, int batch, long long ld,
     if (want_var) {
         for (int b0 = 0; b0 < batch; b0 += 65535) {
             const int nb = std::min(65535, batch - b0);
-            LaunchScope ls("spline_dots", st);
-            k_spline_dots<<<dim3((unsigned)ntile, (unsigned)nb), 256, 0, st>>>(
-                ft + (size_t)b0 * N * (eb / 8), cplx ? 1 : 0, N, 2 * s, P->d_splT, part + (size_t)b0 * 2 * s * ntile,
-                ntile);
+            for (long long t0 = 0; t0 < ntile; t0 += 65535) {
+                LaunchScope ls("spline_dots", st);
+                k_spline_dots<<<dim3((unsigned)nb, (unsigned)std::min(65535ll, ntile - t0)), 256, 0, st>>>(
+                    ft + (size_t)b0 * N * (eb / 8), cplx ? 1 : 0, N, 2 * s, P->d_splT, part + (size_t)b0 * 2 * s * ntile,
+                    ntile, t0);
+            }
         }
         DWT_CK_LAUNCH("k_spline_dots");
     }
