@@ -102,16 +102,10 @@ __device__ __forceinline__ void st16(T* p, const V* v2) {
     *reinterpret_cast<typename P2<T>::v4*>(p) = x;
 }
 
-__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
-    const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(sa), "l"(gmem) : "memory");
-}
 // bulk prefetch of [p, p + bytes) from global memory into L2 (bytes a multiple of 16)
 __device__ __forceinline__ void prefetch_l2(const void* p, unsigned bytes) {
     asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
 }
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
-__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
 
 // ---------------------------------------------------------------------------
 // low pass: tile of 2^L contiguous elements.  Every shared-memory access moves
@@ -211,56 +205,6 @@ __global__ void __launch_bounds__(1 << (L - 6), (L == 14 ? 3 : 4))
         for (int k = 0; k < 32; ++k) v[k] = pmul(v[k], scale);
     }
     lo_tile_store<T, L>(dst, v, t, stream_out);
-}
-
-// Persistent low pass over 2^14 tiles with a two-deep cp.async pipeline: the
-// next tile streams into the idle buffer while the current one is transformed.
-// Tile k (of this CTA) uses buffer k & 1: raw linear data first, then the
-// padded exchange layout.
-template <typename T>
-__global__ void __launch_bounds__(256, 1) k2_lo_pipe(const T* in, T* out, long long ld_in, long long ld_out,
-                                                     long long tiles_per_fn, long long ntiles, float scale,
-                                                     int do_scale) {
-    constexpr int L = 14, NT = 256;
-    constexpr int BUF = (1 << L) + (1 << (L - 4));   // padded elements per buffer
-    using V = typename P2<T>::t;
-    extern __shared__ __align__(16) unsigned char smraw[];
-    T* buf0 = reinterpret_cast<T*>(smraw);
-    const int t = threadIdx.x;
-    auto src_of = [&](long long i) {
-        return in + (i / tiles_per_fn) * ld_in + ((i % tiles_per_fn) << L);
-    };
-    auto issue = [&](long long i, T* b) {
-        if (i < ntiles) {
-            const T* s = src_of(i);
-#pragma unroll
-            for (int q = 0; q < 16; ++q) cp_async16(b + 4 * (t + NT * q), s + 4 * (t + NT * q));
-        }
-        cp_async_commit();
-    };
-    long long i = blockIdx.x;
-    issue(i, buf0);
-    for (int k = 0; i < ntiles; ++k, i += gridDim.x) {
-        T* cur = buf0 + (k & 1) * BUF;
-        T* nxt = buf0 + ((k + 1) & 1) * BUF;
-        issue(i + gridDim.x, nxt);
-        asm volatile("cp.async.wait_group 1;" ::: "memory");
-        __syncthreads();
-        V v[32];
-#pragma unroll
-        for (int q = 0; q < 16; ++q) ld16(cur + 4 * (t + NT * q), v + 2 * q);
-        bfly_range<0, 6>(v);
-        __syncthreads();   // raw tile read by everyone before the padded layout overwrites it
-        lo_tile_compute<T, L>(cur, v, t);
-        if (do_scale) {
-#pragma unroll
-            for (int kk = 0; kk < 32; ++kk) v[kk] = pmul(v[kk], scale);
-        }
-        T* dst = out + (i / tiles_per_fn) * ld_out + ((i % tiles_per_fn) << L);
-        lo_tile_store<T, L>(dst, v, t, false);
-        __syncthreads();   // buffer free before the copy two tiles ahead lands in it
-    }
-    cp_async_wait_all();
 }
 
 // ---------------------------------------------------------------------------
@@ -556,38 +500,6 @@ static int launch_lo(int L, const T* in, T* out, long long ld_in, long long ld_o
     return launch_lo2<T>(L, a, nullptr, N, fam, st);
 }
 
-static int num_sms() {
-    static int n = 0;
-    if (!n) {
-        int dev = 0;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
-        if (n <= 0) n = 148;
-    }
-    return n;
-}
-
-// low pass of L digits over nf functions.  The persistent pipelined variant
-// (one CTA per SM) measured no faster than three independent CTAs per SM, so
-// it is kept switched off.
-static constexpr bool kUseLowPipe = false;
-template <typename T>
-static int launch_low(int L, const T* in, T* out, long long ld_in, long long ld_out, int nf, long long N, float scale,
-                      int do_scale, const char* fam, cudaStream_t st) {
-    if (L != 14 || !kUseLowPipe) return launch_lo<T>(L, in, out, ld_in, ld_out, nf, N, scale, do_scale, fam, st);
-    const long long per = N >> 14, ntiles = per * nf;
-    const size_t smem = 2 * (((size_t)1 << 14) + ((size_t)1 << 10)) * sizeof(T);
-    auto k = k2_lo_pipe<T>;
-    int rc = attr_smem(k, smem);
-    if (rc) return rc;
-    const unsigned grid = (unsigned)std::min<long long>(ntiles, num_sms());
-    {
-        LaunchScope ls(fam, st);
-        k<<<grid, 256, smem, st>>>(in, out, ld_in, ld_out, per, ntiles, scale, do_scale);
-    }
-    DWT_CK_LAUNCH("k2_lo_pipe");
-    return DWT_OK;
-}
 
 template <typename T, int LT, int B, bool FUSED, bool HAS_COEF>
 static int launch_hi_one(HiArgs a, int nf, size_t bins_bytes, const char* fam, cudaStream_t st) {
@@ -644,7 +556,7 @@ static int p2_transform_t(dwt_plan_s* Pl, const T* in, T* out, int batch, long l
             continue;
         }
         const int L = p2_low_digits(m);
-        int rc = launch_low<T>(L, src, dst, ld_in, ld_out, nf, N, 1.f, 0, sgn < 0 ? "p2_lo_fwd" : "p2_lo_inv", st);
+        int rc = launch_lo<T>(L, src, dst, ld_in, ld_out, nf, N, 1.f, 0, sgn < 0 ? "p2_lo_fwd" : "p2_lo_inv", st);
         if (rc) return rc;
         HiArgs a{};
         a.in = dst;
