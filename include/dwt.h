@@ -347,6 +347,16 @@ int dwt_server_destroy(dwt_server_t server);
 const char *dwt_strerror(int status);
 const char *dwt_last_error(void);
 
+/*
+ * Self-test of the bounded device waits: launches one CTA that waits on an
+ * mbarrier phase that never completes, with the same bounded wait as the
+ * tensor-core kernels (a few hundred tries of at most 1 us).  Returns
+ * DWT_ETIMEOUT (with a message) when the wait gave up as designed, after
+ * synchronising `stream`; the context stays usable.  No counterpart in the
+ * paper: it checks the failure path of the library's own device waits.
+ */
+int dwt_selftest_bounded_wait(void *stream);
+
 /* Number of kernels this library has launched in this process. */
 long long dwt_launch_count(void);
 

@@ -76,6 +76,7 @@ _SIGS = {
     "dwt_inverse": (_I, [_VP, _VP, _VP, _I, _LL, _LL, _I, _I, _I, _VP]),
     "dwt_interpolate": (_I, [_VP, _VP, _VP, _VP, _I, _LL, _I, _I, _I, _VP, _VP, ctypes.c_double, _VP]),
     "dwt_interpolate_host": (_I, [_VP, _VP, _VP, _I, _LL, _I, _I, _VP, _VP, ctypes.c_double, _VP]),
+    "dwt_selftest_bounded_wait": (_I, [_VP]),
     "dwt_spline_prepare": (_I, [_VP, ctypes.c_double, _VP, _VP]),
     "dwt_spline": (_I, [_VP, _VP, _VP, _I, _LL, _VP, _VP, _VP, ctypes.c_double, _VP]),
     "dwt_spline_values_shifted": (_I, [_VP, _VP, _VP, _I, _VP, _I, _LL, _VP, _VP, _VP]),
@@ -245,6 +246,11 @@ def dwt_interpolate_host(plan, f, c, batch, ld, f_t, weight, var=None, dim=None,
     """dwt_interpolate on host buffers (f, c, var, dim host-resident; page-locked ones overlap copies)."""
     return _check(lib().dwt_interpolate_host(plan.handle, _ptr(f), _ptr(c), batch, ld, f_t, weight, _ptr(var),
                                              _ptr(dim), threshold, _stream(stream)))
+
+
+def dwt_selftest_bounded_wait(stream=None):
+    """Run the bounded-wait self-test; returns the status (DWT_ETIMEOUT expected) without raising."""
+    return lib().dwt_selftest_bounded_wait(_stream(stream))
 
 
 def dwt_spline_prepare(plan, alpha, gamma, stream=None):

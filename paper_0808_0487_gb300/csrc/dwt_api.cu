@@ -520,6 +520,8 @@ int dwt_interpolate_host(dwt_plan_t P, const void* f, void* c, int batch, long l
     return run_interpolate_host(P, f, c, batch, ld, f_t, weight, var, dim, thr, (cudaStream_t)stream);
 }
 
+int dwt_selftest_bounded_wait(void* stream) { return run_wait_probe((cudaStream_t)stream); }
+
 int dwt_spline_prepare(dwt_plan_t P, double alpha, const double* gamma, void* stream) {
     if (!P || !gamma || !(alpha > 1.0) || !std::isfinite(alpha)) {
         set_error("dwt_spline_prepare: bad arguments (alpha > 1 and gamma[s] required)");

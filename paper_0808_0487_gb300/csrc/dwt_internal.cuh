@@ -123,6 +123,7 @@ struct TcJob {
 int launch_tc_lo14(const TcJob& a, const TcJob* b, int* err, const char* fam, cudaStream_t st);
 bool tc_ok(int m);
 int tc_check(int* err, cudaStream_t st);
+int run_wait_probe(cudaStream_t st);
 int run_interpolate_host(dwt_plan_s* P, const void* f_host, void* c_host, int batch, long long ld, dwt_dtype f_t,
                          dwt_weight weight, double* var_host, int* dim_host, double thr, cudaStream_t st);
 // releases the plan's dwt_interpolate_host resources: after synchronising

@@ -71,15 +71,19 @@ __device__ __forceinline__ void mma_commit(uint32_t mbar) {
                  : "memory");
 }
 
-// bounded wait for the mbarrier phase; false on timeout
-__device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity) {
-    for (uint32_t it = 0; it < (1u << 26); ++it) {
+// bounded wait for the mbarrier phase; false on timeout.  Each try suspends
+// the thread for at most kWaitHintNs unless the phase completes, so a wait
+// gives up after about iters microseconds.
+constexpr uint32_t kWaitHintNs = 1000;
+constexpr uint32_t kWaitIters = 1u << 21;   // about two seconds
+__device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity, uint32_t iters = kWaitIters) {
+    for (uint32_t it = 0; it < iters; ++it) {
         uint32_t done;
         asm volatile(
-            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n"
             " selp.u32 %0, 1, 0, p;\n}\n"
             : "=r"(done)
-            : "r"(mbar), "r"(parity)
+            : "r"(mbar), "r"(parity), "r"(kWaitHintNs)
             : "memory");
         if (done) return true;
     }
@@ -402,6 +406,34 @@ int run_tc_transform(dwt_plan_s* Pl, const float* in, float* out, int batch, lon
     if (!rc) rc = tc_check(err, st);
     else dfree(err, st);
     return rc;
+}
+
+// A wait that can never complete (an mbarrier that expects one arrival that
+// never comes), bounded as every wait of the tensor-core kernels: it must give
+// up and report, leaving the context usable.
+__global__ void k_tc_wait_probe(uint32_t iters, int* err) {
+    __shared__ __align__(8) unsigned long long bar;
+    const uint32_t a = (uint32_t)__cvta_generic_to_shared(&bar);
+    if (threadIdx.x == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(a) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    const bool ok = __syncthreads_and(mbar_wait(a, 0, iters) ? 1 : 0) != 0;
+    if (!ok && threadIdx.x == 0) atomicExch(err, 1);
+}
+
+int run_wait_probe(cudaStream_t st) {
+    int* err = nullptr;
+    int rc = dmalloc((void**)&err, sizeof(int), st);
+    if (rc) return rc;
+    DWT_CK(cudaMemsetAsync(err, 0, sizeof(int), st));
+    {
+        LaunchScope ls("tc_wait_probe", st);
+        k_tc_wait_probe<<<1, 128, 0, st>>>(256u, err);
+    }
+    DWT_CK_LAUNCH("k_tc_wait_probe");
+    return tc_check(err, st);
 }
 
 bool tc_ok(int m) { return m == 14 || (m >= 18 && m <= 24); }

@@ -92,3 +92,17 @@ def test_tc_interpolate_rejects_small_m(dwt, dev):
     with pytest.raises(dwt.DwtError):
         dwt.dwt_interpolate(plan, f, c, None, 1, 2 ** m, dwt.DWT_F32, dwt.DWT_WEIGHT_INV_SQ_WAVENUMBER,
                             dwt.DWT_ALGO_TC_SPLIT_BF16)
+
+
+def test_bounded_wait_gives_up_and_context_survives(dwt, dev, orc):
+    """A device wait that never completes returns DWT_ETIMEOUT instead of hanging,
+    and the tensor-core path still works afterwards."""
+    assert dwt.dwt_selftest_bounded_wait() == dwt.DWT_ETIMEOUT
+    assert "bounded wait" in dwt.lib().dwt_last_error().decode()
+    p, m, N = 2, 14, 2 ** 14
+    plan = dwt.dwt_plan_create(p, m, 1, S.small_net(p, m, 1, index=2), dwt.DWT_PLAN_TRANSFORM_ONLY)
+    v = S.uniform(S.stream_seed(33, S.P_VALUES), N) - 0.5
+    x = torch.tensor(v.astype(np.float32), device=dev)
+    y = torch.empty_like(x)
+    dwt.dwt_forward(plan, x, y, 1, N, N, dwt.DWT_F32, dwt.DWT_F32, dwt.DWT_ALGO_TC_SPLIT_BF16)
+    assert rel_l2(y.cpu().numpy(), orc.fwt(p, m, v).real) < 1e-5
