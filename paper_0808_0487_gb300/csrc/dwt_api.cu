@@ -129,46 +129,66 @@ int ensure_workspace(dwt_plan_s* P, size_t bytes, cudaStream_t st) {
 // Wc consecutive low indices wide, so that every row is a contiguous segment.
 static const size_t kTileBudget = 64 * 1024;   // bytes of shared memory per tile
 
-static void make_pass_plan(int p, int m, int elem, dwt::PassPlan& pp) {
-    long long cap = (long long)(kTileBudget / (size_t)elem);
-    int wc_max = elem >= 8 ? 8 : 16;
+// widest power-of-2 column count for a pass of R rows starting at row distance S
+static int pass_wc(long long R, long long S, long long cap, int wc_max) {
+    int wc = 1;
+    while (wc * 2 <= wc_max && wc * 2 <= S && R * wc * 2 <= cap) wc *= 2;
+    return wc;
+}
+
+// Fewest passes first.  Among the splits with that many passes, the one whose
+// narrowest high pass has the widest rows (wide rows keep the strided passes
+// coalesced), then the one with the longest contiguous low pass.  A high pass
+// then halves its rows (down to 64 bytes) while it has fewer than min_tiles
+// tiles per function.
+static void make_pass_plan(int p, int m, int elem, long long min_tiles, dwt::PassPlan& pp) {
+    const long long cap = (long long)(kTileBudget / (size_t)elem);
+    const int wc_min = std::max(1, 64 / elem);    // 64-byte rows at least in a high pass
+    const int wc_max = std::max(1, 256 / elem);   // 256-byte rows at most
     int blo = 0;
     while (dwt::ipow_ll(p, blo + 1) <= cap) ++blo;
     int bhi = 0;
-    while (dwt::ipow_ll(p, bhi + 1) * wc_max <= cap) ++bhi;
+    while (dwt::ipow_ll(p, bhi + 1) * wc_min <= cap) ++bhi;
+    int b[32];
     pp.q = 0;
     if (m <= blo) {
-        pp.g[0].d0 = 0;
-        pp.g[0].b = m;
+        b[0] = m;
         pp.q = 1;
     } else {
-        // fewest passes: a low pass of blo digits, the rest shared evenly by nh high passes
-        int nh = 1;
-        while (blo + nh * bhi < m) ++nh;
-        int rest = m - blo, d = blo;
-        pp.g[0].d0 = 0;
-        pp.g[0].b = blo;
-        for (int t = 0; t < nh; ++t) {
-            int b = rest / nh + (t < rest % nh ? 1 : 0);
-            pp.g[t + 1].d0 = d;
-            pp.g[t + 1].b = b;
-            d += b;
+        const int nh = (m - blo + bhi - 1) / bhi;
+        int best_wc = -1;
+        for (int lo = blo; lo >= std::max(1, m - nh * bhi); --lo) {
+            const int rest = m - lo;
+            if (rest < nh) continue;
+            int bt[32], wc_lo = 1 << 30, d = lo;
+            bt[0] = lo;
+            for (int t = 0; t < nh; ++t) {
+                bt[t + 1] = rest / nh + (t < rest % nh ? 1 : 0);
+                const int wc = pass_wc(dwt::ipow_ll(p, bt[t + 1]), dwt::ipow_ll(p, d), cap, wc_max);
+                wc_lo = std::min(wc_lo, wc);
+                d += bt[t + 1];
+            }
+            if (wc_lo > best_wc) {
+                best_wc = wc_lo;
+                for (int t = 0; t <= nh; ++t) b[t] = bt[t];
+                pp.q = nh + 1;
+            }
         }
-        pp.q = nh + 1;
     }
-    long long N = dwt::ipow_ll(p, m);
+    const long long N = dwt::ipow_ll(p, m);
+    int d = 0;
     for (int t = 0; t < pp.q; ++t) {
         PassGeom& g = pp.g[t];
+        g.d0 = d;
+        g.b = b[t];
+        d += b[t];
         g.S = dwt::ipow_ll(p, g.d0);
         g.R = (int)dwt::ipow_ll(p, g.b);
-        int wc = 1;
-        if (g.d0 > 0) {
-            while (wc * 2 <= wc_max && wc * 2 <= g.S && (long long)g.R * wc * 2 <= cap) wc *= 2;
-        }
-        g.Wc = wc;
+        g.Wc = g.d0 > 0 ? pass_wc(g.R, g.S, cap, wc_max) : 1;
+        while (g.Wc > wc_min && ((g.S + g.Wc - 1) / g.Wc) * (N / (g.S * g.R)) < min_tiles) g.Wc /= 2;
         g.wlog = 0;
-        while ((1 << g.wlog) < wc) ++g.wlog;
-        g.nlo = (g.S + wc - 1) / wc;
+        while ((1 << g.wlog) < g.Wc) ++g.wlog;
+        g.nlo = (g.S + g.Wc - 1) / g.Wc;
         g.ntile = g.nlo * (N / (g.S * g.R));
     }
 }
@@ -272,9 +292,18 @@ int dwt_plan_create(int p, int m, int s, const uint8_t* C, unsigned flags, void*
     P->N = ipow_ll(p, m);
     P->flags = flags;
     P->C.assign(C, C + (size_t)s * m * m);
-    make_pass_plan(p, m, 4, P->passes[0]);
-    make_pass_plan(p, m, 8, P->passes[1]);
-    make_pass_plan(p, m, 16, P->passes[2]);
+    {
+        // high passes of small transforms take narrower rows, for at least two tiles per SM
+        int dev = 0, sms = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) !=
+                                                      cudaSuccess || sms < 1) {
+            cudaGetLastError();
+            sms = 1;
+        }
+        make_pass_plan(p, m, 4, 2ll * sms, P->passes[0]);
+        make_pass_plan(p, m, 8, 2ll * sms, P->passes[1]);
+        make_pass_plan(p, m, 16, 2ll * sms, P->passes[2]);
+    }
     // row coset labels and column point contributions
     std::vector<uint32_t> R((size_t)s * m), col((size_t)s * m);
     for (int j = 0; j < s; ++j)

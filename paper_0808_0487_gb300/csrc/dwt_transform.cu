@@ -11,6 +11,8 @@
 // writes back.  Inside a tile every thread takes p^K elements that differ only
 // in K consecutive digits and runs those K stages in registers; groups of K
 // digits follow one another through shared memory.
+#include <string.h>
+
 #include <type_traits>
 
 #include "dwt_internal.cuh"
@@ -50,8 +52,17 @@ template <typename T, typename TI> __device__ __forceinline__ T promote(TI v) { 
 template <> __device__ __forceinline__ float2 promote<float2, float>(float v) { return make_float2(v, 0.f); }
 template <> __device__ __forceinline__ double2 promote<double2, double>(double v) { return make_double2(v, 0.0); }
 
-__device__ __forceinline__ float2 operator+(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
-__device__ __forceinline__ float2 operator-(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+// complex FP32 on the packed f32x2 pipe: one instruction per complex add
+__device__ __forceinline__ float2 operator+(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 operator-(float2 a, float2 b) {
+    unsigned long long ua, ub, ud;
+    memcpy(&ua, &a, 8);
+    memcpy(&ub, &b, 8);
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(ud) : "l"(ua), "l"(ub));
+    float2 d;
+    memcpy(&d, &ud, 8);
+    return d;
+}
 __device__ __forceinline__ double2 operator+(double2 a, double2 b) { return make_double2(a.x + b.x, a.y + b.y); }
 __device__ __forceinline__ double2 operator-(double2 a, double2 b) { return make_double2(a.x - b.x, a.y - b.y); }
 
@@ -77,33 +88,59 @@ template <typename T> static inline size_t spad_bytes(int nel) {
 constexpr int cpow(int p, int k) { return k == 0 ? 1 : p * cpow(p, k - 1); }
 
 // ---------------------------------------------------------------------------
-// one p-point DFT y_t = sum_u omega^{SGN u t} x_u in registers
+// one p-point DFT y_t = sum_u omega^{SGN u t} x_u in registers, odd p.  The
+// terms u and p - u pair up: with s_u = x_u + x_{p-u} and d_u = x_u - x_{p-u},
+//   y_t     = x_0 + sum_u cos(2 pi ut/p) s_u + i SGN sum_u sin(2 pi ut/p) d_u,
+//   y_{p-t} = the same with the sine sum negated,
+// for u, t = 1 .. (p-1)/2: real-by-complex products only, shared by both outputs.
+template <typename T> struct TwOf;
+template <> struct TwOf<float2> {
+    static __device__ __forceinline__ float c(const Tw& tw, int e) { return tw.c[e]; }
+    static __device__ __forceinline__ float s(const Tw& tw, int e) { return tw.s[e]; }
+};
+template <> struct TwOf<double2> {
+    static __device__ __forceinline__ double c(const Tw& tw, int e) { return tw.cd[e]; }
+    static __device__ __forceinline__ double s(const Tw& tw, int e) { return tw.sd[e]; }
+};
+
+// y = c x + a for real c and complex x, a
+__device__ __forceinline__ float2 cfma(float c, float2 x, float2 a) { return __ffma2_rn(make_float2(c, c), x, a); }
+__device__ __forceinline__ double2 cfma(double c, double2 x, double2 a) {
+    return make_double2(fma(c, x.x, a.x), fma(c, x.y, a.y));
+}
+// a + g i b with g = +-1: (a.x - g b.y, a.y + g b.x)
+template <int G> __device__ __forceinline__ float2 add_ib(float2 a, float2 b) {
+    return __ffma2_rn(make_float2(-(float)G, (float)G), make_float2(b.y, b.x), a);
+}
+template <int G> __device__ __forceinline__ double2 add_ib(double2 a, double2 b) {
+    return make_double2(a.x - G * b.y, a.y + G * b.x);
+}
+
 template <int P, int SGN, typename T> struct Dft {
     static __device__ __forceinline__ void run(T* x, const Tw& tw) {
         static_assert(IsCplx<T>::value, "p > 2 needs complex data");
-        T y[P];
+        constexpr int H = (P - 1) / 2;
+        T sp[H], dm[H];
+        T y0 = x[0];
 #pragma unroll
-        for (int t = 0; t < P; ++t) {
-            T acc = x[0];
-#pragma unroll
-            for (int u = 1; u < P; ++u) {
-                const int e = SGN > 0 ? (u * t) % P : (P - (u * t) % P) % P;
-                if (e == 0) {
-                    acc = acc + x[u];
-                } else if (std::is_same<T, float2>::value) {
-                    const float c = tw.c[e], s = tw.s[e];
-                    acc.x += x[u].x * c - x[u].y * s;
-                    acc.y += x[u].x * s + x[u].y * c;
-                } else {
-                    const double c = tw.cd[e], s = tw.sd[e];
-                    acc.x += x[u].x * c - x[u].y * s;
-                    acc.y += x[u].x * s + x[u].y * c;
-                }
-            }
-            y[t] = acc;
+        for (int u = 1; u <= H; ++u) {
+            sp[u - 1] = x[u] + x[P - u];
+            dm[u - 1] = x[u] - x[P - u];
+            y0 = y0 + sp[u - 1];
         }
 #pragma unroll
-        for (int t = 0; t < P; ++t) x[t] = y[t];
+        for (int t = 1; t <= H; ++t) {
+            T a = x[0], b = zero_of<T>();
+#pragma unroll
+            for (int u = 1; u <= H; ++u) {
+                const int e = (u * t) % P;
+                a = cfma(TwOf<T>::c(tw, e), sp[u - 1], a);
+                b = cfma(TwOf<T>::s(tw, e), dm[u - 1], b);
+            }
+            x[t] = add_ib<SGN>(a, b);
+            x[P - t] = add_ib<-SGN>(a, b);
+        }
+        x[0] = y0;
     }
 };
 
@@ -179,7 +216,7 @@ __device__ void tile_stages(T* sm, int b, int R, int wlog, const Tw& tw) {
 }
 
 template <int P, typename T> struct KMax {
-    static constexpr int v = P == 2 ? (sizeof(T) == 4 ? 5 : 4)
+    static constexpr int v = P == 2 ? (sizeof(T) == 8 ? 4 : 5)
                                     : (sizeof(T) == 8 ? (P == 3 ? 3 : P == 5 ? 2 : 1) : (P == 3 ? 2 : 1));
 };
 
@@ -214,9 +251,95 @@ struct PassArgs {
     Tw tw;
 };
 
-// one pass over the digits d0..d0+b-1 of every function: grid (tiles, functions)
-template <int P, typename T, typename TI, int SGN>
-__global__ void __launch_bounds__(256) k_pass(PassArgs a) {
+// Register groups of a pass.  A tile has R = p^b rows (row digits 0 .. b-1) of
+// Wc columns; element (r, c) sits at tile index (r << wlog) + c in shared
+// memory and at offset c + S r from the tile base in global memory.  A group
+// runs the stages of the k row digits [g0, g0 + k): each task holds the p^k
+// elements that differ in those digits, rows r0 + i p^g0 with
+// r0 = rl + rh p^(g0+k) (rl < p^g0, rh < R / p^(g0+k)), in one column.  Tasks
+// are numbered column first, then rl, then rh, so that neighbouring threads
+// touch neighbouring columns and rows (coalesced global access); with RHF the
+// order of rl and rh is swapped, so that neighbouring threads are p^(g0+k)
+// rows apart: an odd stride for odd p, which spreads them over all shared
+// memory banks without padding.  A group reads from global memory (SRC_G) or
+// shared memory and writes to global memory (DST_G) or shared memory.
+template <int P, typename T> __device__ __forceinline__ int sx(int e) { return (P & 1) ? e : spad<T>(e); }
+
+template <int P, int K, int SGN, typename T, typename TI, bool SRC_G, bool DST_G, bool RHF>
+__device__ __forceinline__ void rgroup(T* sm, const TI* gin, T* gout, int g0, const PassArgs& a, int ncols) {
+    constexpr int NK = cpow(P, K);
+    unsigned pg0 = 1;
+    for (int i = 0; i < g0; ++i) pg0 *= P;
+    const unsigned pgk = pg0 * NK;
+    const unsigned nrh = (unsigned)a.R / pgk;
+    const unsigned ntask = ((unsigned)a.R / NK) << a.wlog;
+    // q / dv = (q mg) >> 42, exact while q dv < 2^42 (q, dv <= R <= 2^16 here)
+    const unsigned dv = RHF ? nrh : pg0;
+    const unsigned long long mg = (1ull << 42) / dv + 1;
+    const unsigned cmask = (unsigned)a.Wc - 1;
+    const long long step = a.S * (long long)pg0;
+    for (unsigned t = threadIdx.x; t < ntask; t += blockDim.x) {
+        const unsigned c = t & cmask, q = t >> a.wlog;
+        const unsigned qd = (unsigned)(((unsigned long long)q * mg) >> 42), qm = q - qd * dv;
+        const unsigned rl = RHF ? qd : qm, rh = RHF ? qm : qd;
+        const unsigned r0 = rl + rh * pgk;
+        const bool live = (int)c < ncols;
+        T v[NK];
+        if constexpr (SRC_G) {
+            const TI* src = gin + c + a.S * (long long)r0;
+#pragma unroll
+            for (int i = 0; i < NK; ++i) v[i] = live ? promote<T, TI>(src[i * step]) : zero_of<T>();
+        } else {
+#pragma unroll
+            for (int i = 0; i < NK; ++i) v[i] = sm[sx<P, T>((int)(((r0 + i * pg0) << a.wlog) + c))];
+        }
+        RegStages<P, NK, 1, SGN, T>::run(v, a.tw);
+        if constexpr (DST_G) {
+            if (live) {
+                T* dst = gout + c + a.S * (long long)r0;
+#pragma unroll
+                for (int i = 0; i < NK; ++i) dst[i * step] = a.do_scale ? scale_by<T>(v[i], a.scale) : v[i];
+            }
+        } else {
+#pragma unroll
+            for (int i = 0; i < NK; ++i) sm[sx<P, T>((int)(((r0 + i * pg0) << a.wlog) + c))] = v[i];
+        }
+    }
+}
+
+// mode bits: 1 read global, 2 write global, 4 rh-first numbering
+template <int P, int SGN, typename T, typename TI, int K>
+__device__ __forceinline__ void rgroup_k(int k, int mode, T* sm, const TI* gin, T* gout, int g0, const PassArgs& a,
+                                         int ncols) {
+    if constexpr (K >= 1) {
+        if (k == K) {
+            switch (mode) {
+                case 1: rgroup<P, K, SGN, T, TI, true, false, false>(sm, gin, gout, g0, a, ncols); break;
+                case 2: rgroup<P, K, SGN, T, TI, false, true, false>(sm, gin, gout, g0, a, ncols); break;
+                case 3: rgroup<P, K, SGN, T, TI, true, true, false>(sm, gin, gout, g0, a, ncols); break;
+                default:
+                    if constexpr (P & 1) rgroup<P, K, SGN, T, TI, false, false, true>(sm, gin, gout, g0, a, ncols);
+                    else rgroup<P, K, SGN, T, TI, false, false, false>(sm, gin, gout, g0, a, ncols);
+                    break;
+            }
+            return;
+        }
+        rgroup_k<P, SGN, T, TI, K - 1>(k, mode, sm, gin, gout, g0, a, ncols);
+    }
+}
+
+// One pass over the digits d0 .. d0+b-1 of every function: grid (tiles,
+// functions).  The first group takes the top digits and reads the tile from
+// global memory straight into registers (coalesced: neighbouring threads hold
+// neighbouring rows, or columns); the other digits follow bottom-up through
+// shared memory.  The last group, which then has the longest runs of
+// neighbouring rows below it, writes straight to global memory when a run
+// (p^g0 rows in the low pass, Wc columns in the others) spans at least 64
+// bytes; otherwise it writes shared memory and the tile leaves in element
+// order.  In place is safe: a tile is read in full before any of it is written
+// (a one-group pass reads and writes the same elements per thread).
+template <int P, typename T, typename TI, int SGN, int KM>
+__global__ void __maxnreg__(96) k_pass(PassArgs a) {   // 96 x 512 threads fit the register file
     extern __shared__ __align__(16) unsigned char smraw[];
     T* sm = reinterpret_cast<T*>(smraw);
     const long long fn = blockIdx.y;
@@ -224,19 +347,39 @@ __global__ void __launch_bounds__(256) k_pass(PassArgs a) {
     const long long lo0 = (tile % a.nlo) << a.wlog;
     const long long base = lo0 + (tile / a.nlo) * a.SR;
     const int ncols = (int)min((long long)a.Wc, a.S - lo0);
-    const int nel = a.R << a.wlog;
-    const int cmask = a.Wc - 1;
     const TI* in = reinterpret_cast<const TI*>(a.in) + fn * a.ld_in + base;
     T* out = reinterpret_cast<T*>(a.out) + fn * a.ld_out + base;
-    load_tile<T, TI>(sm, in, nel, a.wlog, cmask, ncols, a.S);
-    __syncthreads();
-    tile_stages<P, SGN, T, KMax<P, T>::v>(sm, a.b, a.R, a.wlog, a.tw);
-    for (int e = threadIdx.x; e < nel; e += blockDim.x) {
-        const int r = e >> a.wlog, c = e & cmask;
-        if (c < ncols) {
-            T v = sm[spad<T>(e)];
-            if (a.do_scale) v = scale_by<T>(v, a.scale);
-            out[c + (long long)r * a.S] = v;
+    const int b = a.b;
+    const int k0 = min(KM, b);
+    // the last group: the top of the digits below the first group
+    const int g_last = b == k0 ? 0 : ((b - k0 - 1) / KM) * KM;
+    long long run = 1;
+    if (a.S == 1) {
+        for (int i = 0; i < g_last; ++i) run *= P;
+    } else {
+        run = a.Wc;
+    }
+    const bool direct_out = run * (long long)sizeof(T) >= 64;
+    int g0 = b - k0, k = k0;
+    for (;;) {
+        const bool last = g0 == g_last;
+        const int mode = (g0 + k == b ? 1 : 0) | (last && direct_out ? 2 : 0) | (g0 + k != b && !(last && direct_out) ? 4 : 0);
+        rgroup_k<P, SGN, T, TI, KM>(k, mode, sm, in, out, g0, a, ncols);
+        if (!(last && direct_out)) __syncthreads();
+        if (last) break;
+        g0 = g0 + k == b ? 0 : g0 + k;   // after the top group, bottom-up
+        k = min(KM, b - k0 - g0);
+    }
+    if (!direct_out) {
+        const int nel = a.R << a.wlog;
+        const int cmask = a.Wc - 1;
+        for (int e = threadIdx.x; e < nel; e += blockDim.x) {
+            const int r = e >> a.wlog, c = e & cmask;
+            if (c < ncols) {
+                T v = sm[sx<P, T>(e)];
+                if (a.do_scale) v = scale_by<T>(v, a.scale);
+                out[c + (long long)r * a.S] = v;
+            }
         }
     }
 }
@@ -262,20 +405,26 @@ template <typename T> __device__ __forceinline__ T mulw(T v, float w);
 template <> __device__ __forceinline__ float mulw<float>(float v, float w) { return v * w; }
 template <> __device__ __forceinline__ float2 mulw<float2>(float2 v, float w) { return make_float2(v.x * w, v.y * w); }
 
-// per-lane FP32 class sums -> one FP64 value per class and tile, fixed order
-__device__ __forceinline__ void reduce_bins(const float* bins, int nb2, double* out, long long stride) {
+// per-lane FP32 class sums of the first nwb warps -> one FP64 value per class
+// and tile, fixed order
+__device__ __forceinline__ void reduce_bins(const float* bins, int nb2, int nwb, double* out, long long stride) {
     const int nw = blockDim.x >> 5, w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     for (int bi = w; bi < nb2; bi += nw) {
         float x = 0.f;
-        for (int ww = 0; ww < nw; ++ww) x += bins[(ww * nb2 + bi) * 32 + lane];
+        for (int ww = 0; ww < nwb; ++ww) x += bins[(ww * nb2 + bi) * 32 + lane];
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
         if (lane == 0) out[bi * stride] = (double)x;
     }
 }
 
-template <int P, typename T, typename TI>
-__global__ void __launch_bounds__(256) k_mid(MidArgs m) {
+// The fused top pass in register groups (as k_pass): forward groups from the
+// top digits down, the last one leaving the tile in shared memory; the scale,
+// weight, optional coefficient store and class partials (per-lane FP32 bins of
+// the first nwb warps, a fixed summation order) element by element; then the
+// inverse groups, the last one writing global memory as in k_pass.
+template <int P, typename T, typename TI, int KM>
+__global__ void __maxnreg__(96) k_mid(MidArgs m, int nwb) {
     const PassArgs& a = m.pa;
     extern __shared__ __align__(16) unsigned char smraw[];
     T* sm = reinterpret_cast<T*>(smraw);
@@ -292,33 +441,84 @@ __global__ void __launch_bounds__(256) k_mid(MidArgs m) {
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const TI* in = reinterpret_cast<const TI*>(a.in) + fn * a.ld_in + base;
     T* out = reinterpret_cast<T*>(a.out) + fn * a.ld_out + base;
-    load_tile<T, TI>(sm, in, nel, a.wlog, cmask, ncols, a.S);
-    for (int i = threadIdx.x; i < (int)(blockDim.x >> 5) * nb2 * 32; i += blockDim.x) bins[i] = 0.f;
-    __syncthreads();
-    tile_stages<P, -1, T, KMax<P, T>::v>(sm, a.b, a.R, a.wlog, a.tw);
-    float* mybins = bins + (size_t)w * nb2 * 32 + lane;
-    T* coef = m.coef ? reinterpret_cast<T*>(m.coef) + fn * a.ld_out + base : nullptr;
-    for (int e = threadIdx.x; e < nel; e += blockDim.x) {
-        const int r = e >> a.wlog, c = e & cmask;
-        if (c >= ncols) continue;
-        const long long H = base + c + (long long)r * a.S;
-        T v = scale_by<T>(sm[spad<T>(e)], a.scale);
-        if (m.W) v = mulw<T>(v, __ldg(m.W + H));
-        if (coef) coef[c + (long long)r * a.S] = v;
-        if (H != 0) {
-            const float q = mag2<T>(v);
-            const uchar2 k = __ldg(reinterpret_cast<const uchar2*>(m.cls) + H);
-            mybins[(int)k.x * 32] += q;
-            mybins[(m.nb + (int)k.y) * 32] += q;
+    for (int i = threadIdx.x; i < nwb * nb2 * 32; i += blockDim.x) bins[i] = 0.f;
+    const int b = a.b;
+    const int k0 = min(KM, b);
+    const int g_last = b == k0 ? 0 : ((b - k0 - 1) / KM) * KM;
+    long long run = 1;
+    if (a.S == 1) {
+        for (int i = 0; i < g_last; ++i) run *= P;
+    } else {
+        run = a.Wc;
+    }
+    const bool direct_out = run * (long long)sizeof(T) >= 64;
+    // forward stages
+    {
+        int g0 = b - k0, k = k0;
+        for (;;) {
+            const bool first = g0 + k == b;
+            rgroup_k<P, -1, T, TI, KM>(k, first ? 1 : 4, sm, in, out, g0, a, ncols);
+            __syncthreads();
+            if (g0 == g_last) break;
+            g0 = first ? 0 : g0 + k;
+            k = min(KM, b - k0 - g0);
         }
-        sm[spad<T>(e)] = v;
+    }
+    // scale, weight, coefficients, class partials; the weight and class loads
+    // of 8 elements per thread are issued together
+    if (w < nwb) {
+        float* mybins = bins + (size_t)w * nb2 * 32 + lane;
+        T* coef = m.coef ? reinterpret_cast<T*>(m.coef) + fn * a.ld_out + base : nullptr;
+        const int step = nwb * 32;
+        for (int e0 = threadIdx.x; e0 < nel; e0 += 8 * step) {
+            float wv[8];
+            uchar2 kc[8];
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+                const int e = e0 + j * step;
+                const int r = e >> a.wlog, c = e & cmask;
+                const long long H = base + c + (long long)r * a.S;
+                const bool ok = e < nel && c < ncols;
+                wv[j] = ok && m.W ? __ldg(m.W + H) : 1.f;
+                kc[j] = ok ? __ldg(reinterpret_cast<const uchar2*>(m.cls) + H) : make_uchar2(0, 0);
+            }
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+                const int e = e0 + j * step;
+                const int r = e >> a.wlog, c = e & cmask;
+                if (e >= nel || c >= ncols) continue;
+                const long long H = base + c + (long long)r * a.S;
+                T v = mulw<T>(scale_by<T>(sm[sx<P, T>(e)], a.scale), wv[j]);
+                if (coef) coef[c + (long long)r * a.S] = v;
+                if (H != 0) {
+                    const float q = mag2<T>(v);
+                    mybins[(int)kc[j].x * 32] += q;
+                    mybins[(m.nb + (int)kc[j].y) * 32] += q;
+                }
+                sm[sx<P, T>(e)] = v;
+            }
+        }
     }
     __syncthreads();
-    reduce_bins(bins, nb2, m.part + fn * nb2 * m.ntile + tile, m.ntile);
-    tile_stages<P, +1, T, KMax<P, T>::v>(sm, a.b, a.R, a.wlog, a.tw);
-    for (int e = threadIdx.x; e < nel; e += blockDim.x) {
-        const int r = e >> a.wlog, c = e & cmask;
-        if (c < ncols) out[c + (long long)r * a.S] = sm[spad<T>(e)];
+    reduce_bins(bins, nb2, nwb, m.part + fn * nb2 * m.ntile + tile, m.ntile);
+    // inverse stages of the same digits, in the same order
+    {
+        int g0 = b - k0, k = k0;
+        for (;;) {
+            const bool last = g0 == g_last;
+            const bool dst_g = last && direct_out;
+            rgroup_k<P, +1, T, T, KM>(k, dst_g ? 2 : 4, sm, out, out, g0, a, ncols);
+            if (!dst_g) __syncthreads();
+            if (last) break;
+            g0 = g0 + k == b ? 0 : g0 + k;
+            k = min(KM, b - k0 - g0);
+        }
+    }
+    if (!direct_out) {
+        for (int e = threadIdx.x; e < nel; e += blockDim.x) {
+            const int r = e >> a.wlog, c = e & cmask;
+            if (c < ncols) out[c + (long long)r * a.S] = sm[sx<P, T>(e)];
+        }
     }
 }
 
@@ -343,7 +543,7 @@ __global__ void __launch_bounds__(256) k_effdim_bins(const T* coef, long long ld
         mybins[(nb + (int)k.y) * 32] += q;
     }
     __syncthreads();
-    reduce_bins(bins, nb2, part + fn * nb2 * nchunk + chunk, nchunk);
+    reduce_bins(bins, nb2, blockDim.x >> 5, part + fn * nb2 * nchunk + chunk, nchunk);
 }
 
 // partials part[fn][class][tile] -> per-class totals: one block per (class,
@@ -437,19 +637,33 @@ static PassArgs pass_args(const PassGeom& g, const void* in, void* out, long lon
 
 static const char* pass_family(int t, int q) { return t == 0 ? "pass_lo" : (t == q - 1 ? "pass_hi" : "pass_mid"); }
 
-template <int P, typename T, typename TI, int SGN>
-static int launch_pass(const PassGeom& g, const PassArgs& a, int nf, const char* fam, cudaStream_t st) {
+// threads of a pass: one per task of its first (top) group, 32 .. 512
+template <int P, int KM>
+static int pass_threads(const PassGeom& g) {
+    const int k0 = std::min(KM, g.b);
+    long long tasks = ((long long)g.R / ipow_ll(P, k0)) << g.wlog;
+    tasks = (tasks + 31) / 32 * 32;
+    return (int)std::min(512ll, std::max(32ll, tasks));
+}
+
+template <int P, typename T, typename TI, int SGN, int KM>
+static int launch_pass_k(const PassGeom& g, const PassArgs& a, int nf, const char* fam, cudaStream_t st) {
     const size_t smem = spad_bytes<T>(g.R << g.wlog);
-    auto kern = k_pass<P, T, TI, SGN>;
+    auto kern = k_pass<P, T, TI, SGN, KM>;
     int rc = set_smem(kern, smem);
     if (rc) return rc;
     dim3 grid((unsigned)g.ntile, (unsigned)nf);
     {
         LaunchScope ls(fam, st);
-        kern<<<grid, 256, smem, st>>>(a);
+        kern<<<grid, pass_threads<P, KM>(g), smem, st>>>(a);
     }
     DWT_CK_LAUNCH("k_pass");
     return DWT_OK;
+}
+
+template <int P, typename T, typename TI, int SGN>
+static int launch_pass(const PassGeom& g, const PassArgs& a, int nf, const char* fam, cudaStream_t st) {
+    return launch_pass_k<P, T, TI, SGN, KMax<P, T>::v>(g, a, nf, fam, st);
 }
 
 // L2-sized groups of functions: the passes of one group run back to back so
@@ -530,11 +744,13 @@ int run_transform(dwt_plan_s* Pl, const void* in, void* out, int batch, long lon
 }
 
 // ---------------------------------------------------------------------------
-static int bins_warps(size_t tile_bytes, int nb2) {
+// warps that keep class bins next to a tile: up to maxw within `budget` bytes
+// of bins (at least one while it fits beside the tile)
+static int bins_warps(size_t tile_bytes, int nb2, size_t budget = 227 * 1024, int maxw = 8) {
     const size_t avail = 227 * 1024 - ((tile_bytes + 15) & ~(size_t)15);
     const size_t per_warp = (size_t)nb2 * 32 * 4;
-    int nw = (int)std::min<size_t>(8, avail / per_warp);
-    return nw;
+    if (per_warp > avail) return 0;
+    return (int)std::max<size_t>(1, std::min<size_t>(maxw, std::min(avail, budget) / per_warp));
 }
 
 static int finalize(dwt_plan_s* Pl, const double* part, long long nchunk, int batch, double thr, double* var, int* dim,
@@ -566,8 +782,12 @@ static int interpolate_t(dwt_plan_s* Pl, const void* f, void* c, void* coef, int
     const int nb = Pl->s + 1, nb2 = 2 * nb;
     const PassGeom& gm = pp.g[pp.q - 1];
     const long long ntile = gm.ntile;
+    constexpr int KM = KMax<P, T>::v;
     const size_t tile_bytes = spad_bytes<T>(gm.R << gm.wlog);
-    const int nw = bins_warps(tile_bytes, nb2);
+    const int nt = pass_threads<P, KM>(gm);
+    // warps that bin: their bins within 48 KB, so that the tile and its bins
+    // leave room for a second CTA
+    const int nw = std::min(nt / 32, bins_warps(tile_bytes, nb2, 48 * 1024, 16));
     if (nw < 1) {
         set_error("s = %d too large for the fused variance pass", Pl->s);
         return DWT_EUNSUPPORTED;
@@ -576,8 +796,8 @@ static int interpolate_t(dwt_plan_s* Pl, const void* f, void* c, void* coef, int
     int rc = ensure_workspace(Pl, (size_t)batch * (ntile + 1) * nb2 * sizeof(double), st);
     if (rc) return rc;
     double* part = (double*)Pl->d_ws;
-    auto kmid_first = k_mid<P, T, TI>;   // single pass: reads f directly
-    auto kmid_next = k_mid<P, T, T>;     // after lower passes: in place on c
+    auto kmid_first = k_mid<P, T, TI, KM>;   // single pass: reads f directly
+    auto kmid_next = k_mid<P, T, T, KM>;     // after lower passes: in place on c
     rc = set_smem(kmid_first, smem);
     if (rc) return rc;
     rc = set_smem(kmid_next, smem);
@@ -614,8 +834,8 @@ static int interpolate_t(dwt_plan_s* Pl, const void* f, void* c, void* coef, int
         {
             LaunchScope ls("interp_top", st);
             dim3 grid((unsigned)ntile, (unsigned)nf);
-            if (pp.q == 1) kmid_first<<<grid, nw * 32, smem, st>>>(m);
-            else kmid_next<<<grid, nw * 32, smem, st>>>(m);
+            if (pp.q == 1) kmid_first<<<grid, nt, smem, st>>>(m, nw);
+            else kmid_next<<<grid, nt, smem, st>>>(m, nw);
         }
         DWT_CK_LAUNCH("k_mid");
         // inverse passes below the top one, in place on c
