@@ -76,13 +76,16 @@ def test_interpolate_m20_batch(dwt, dev, orc):
         _check_dims(dg[b], dt, ds, vt, vs)
 
 
-@pytest.mark.parametrize("which", ["p3_m13", "p11_m4", "p13_m4"])
+# p3_m11_s40: the top pass bins in one warp (40 coordinates: 82 classes);
+# p7_m6: a top pass of two digits with seven binning warps; p5_m7: lo 5 + top 2
+@pytest.mark.parametrize("which", ["p3_m13", "p11_m4", "p13_m4", "p3_m11_s40", "p7_m6", "p5_m7"])
 def test_interpolate_p_odd(dwt, dev, orc, which):
     if which == "p3_m13":
         w = S.workload_p3_m13()
         p, m, s, C = w["p"], w["m"], w["s"], w["C"]
     else:
-        p, m, s = (11, 4, 5) if which == "p11_m4" else (13, 4, 3)
+        p, m, s = {"p11_m4": (11, 4, 5), "p13_m4": (13, 4, 3), "p3_m11_s40": (3, 11, 40), "p7_m6": (7, 6, 5),
+                   "p5_m7": (5, 7, 4)}[which]
         C = S.small_net(p, m, s, index=90 + p)
     N = p ** m
     plan = dwt.dwt_plan_create(p, m, s, C)

@@ -144,7 +144,8 @@ def test_sizes_and_primes(dwt, dev, orc, p, m):
         assert rel_l2(_cplx(back), f) < TOL32
 
 
-@pytest.mark.parametrize("p,m", [(3, 7), (5, 4), (2, 16)])
+# (3, 10), (5, 6), (7, 5): a low pass and a high pass of 16-byte elements
+@pytest.mark.parametrize("p,m", [(3, 7), (5, 4), (2, 16), (3, 10), (5, 6), (7, 5)])
 def test_double_precision(dwt, dev, orc, p, m):
     N = p ** m
     C = S.small_net(p, m, 2, index=1)
