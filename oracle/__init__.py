@@ -62,6 +62,9 @@ def lib():
         L.orc_rprime.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_uint32]
         L.orc_rprime.restype = ctypes.c_double
         L.orc_kernel_data.argtypes = [ctypes.c_int] * 3 + [_u32p, ctypes.c_double, _f64p, _f64p, _f64p, _f64p]
+        L.orc_spline_eval.argtypes = [ctypes.c_int] * 3 + [_u32p, _f64p, _u32p, ctypes.c_int, ctypes.c_int,
+                                                            ctypes.c_double, _f64p, _f64p]
+        L.orc_spline_eval.restype = None
         L.orc_kernel_shift_data.argtypes = [ctypes.c_int] * 3 + [_u32p, _u32p, ctypes.c_int, ctypes.c_double, _f64p,
                                                                   _f64p]
         _lib = L
@@ -329,6 +332,22 @@ def spline_values_shifted(p, m, Y, c, delta, M, alpha, gamma):
     kt = fwt(p, m, Kd)
     ct = fwt(p, m, c)
     return fiwt(p, m, N * ct * kt)
+
+
+def spline_eval(p, m, Y, c, X, M, alpha, gamma):
+    """The spline Sf(x) = sum_n c_n K(x (-) x_n, 0) at arbitrary points x_q
+    (Sec. 3.1): X[q][j] the M-digit numerators (x_{q,j} = X[q][j] / p^M, M >= m),
+    c the real spline coefficients on the net; direct sum over the net with the
+    short form of K' on M digits, O(N s) per point."""
+    Y = np.ascontiguousarray(Y, dtype=np.uint32)
+    s, N = Y.shape
+    X = np.ascontiguousarray(X, dtype=np.uint32).reshape(-1, s)
+    c = np.ascontiguousarray(np.real(c), dtype=np.float64)
+    g = np.ascontiguousarray(gamma, dtype=np.float64)
+    out = np.empty(X.shape[0])
+    lib().orc_spline_eval(p, m, s, _p(Y, _u32p), _p(c, _f64p), _p(X, _u32p), X.shape[0], M, alpha, _p(g, _f64p),
+                          _p(out, _f64p))
+    return out
 
 
 # --- synthetic test functions ------------------------------------------------

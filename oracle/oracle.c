@@ -763,6 +763,36 @@ void orc_kernel_data(int p, int m, int s, const uint32_t *Y, double alpha, const
     free(e);
 }
 
+/* The spline at arbitrary points (Sec. 3.1): for q = 0..Q-1,
+ *   out[q] = sum_n c[n] prod_j (1 + gamma_j K'(x_{q,j} (-) x_{j,n}, 0)),
+ * x_{q,j} = X[q s + j] / p^M with M >= m digits, x_{j,n} = Y[j][n] / p^m, and (-)
+ * the digit-wise difference mod p of the M-digit numerators (the net point's
+ * digits below the m-th are zero).  Direct sum, O(N s) per point.           */
+void orc_spline_eval(int p, int m, int s, const uint32_t *Y, const double *c, const uint32_t *X, int Q, int M,
+                     double alpha, const double *gamma, double *out)
+{
+    uint64_t N = ipow_u64(p, m);
+    uint64_t up = ipow_u64(p, M - m);
+    for (int q = 0; q < Q; ++q) {
+        double acc = 0.0;
+        for (uint64_t n = 0; n < N; ++n) {
+            double kv = 1.0;
+            for (int j = 0; j < s; ++j) {
+                uint64_t a = (uint64_t)X[(size_t)q * s + j], b = (uint64_t)Y[(size_t)j * N + n] * up, z = 0, pw = 1;
+                for (int d = 0; d < M; ++d) {          /* digit-wise difference mod p */
+                    z += ((a % (uint64_t)p + (uint64_t)p - b % (uint64_t)p) % (uint64_t)p) * pw;
+                    a /= (uint64_t)p;
+                    b /= (uint64_t)p;
+                    pw *= (uint64_t)p;
+                }
+                kv *= 1.0 + gamma[j] * orc_kprime(p, M, alpha, (uint32_t)z);
+            }
+            acc += c[n] * kv;
+        }
+        out[q] = acc;
+    }
+}
+
 /* Kernel data at digitally shifted points (Sec. 3.1 and 5.1): for w = 0..N-1,
  * Kd[w] = prod_j (1 + gamma_j K'(x_{j,w} (+) delta_j, 0)), where x_{j,w} = Y/p^m has
  * m digits, delta_j = D[j] / p^M has M >= m digits, and (+) adds digits mod p.  */

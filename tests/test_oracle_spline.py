@@ -142,3 +142,58 @@ def test_spline_values_at_shifted_points(orc, p, m, s, M):
     assert np.abs(got.imag).max() < 1e-10 * np.abs(ref).max()
     if np.all(delta == 0):
         assert np.allclose(got.real, f, rtol=1e-10)   # interpolation at the net itself
+
+
+def _shift_points(Y, delta, p, m, M):
+    up = p ** (M - m)
+    s, N = Y.shape
+    X = np.empty((N, s), dtype=np.uint32)
+    for n in range(N):
+        for j in range(s):
+            X[n, j] = _dadd(int(Y[j, n]) * up, int(delta[j]), p, M)
+    return X
+
+
+@pytest.mark.parametrize("p,m,s,M", [(2, 5, 3, 5), (2, 4, 2, 7), (3, 3, 2, 4), (5, 2, 3, 3)])
+def test_spline_eval_interpolates_and_matches_shifted_route(orc, p, m, s, M):
+    """The direct sum at the net points returns f (the interpolation conditions,
+    with c from the DWT solve), and at shifted points x_n (+) delta it equals the
+    convolution route of spline_values_shifted."""
+    C = S.small_net(p, m, s, index=140 + m)
+    Y = orc.net_points(p, m, C)
+    gamma = 0.8 / np.arange(1, s + 1) ** 1.5
+    alpha = 2.0
+    f = orc.eval_product(p, m, Y, 0.3 + 0.2 * np.arange(s))
+    c = orc.spline(p, m, Y, f, alpha, gamma)["c"].real
+    up = p ** (M - m)
+    at_net = orc.spline_eval(p, m, Y, c, (Y.T.astype(np.uint64) * up).astype(np.uint32), M, alpha, gamma)
+    assert np.allclose(at_net, f, rtol=1e-10, atol=1e-12)
+    delta = S.integers(S.stream_seed(62, S.P_SAMPLE, m), s, 0, p ** M - 1).astype(np.uint32)
+    got = orc.spline_eval(p, m, Y, c, _shift_points(Y, delta, p, m, M), M, alpha, gamma)
+    ref = orc.spline_values_shifted(p, m, Y, c, delta, M, alpha, gamma).real
+    assert np.allclose(got, ref, rtol=1e-10, atol=1e-12 * np.abs(ref).max())
+
+
+@pytest.mark.parametrize("p,m,s,M", [(2, 4, 3, 9), (3, 3, 2, 6), (5, 2, 2, 4)])
+def test_spline_eval_reproduces_kernel_sections(orc, p, m, s, M):
+    """The spline of a kernel section f = K(. (-) x_v, 0) sampled on the net is
+    that section itself (it lies in the span of the interpolant), so at points
+    off the net the direct sum must return K(x (-) x_v, 0)."""
+    C = S.small_net(p, m, s, index=150 + m)
+    Y = orc.net_points(p, m, C)
+    N = p ** m
+    gamma = np.linspace(0.9, 0.4, s)
+    alpha = 1.7
+    v = N // 3
+    f = np.array([np.prod([1.0 + gamma[j] * orc.kprime(p, m, alpha, _dsub(int(Y[j, n]), int(Y[j, v]), p, m))
+                           for j in range(s)]) for n in range(N)])
+    c = orc.spline(p, m, Y, f, alpha, gamma)["c"].real
+    unit = np.zeros(N)
+    unit[v] = 1.0
+    assert np.allclose(c, unit, atol=1e-9)
+    X = S.integers(S.stream_seed(63, S.P_SAMPLE, p), 40 * s, 0, p ** M - 1).astype(np.uint32).reshape(40, s)
+    got = orc.spline_eval(p, m, Y, c, X, M, alpha, gamma)
+    up = p ** (M - m)
+    ref = np.array([np.prod([1.0 + gamma[j] * orc.kprime(p, M, alpha, _dsub(int(X[q, j]), int(Y[j, v]) * up, p, M))
+                             for j in range(s)]) for q in range(40)])
+    assert np.allclose(got, ref, rtol=1e-9, atol=1e-12)
