@@ -264,6 +264,7 @@ def run_other_configs(dwt, dev, stream, timed, steps):
     """Throughput of the transforms at the other workload shapes: p = 2, m = 20,
     s = 16 with 32 FP32 and 32 int32 functions (forward, inverse, round trip) and
     p = 3, m = 13, s = 8 (real FP32 in, complex FP32 out; forward and inverse)."""
+    import numpy as np
     import torch
 
     import synthetic as S
@@ -327,12 +328,30 @@ def run_other_configs(dwt, dev, stream, timed, steps):
         dwt.dwt_spline_values_shifted(plan2, cs, delta, 21, vals, 32, N2, fs, sse, stream=stream)
 
     ms_h, _ = timed(hold, steps)
+    # the spline at 256 arbitrary points (24 digits per coordinate), direct sums
+    # over the net: s kernel factors and one multiply-add per function for every
+    # (point, net point) pair, all FP64
+    Qe = 256
+    Xe = torch.from_numpy(S.integers(S.stream_seed(2, S.P_SAMPLE, 99), Qe * 16, 0, (1 << 24) - 1)
+                          .astype(np.uint32).view(np.int32).reshape(Qe, 16)).to(dev)
+    ve = torch.empty((32, Qe), dtype=torch.float64, device=dev)
+
+    def ev():
+        dwt.dwt_spline_eval(plan2, cs, 32, N2, Xe, Qe, 24, ve, stream=stream)
+
+    ms_e, _ = timed(ev, max(1, steps // 10))
+    ne = max(1, steps // 10)
+    fp64_ops = (16 + 32) * Qe * N2 * ne / (ms_e / 1e3)
     out["spline_p2_m20_s16_b32"] = {"points_per_s": 32 * N2 * steps / (ms_s / 1e3), "dtype": "f64",
                                     "alpha": 2.0, "gamma": "0.9 / j^1.2",
                                     "holdout_points_per_s": 32 * N2 * steps / (ms_h / 1e3),
+                                    "eval_at_points": {"points": Qe, "functions": 32, "digits": 24,
+                                                       "ms": ms_e / ne,
+                                                       "function_values_per_s": 32 * Qe * ne / (ms_e / 1e3),
+                                                       "fp64_mul_per_s": fp64_ops},
                                     "dots_kernel": {"achieved_gbs": dots_gbs, "bytes_per_point": (2 * 16 + 1) * 8,
                                                     "frac": dots_gbs / _peaks()[0] if dots_gbs else None}}
-    del fs, cs, vals
+    del fs, cs, vals, ve
     w = S.workload_p3_m13()
     p, m, s = w["p"], w["m"], w["s"]
     N = p ** m

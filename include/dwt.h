@@ -250,6 +250,28 @@ int dwt_spline_values_shifted(dwt_plan_t plan, const void *c, const uint32_t *de
                               int batch, long long ld, const double *f_shift, double *sse, void *stream);
 
 /*
+ * The spline at arbitrary points (Sec. 3.1): for each function b and point q,
+ *   values[b][q] = sum_n Re c[b][n] K(x_q (-) x_n, 0),
+ *   K(x, 0) = prod_j (1 + gamma_j K'(x_j, 0)), K' by its short form (Sec. 4)
+ * on M digits: it depends only on the first base-p digit where x_{q,j} and
+ * x_{j,n} differ (or, when their top m digits agree, the first nonzero digit
+ * of x_{q,j} below them).  A direct sum over the net, O(N s) per point and
+ * function, FP64.
+ *   c: device spline coefficients [batch][ld] from dwt_spline (double for
+ *      p = 2, complex double for p > 2, whose real parts are used);
+ *   X: device uint32 [Q][s], x_{q,j} = X[q][j] / p^M, m <= M, p^M <= 2^32
+ *      (entries are read modulo p^M);
+ *   values: device double output [batch][ldv], ldv >= Q.
+ * The net is split into chunks summed by separate blocks; the chunk sums are
+ * added in chunk order, so results are reproducible for a given device.
+ * Uses the kernel of the last dwt_spline_prepare (DWT_EINVAL without one);
+ * DWT_EINVAL for M < m or p^M > 2^32.  Allocates its scratch (12 s N bytes
+ * plus the chunk sums) in stream order.
+ */
+int dwt_spline_eval(dwt_plan_t plan, const void *c, int batch, long long ld, const uint32_t *X, int Q, int M,
+                    double *values, long long ldv, void *stream);
+
+/*
  * Effective dimension of given coefficients g (Sec. 4), the variance and
  * threshold part of dwt_interpolate alone.  coef: device, type DWT_F32
  * (p = 2) or DWT_C64, ld elements per function.  var/dim as above (device).

@@ -80,6 +80,7 @@ _SIGS = {
     "dwt_spline_prepare": (_I, [_VP, ctypes.c_double, _VP, _VP]),
     "dwt_spline": (_I, [_VP, _VP, _VP, _I, _LL, _VP, _VP, _VP, ctypes.c_double, _VP]),
     "dwt_spline_values_shifted": (_I, [_VP, _VP, _VP, _I, _VP, _I, _LL, _VP, _VP, _VP]),
+    "dwt_spline_eval": (_I, [_VP, _VP, _I, _LL, _VP, _I, _I, _VP, _LL, _VP]),
     "dwt_effdim": (_I, [_VP, _VP, _I, _LL, _I, _VP, _VP, ctypes.c_double, _VP]),
     "dwt_effdim_static": (_I, [_VP, _VP, _I, _LL, _I, _VP, _VP, ctypes.c_double, _VP]),
     "dwt_eval_product": (_I, [_VP, _VP, _VP, _I, _LL, _I, _VP]),
@@ -270,6 +271,12 @@ def dwt_spline_values_shifted(plan, c, delta, M, values, batch, ld, f_shift=None
     d = np.ascontiguousarray(delta, dtype=np.uint32)
     return _check(lib().dwt_spline_values_shifted(plan.handle, _ptr(c), d.ctypes.data, int(M), _ptr(values), batch, ld,
                                                   _ptr(f_shift), _ptr(sse), _stream(stream)))
+
+
+def dwt_spline_eval(plan, c, batch, ld, X, Q, M, values, ldv=None, stream=None):
+    """Spline values at Q arbitrary points X (device uint32 [Q][s], M digits) into values [batch][ldv]."""
+    return _check(lib().dwt_spline_eval(plan.handle, _ptr(c), batch, ld, _ptr(X), int(Q), int(M), _ptr(values),
+                                        Q if ldv is None else ldv, _stream(stream)))
 
 
 def dwt_effdim(plan, coef, batch, ld, t, var=None, dim=None, threshold=0.99, stream=None):

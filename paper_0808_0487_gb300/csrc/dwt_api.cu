@@ -574,6 +574,16 @@ int dwt_spline_values_shifted(dwt_plan_t P, const void* c, const uint32_t* delta
     return run_spline_shifted(P, c, delta, M, values, batch, ld, f_shift, sse, (cudaStream_t)stream);
 }
 
+int dwt_spline_eval(dwt_plan_t P, const void* c, int batch, long long ld, const uint32_t* X, int Q, int M,
+                    double* values, long long ldv, void* stream) {
+    if (!P || batch < 0 || Q < 0 || ld < P->N || ldv < Q || (batch > 0 && Q > 0 && (!c || !X || !values))) {
+        set_error("dwt_spline_eval: bad arguments");
+        return DWT_EINVAL;
+    }
+    if (batch == 0 || Q == 0) return DWT_OK;
+    return run_spline_eval(P, c, batch, ld, X, Q, M, values, ldv, (cudaStream_t)stream);
+}
+
 int dwt_spline(dwt_plan_t P, const double* f, void* c, int batch, long long ld, double* var_trc, double* var_sup,
                int* dim, double thr, void* stream) {
     if (!P || batch < 0 || (batch > 0 && !f) || ld < P->N || !(thr > 0.0 && thr <= 1.0)) {

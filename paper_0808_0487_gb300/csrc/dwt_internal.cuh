@@ -133,6 +133,8 @@ int run_spline_prepare(dwt_plan_s* P, double alpha, const double* gamma, cudaStr
 int run_spline(dwt_plan_s* P, const double* f, void* c, int batch, long long ld, double* var_trc, double* var_sup,
                int* dim, double thr, cudaStream_t st);
 void spline_free(dwt_plan_s* P, cudaStream_t st, bool sync);
+int run_spline_eval(dwt_plan_s* P, const void* c, int batch, long long ld, const uint32_t* X, int Q, int M,
+                    double* values, long long ldv, cudaStream_t st);
 int run_spline_shifted(dwt_plan_s* P, const void* c, const uint32_t* delta, int M, void* values, int batch,
                        long long ld, const double* f_shift, double* sse, cudaStream_t st);
 int run_points(dwt_plan_s* P, uint32_t* Y, long long ldY, cudaStream_t st);

@@ -267,6 +267,118 @@ __global__ void k_spline_sse_final(const double* __restrict__ part, long long nt
     sse[b] = x;
 }
 
+// ---- the spline at arbitrary points (Sec. 3.1) ----------------------------
+// K(x (-) x_n, 0) = prod_j (1 + gamma_j K'(x_j (-) x_{j,n}, 0)), and K' depends
+// only on the position i of the first nonzero digit of the difference: the
+// first digit (of m) where x_j and the net point differ, or, when the top m
+// digits agree, the first nonzero digit of x_j below them (0 if none).  With
+// the base-p digits packed BP bits each (1, 2, 3, 4 bits for p = 2, 3, 5 / 7,
+// 11 / 13), the first differing digit is the highest set bit of an XOR.
+constexpr int kEvalQB = 128;   // points per block, one per thread
+constexpr int kEvalFB = 8;     // functions per block
+
+__host__ __device__ inline int eval_bits(int p) { return p == 2 ? 1 : p == 3 ? 2 : p <= 7 ? 3 : 4; }
+
+__device__ __forceinline__ unsigned long long pack_digits(uint32_t v, int p, int m, int bp) {
+    unsigned long long r = 0;
+    for (int k = 0; k < m; ++k) {
+        r |= (unsigned long long)(v % (uint32_t)p) << (bp * k);
+        v /= (uint32_t)p;
+    }
+    return r;
+}
+
+// packed top-m digits of the net points, [s][N]
+__global__ void k_eval_pack(const uint32_t* __restrict__ Y, long long total, int p, int m,
+                            unsigned long long* __restrict__ PY) {
+    const int bp = eval_bits(p);
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total; e += (long long)gridDim.x * blockDim.x)
+        PY[e] = p == 2 ? (unsigned long long)Y[e] : pack_digits(Y[e], p, m, bp);
+}
+
+// Partial sums over one chunk of the net (blockIdx.z) for kEvalQB points
+// (blockIdx.x) and kEvalFB functions (blockIdx.y):
+//   part[z][f][q] = sum_{n in chunk} Re c[f][n] prod_j T[j][i_j(q, n)],
+// T[j][i] = 1 + gamma_j K'(i) (i = 0 .. M).  The net points and coefficients
+// of the chunk pass through shared memory in tiles of TN; each thread keeps
+// its point's packed digits and tail positions in shared memory too.
+__global__ void __launch_bounds__(kEvalQB) k_spline_eval(const unsigned long long* __restrict__ PY, long long N,
+                                                          const double* __restrict__ c, long long ldc, int cstride,
+                                                          int batch, const uint32_t* __restrict__ X, int Q, int s,
+                                                          int p, int m, int M, const double* __restrict__ Tg,
+                                                          long long chunk, int TN, double* __restrict__ part) {
+    extern __shared__ __align__(16) unsigned char smraw[];
+    const int M1 = M + 1;
+    double* T = reinterpret_cast<double*>(smraw);                                   // [s][M+1]
+    unsigned long long* PX = reinterpret_cast<unsigned long long*>(T + (size_t)s * M1);   // [s][QB]
+    unsigned long long* PYs = PX + (size_t)s * kEvalQB;                             // [s][TN]
+    double* cs = reinterpret_cast<double*>(PYs + (size_t)s * TN);                   // [FB][TN]
+    unsigned char* tl = reinterpret_cast<unsigned char*>(cs + (size_t)kEvalFB * TN);   // [s][QB]
+    const int t = threadIdx.x;
+    const int q = blockIdx.x * kEvalQB + t;
+    const int f0 = blockIdx.y * kEvalFB;
+    const int nf = min(kEvalFB, batch - f0);
+    const int bp = eval_bits(p);
+    for (int e = t; e < s * M1; e += blockDim.x) T[e] = Tg[e];
+    {
+        uint32_t up = 1;
+        for (int k = 0; k < M - m; ++k) up *= (uint32_t)p;
+        for (int j = 0; j < s; ++j) {
+            const uint32_t x = q < Q ? X[(long long)q * s + j] : 0u;
+            const uint32_t top = up > 1 ? x / up : x, tail = up > 1 ? x % up : 0u;
+            PX[j * kEvalQB + t] = p == 2 ? (unsigned long long)top : pack_digits(top, p, m, bp);
+            int tp = 0;   // first nonzero digit of the tail, as a position in 1..M
+            if (tail) {
+                int e = 0;
+                for (uint32_t v = tail; v >= (uint32_t)p; v /= (uint32_t)p) ++e;
+                tp = M - e;
+            }
+            tl[j * kEvalQB + t] = (unsigned char)tp;
+        }
+    }
+    double acc[kEvalFB];
+#pragma unroll
+    for (int f = 0; f < kEvalFB; ++f) acc[f] = 0.0;
+    const long long n0 = blockIdx.z * chunk, n1 = min(N, n0 + chunk);
+    for (long long nb = n0; nb < n1; nb += TN) {
+        const int tn = (int)min((long long)TN, n1 - nb);
+        __syncthreads();   // the previous tile is consumed (and the tables above are written)
+        for (int e = t; e < s * TN; e += blockDim.x) {
+            const int j = e / TN, u = e - j * TN;
+            PYs[e] = u < tn ? PY[(long long)j * N + nb + u] : 0ull;
+        }
+        for (int e = t; e < kEvalFB * TN; e += blockDim.x) {
+            const int f = e / TN, u = e - f * TN;
+            cs[e] = (f < nf && u < tn) ? c[(long long)(f0 + f) * ldc + (nb + u) * cstride] : 0.0;
+        }
+        __syncthreads();
+        for (int u = 0; u < tn; ++u) {
+            double prod = 1.0;
+            for (int j = 0; j < s; ++j) {
+                const unsigned long long d = PX[j * kEvalQB + t] ^ PYs[j * TN + u];
+                const int i = d ? m - (63 - __clzll((long long)d)) / bp : (int)tl[j * kEvalQB + t];
+                prod *= T[j * M1 + i];
+            }
+#pragma unroll
+            for (int f = 0; f < kEvalFB; ++f) acc[f] = fma(cs[f * TN + u], prod, acc[f]);
+        }
+    }
+    if (q < Q) {
+        for (int f = 0; f < nf; ++f) part[((long long)blockIdx.z * batch + f0 + f) * Q + q] = acc[f];
+    }
+}
+
+// values[f][q] = sum over the chunks in order
+__global__ void k_spline_eval_reduce(const double* __restrict__ part, int nch, int batch, int Q,
+                                     double* __restrict__ values, long long ldv) {
+    const long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (e >= (long long)batch * Q) return;
+    const long long f = e / Q, q = e - f * Q;
+    double a = 0.0;
+    for (int z = 0; z < nch; ++z) a += part[(long long)z * batch * Q + e];
+    values[f * ldv + q] = a;
+}
+
 unsigned grid_sp(long long n) { return (unsigned)std::max(1ll, std::min((n + 255) / 256, 8ll * 152)); }
 
 }  // namespace
@@ -417,6 +529,80 @@ int run_spline_shifted(dwt_plan_s* P, const void* c, const uint32_t* delta, int 
         k_spline_sse_final<<<(batch + 127) / 128, 128, 0, st>>>(part, ntile, batch, sse);
     }
     DWT_CK_LAUNCH("k_spline_sse");
+    cleanup();
+    return DWT_OK;
+}
+
+int run_spline_eval(dwt_plan_s* P, const void* c, int batch, long long ld, const uint32_t* X, int Q, int M,
+                    double* values, long long ldv, cudaStream_t st) {
+    if (!P->d_splW) {
+        set_error("dwt_spline_eval: no kernel (call dwt_spline_prepare first)");
+        return DWT_EINVAL;
+    }
+    const long long N = P->N;
+    const int s = P->s, p = P->p, m = P->m;
+    if (M < m || (double)M * std::log2((double)p) > 32.0) {
+        set_error("dwt_spline_eval: need m <= M and p^M <= 2^32");
+        return DWT_EINVAL;
+    }
+    if (Q == 0) return DWT_OK;
+    // T[j][i] = 1 + gamma_j K'(i) on M digits
+    const double alpha = P->spl_alpha;
+    const double pa = std::pow((double)p, alpha);
+    std::vector<double> hT((size_t)s * (M + 1));
+    for (int j = 0; j < s; ++j)
+        for (int i = 0; i <= M; ++i) {
+            const double kp = i == 0 ? 1.0 : 1.0 - std::pow((double)p, i * (1.0 - alpha)) * (pa - 1.0) / (p - 1.0);
+            hT[(size_t)j * (M + 1) + i] = 1.0 + P->spl_gamma[j] * kp;
+        }
+    // tiles of the net: TN points, within the shared-memory budget
+    const int TN = s > 32 ? 64 : 128;
+    const size_t smem = (size_t)s * (M + 1) * 8 + (size_t)s * kEvalQB * 8 + (size_t)s * TN * 8 +
+                        (size_t)kEvalFB * TN * 8 + (size_t)s * kEvalQB;
+    int dev = 0, sms = 0;
+    DWT_CK(cudaGetDevice(&dev));
+    DWT_CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    const int qb = (Q + kEvalQB - 1) / kEvalQB, fb = (batch + kEvalFB - 1) / kEvalFB;
+    const long long ntn = (N + TN - 1) / TN;
+    long long nch = std::max(1ll, std::min(ntn, (4ll * sms + (long long)qb * fb - 1) / ((long long)qb * fb)));
+    nch = std::min(nch, 65535ll);
+    const long long chunk = (ntn + nch - 1) / nch * TN;
+    nch = (N + chunk - 1) / chunk;
+    if (fb > 65535 || qb > (1 << 30)) {
+        set_error("dwt_spline_eval: too many functions in one call");
+        return DWT_EINVAL;
+    }
+    uint32_t* Y = nullptr;
+    unsigned long long* PY = nullptr;
+    double *dT = nullptr, *part = nullptr;
+    auto cleanup = [&]() { dfree(Y, st); dfree(PY, st); dfree(dT, st); dfree(part, st); };
+    if (dmalloc((void**)&Y, (size_t)s * N * 4, st) || dmalloc((void**)&PY, (size_t)s * N * 8, st) ||
+        dmalloc((void**)&dT, hT.size() * 8, st) || dmalloc((void**)&part, (size_t)nch * batch * Q * 8, st)) {
+        cleanup();
+        return DWT_ENOMEM;
+    }
+    DWT_CK(cudaMemcpyAsync(dT, hT.data(), hT.size() * 8, cudaMemcpyHostToDevice, st));
+    int rc = run_points(P, Y, N, st);
+    if (rc) { cleanup(); return rc; }
+    {
+        LaunchScope ls("spline_eval_pack", st);
+        k_eval_pack<<<grid_sp((long long)s * N), 256, 0, st>>>(Y, (long long)s * N, p, m, PY);
+    }
+    DWT_CK_LAUNCH("k_eval_pack");
+    if ((rc = smem_limit_max(k_spline_eval))) { cleanup(); return rc; }
+    {
+        LaunchScope ls("spline_eval", st);
+        k_spline_eval<<<dim3((unsigned)qb, (unsigned)fb, (unsigned)nch), kEvalQB, smem, st>>>(
+            PY, N, reinterpret_cast<const double*>(c), (p == 2 ? 1 : 2) * ld, p == 2 ? 1 : 2, batch, X, Q, s, p, m, M,
+            dT, chunk, TN, part);
+    }
+    DWT_CK_LAUNCH("k_spline_eval");
+    {
+        LaunchScope ls("spline_eval_reduce", st);
+        const long long tot = (long long)batch * Q;
+        k_spline_eval_reduce<<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(part, (int)nch, batch, Q, values, ldv);
+    }
+    DWT_CK_LAUNCH("k_spline_eval_reduce");
     cleanup();
     return DWT_OK;
 }

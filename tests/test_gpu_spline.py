@@ -94,3 +94,63 @@ def test_spline_values_shifted(dwt, dev, orc, p, m, s, M, B):
         assert rel_l2(vg[b].real, ref) < tol
         err = float(((fs[::-1][b] - ref) ** 2).sum())
         assert sse.cpu().numpy()[b] == pytest.approx(err, rel=max(1e-8, 10 * tol), abs=1e-14)
+
+
+# (2, 8, 40, 20, 9, 130): s > 32 (narrower net tiles), two function blocks and
+# two point blocks; (2, 12, 3, 12, 1, 129): M = m (no digits below the net's)
+@pytest.mark.parametrize("p,m,s,M,B,Q", [(2, 10, 4, 14, 2, 300), (2, 12, 3, 12, 1, 129), (3, 6, 3, 9, 1, 200),
+                                         (5, 4, 3, 6, 2, 150), (7, 4, 2, 5, 1, 64), (13, 3, 2, 4, 1, 50),
+                                         (2, 8, 40, 20, 9, 130), (3, 5, 2, 20, 3, 257)])
+def test_spline_eval_matches_oracle(dwt, dev, orc, p, m, s, M, B, Q):
+    """Sf at arbitrary points against the oracle's direct sum, both from the
+    oracle's coefficients (so only the evaluation is compared)."""
+    N = p ** m
+    ld = N + 3
+    C = S.small_net(p, m, s, index=230 + m)
+    Y = orc.net_points(p, m, C)
+    gamma = 0.8 / np.arange(1, s + 1) ** 1.3
+    alpha = 1.8
+    coefs = S.uniform(S.stream_seed(64, S.P_COEFFS, m), B * s).reshape(B, s)
+    cs = np.stack([orc.spline(p, m, Y, orc.eval_product(p, m, Y, coefs[b]), alpha, gamma)["c"] for b in range(B)])
+    X = S.integers(S.stream_seed(65, S.P_SAMPLE, m), Q * s, 0, p ** M - 1).astype(np.uint32).reshape(Q, s)
+    X[0] = (Y[:, N // 2].astype(np.uint64) * p ** (M - m)).astype(np.uint32)   # a net point itself
+    plan = dwt.dwt_plan_create(p, m, s, C, dwt.DWT_PLAN_TRANSFORM_ONLY)
+    dwt.dwt_spline_prepare(plan, alpha, gamma)
+    cdt = torch.float64 if p == 2 else torch.complex128
+    c = torch.zeros((B, ld), dtype=cdt, device=dev)
+    c[:, :N] = torch.from_numpy(cs if p != 2 else cs.real.copy())
+    Xd = torch.from_numpy(X.view(np.int32)).to(dev)
+    vals = torch.full((B, Q + 5), np.nan, dtype=torch.float64, device=dev)
+    dwt.dwt_spline_eval(plan, c, B, ld, Xd, Q, M, vals, Q + 5)
+    vg = vals.cpu().numpy()
+    kmax = np.prod(1.0 + gamma)
+    for b in range(B):
+        ref = orc.spline_eval(p, m, Y, cs[b].real, X, M, alpha, gamma)
+        scale = np.abs(cs[b].real).sum() * kmax
+        assert np.allclose(vg[b, :Q], ref, rtol=1e-12, atol=1e-13 * scale)
+        assert np.all(np.isnan(vg[b, Q:]))
+
+
+def test_spline_eval_full_size_sampled(dwt, dev, orc):
+    """p = 2, m = 20, s = 16, a batch of 32 and 256 points (the timed launch
+    shape): eight points checked against the oracle's direct sum."""
+    w = S.workload_p2_m20()
+    p, m, s, C = w["p"], w["m"], 16, w["C"][:16]
+    N, B, Q, M = 2 ** m, 32, 256, 24
+    Y = orc.net_points(p, m, C)
+    gamma = 0.9 / np.arange(1, s + 1) ** 1.2
+    alpha = 2.0
+    f = orc.eval_product(p, m, Y, w["coef"][0][:s])
+    c0 = orc.spline(p, m, Y, f, alpha, gamma)["c"].real
+    X = S.integers(S.stream_seed(66, S.P_SAMPLE, 0), Q * s, 0, 2 ** 24 - 1).astype(np.uint32).reshape(Q, s)
+    plan = dwt.dwt_plan_create(p, m, s, C, dwt.DWT_PLAN_TRANSFORM_ONLY)
+    dwt.dwt_spline_prepare(plan, alpha, gamma)
+    c = torch.from_numpy(c0).to(dev).unsqueeze(0).repeat(B, 1).contiguous()
+    vals = torch.empty((B, Q), dtype=torch.float64, device=dev)
+    dwt.dwt_spline_eval(plan, c, B, N, torch.from_numpy(X.view(np.int32)).to(dev), Q, M, vals)
+    vg = vals.cpu().numpy()
+    pick = S.sample_indices(8, Q, index=3)
+    ref = orc.spline_eval(p, m, Y, c0, X[pick], M, alpha, gamma)
+    scale = np.abs(c0).sum() * np.prod(1.0 + gamma)
+    for b in (0, 13, 31):
+        assert np.allclose(vg[b, pick], ref, rtol=1e-12, atol=1e-13 * scale)
