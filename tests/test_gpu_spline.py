@@ -154,3 +154,22 @@ def test_spline_eval_full_size_sampled(dwt, dev, orc):
     scale = np.abs(c0).sum() * np.prod(1.0 + gamma)
     for b in (0, 13, 31):
         assert np.allclose(vg[b, pick], ref, rtol=1e-12, atol=1e-13 * scale)
+
+
+def test_spline_eval_rejects_bad_calls(dwt, dev):
+    p, m, s = 3, 4, 2
+    N = p ** m
+    plan = dwt.dwt_plan_create(p, m, s, S.small_net(p, m, s, index=2), dwt.DWT_PLAN_TRANSFORM_ONLY)
+    c = torch.zeros(N, dtype=torch.complex128, device=dev)
+    X = torch.zeros((4, s), dtype=torch.int32, device=dev)
+    v = torch.empty(4, dtype=torch.float64, device=dev)
+    with pytest.raises(dwt.DwtError):           # no dwt_spline_prepare yet
+        dwt.dwt_spline_eval(plan, c, 1, N, X, 4, 6, v)
+    dwt.dwt_spline_prepare(plan, 2.0, np.ones(s))
+    with pytest.raises(dwt.DwtError):           # M < m
+        dwt.dwt_spline_eval(plan, c, 1, N, X, 4, m - 1, v)
+    with pytest.raises(dwt.DwtError):           # 3^21 > 2^32
+        dwt.dwt_spline_eval(plan, c, 1, N, X, 4, 21, v)
+    dwt.dwt_spline_eval(plan, c, 1, N, X, 0, 6, v)   # no points: nothing to do
+    dwt.dwt_spline_eval(plan, c, 1, N, X, 4, 6, v)
+    assert np.all(v.cpu().numpy() == 0.0)        # zero coefficients
