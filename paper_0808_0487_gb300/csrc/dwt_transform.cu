@@ -555,7 +555,15 @@ __global__ void __launch_bounds__(256) k_effdim_classes(const double* __restrict
     const long long fn = blockIdx.y;
     const double* pp = part + (fn * nb2 + bi) * nchunk;
     double acc = 0.0;
-    for (long long t = threadIdx.x; t < nchunk; t += 256) acc += pp[t];
+    long long t = threadIdx.x;
+    for (; t + 3 * 256 < nchunk; t += 4 * 256) {   // four loads in flight, added in order
+        const double a0 = pp[t], a1 = pp[t + 256], a2 = pp[t + 512], a3 = pp[t + 768];
+        acc += a0;
+        acc += a1;
+        acc += a2;
+        acc += a3;
+    }
+    for (; t < nchunk; t += 256) acc += pp[t];
     red[threadIdx.x] = acc;
     __syncthreads();
     for (int o = 128; o > 0; o >>= 1) {
@@ -566,19 +574,25 @@ __global__ void __launch_bounds__(256) k_effdim_classes(const double* __restrict
 }
 
 // per-class totals -> cumulative truncation / superposition variances and dimensions
-__global__ void k_effdim_finalize(const double* __restrict__ csum, int nb, double thr, double* var, int* dim,
-                                  int batch) {
-    const int fn = blockIdx.x * blockDim.x + threadIdx.x;
+__global__ void __launch_bounds__(32) k_effdim_finalize(const double* __restrict__ csum, int nb, double thr,
+                                                         double* __restrict__ var, int* __restrict__ dim, int batch) {
+    // one warp per function: the class totals come into shared memory together,
+    // then lane 0 forms the cumulative sums in class order
+    __shared__ double c[2 * 256];
+    const int fn = blockIdx.x;
     if (fn >= batch) return;
     const double* cs_ = csum + (long long)fn * 2 * nb;
+    for (int i = threadIdx.x; i < 2 * nb; i += 32) c[i] = cs_[i];
+    __syncwarp();
+    if (threadIdx.x != 0) return;
     double tot = 0.0;
-    for (int d = 0; d < nb; ++d) tot += cs_[d];
+    for (int d = 0; d < nb; ++d) tot += c[d];
     double ct = 0.0, cs = 0.0;
     int dt = 0, ds = 0;
     bool ft = false, fs = false;
     for (int d = 0; d < nb; ++d) {
-        ct += cs_[d];
-        cs += cs_[nb + d];
+        ct += c[d];
+        cs += c[nb + d];
         if (var) {
             var[((long long)fn * 2 + 0) * nb + d] = ct;
             var[((long long)fn * 2 + 1) * nb + d] = cs;
@@ -768,7 +782,7 @@ static int finalize(dwt_plan_s* Pl, const double* part, long long nchunk, int ba
     DWT_CK_LAUNCH("k_effdim_classes");
     {
         LaunchScope ls("effdim_finalize", st);
-        k_effdim_finalize<<<(batch + 127) / 128, 128, 0, st>>>(csum, nb, thr, var, dim, batch);
+        k_effdim_finalize<<<batch, 32, 0, st>>>(csum, nb, thr, var, dim, batch);
     }
     DWT_CK_LAUNCH("k_effdim_finalize");
     return DWT_OK;
