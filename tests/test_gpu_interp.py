@@ -190,3 +190,28 @@ def _read_W(dwt, plan, N):
     torch.cuda.synchronize()
     assert rt.cudaMemcpy(W.ctypes.data, Wp, 4 * N, 2) == 0
     return W
+
+
+@pytest.mark.parametrize("p,m,s", [(3, 9, 4), (5, 6, 3)])
+def test_interpolate_p_odd_unweighted(dwt, dev, orc, p, m, s):
+    """Weight 1 through the generic fused pass: c returns f (the interpolation
+    property of the inverse, Lemma 3.1), and the class variances are those of
+    f~ itself."""
+    N = p ** m
+    C = S.small_net(p, m, s, index=70 + p)
+    plan = dwt.dwt_plan_create(p, m, s, C)
+    f = orc.eval_exp(p, m, orc.net_points(p, m, C))
+    tab = orc.coset_leaders_dp(p, m, C)
+    cref, g, vt, vs, dt, ds = orc.interpolate(p, m, f, np.ones(N), tab["cls"], s)
+    fin = torch.tensor(f.astype(np.float32), device=dev)
+    c = torch.empty(2 * N, device=dev)
+    var = torch.empty((1, 2, s + 1), dtype=torch.float64, device=dev)
+    dim = torch.empty((1, 2), dtype=torch.int32, device=dev)
+    dwt.dwt_interpolate(plan, fin, c, None, 1, N, dwt.DWT_F32, dwt.DWT_WEIGHT_NONE, var=var, dim=dim)
+    got = _cplx(_np(c))
+    assert rel_l2(got.real, f) < 1e-5
+    assert np.abs(got.imag).max() < 1e-5 * np.abs(f).max()
+    v = _np(var)[0]
+    assert np.allclose(v[0], vt, rtol=1e-5, atol=1e-14 * vt[-1])
+    assert np.allclose(v[1], vs, rtol=1e-5, atol=1e-14 * vt[-1])
+    _check_dims(_np(dim)[0], dt, ds, vt, vs)

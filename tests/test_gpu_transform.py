@@ -219,3 +219,19 @@ def test_p2_unaligned_ld_takes_generic_path(dwt, dev, orc):
     got = _np(out)
     for b in range(2):
         assert rel_l2(got[b * ld:b * ld + N], orc.fwt(p, m, f[b * ld:b * ld + N]).real) < TOL32
+
+
+# int32 through the generic passes (m outside the register-tile range): one,
+# two and three passes, exact against the oracle's int64 form; values small
+# enough that N max|v| < 2^31
+@pytest.mark.parametrize("m,vmax", [(11, 1000), (15, 1000), (25, 60)])
+def test_p2_int32_generic_passes(dwt, dev, orc, m, vmax):
+    p, N = 2, 2 ** m
+    plan = dwt.dwt_plan_create(p, m, 2, S.small_net(p, m, 2, index=m), dwt.DWT_PLAN_TRANSFORM_ONLY)
+    iv = S.integers(S.stream_seed(28, S.P_INTS, m), N, -vmax, vmax)
+    ii = torch.tensor(iv.astype(np.int32), device=dev)
+    io = torch.empty_like(ii)
+    dwt.dwt_forward(plan, ii, io, 1, N, N, dwt.DWT_I32, dwt.DWT_I32)
+    assert np.array_equal(_np(io).astype(np.int64), orc.fwt_i64(m, iv))
+    dwt.dwt_inverse(plan, io, io, 1, N, N, dwt.DWT_I32, dwt.DWT_I32)
+    assert np.array_equal(_np(io).astype(np.int64), N * iv.astype(np.int64))
