@@ -302,11 +302,13 @@ __global__ void k_eval_pack(const uint32_t* __restrict__ Y, long long total, int
 // T[j][i] = 1 + gamma_j K'(i) (i = 0 .. M).  The net points and coefficients
 // of the chunk pass through shared memory in tiles of TN; each thread keeps
 // its point's packed digits and tail positions in shared memory too.
+template <int P>
 __global__ void __launch_bounds__(kEvalQB) k_spline_eval(const unsigned long long* __restrict__ PY, long long N,
                                                           const double* __restrict__ c, long long ldc, int cstride,
                                                           int batch, const uint32_t* __restrict__ X, int Q, int s,
-                                                          int p, int m, int M, const double* __restrict__ Tg,
+                                                          int m, int M, const double* __restrict__ Tg,
                                                           long long chunk, int TN, double* __restrict__ part) {
+    constexpr int p = P;
     extern __shared__ __align__(16) unsigned char smraw[];
     const int M1 = M + 1;
     double* T = reinterpret_cast<double*>(smraw);                                   // [s][M+1]
@@ -318,7 +320,7 @@ __global__ void __launch_bounds__(kEvalQB) k_spline_eval(const unsigned long lon
     const int q = blockIdx.x * kEvalQB + t;
     const int f0 = blockIdx.y * kEvalFB;
     const int nf = min(kEvalFB, batch - f0);
-    const int bp = eval_bits(p);
+    constexpr int bp = P == 2 ? 1 : P == 3 ? 2 : P <= 7 ? 3 : 4;   // eval_bits(P)
     for (int e = t; e < s * M1; e += blockDim.x) T[e] = Tg[e];
     {
         uint32_t up = 1;
@@ -353,12 +355,24 @@ __global__ void __launch_bounds__(kEvalQB) k_spline_eval(const unsigned long lon
         }
         __syncthreads();
         for (int u = 0; u < tn; ++u) {
-            double prod = 1.0;
-            for (int j = 0; j < s; ++j) {
-                const unsigned long long d = PX[j * kEvalQB + t] ^ PYs[j * TN + u];
-                const int i = d ? m - (63 - __clzll((long long)d)) / bp : (int)tl[j * kEvalQB + t];
-                prod *= T[j * M1 + i];
+            // two partial products (even and odd coordinates) keep two
+            // multiplication chains in flight
+            double pr0 = 1.0, pr1 = 1.0;
+            int j = 0;
+            for (; j + 1 < s; j += 2) {
+                const unsigned long long d0 = PX[j * kEvalQB + t] ^ PYs[j * TN + u];
+                const unsigned long long d1 = PX[(j + 1) * kEvalQB + t] ^ PYs[(j + 1) * TN + u];
+                const int i0 = d0 ? m - (63 - __clzll((long long)d0)) / bp : (int)tl[j * kEvalQB + t];
+                const int i1 = d1 ? m - (63 - __clzll((long long)d1)) / bp : (int)tl[(j + 1) * kEvalQB + t];
+                pr0 *= T[j * M1 + i0];
+                pr1 *= T[(j + 1) * M1 + i1];
             }
+            if (j < s) {
+                const unsigned long long d0 = PX[j * kEvalQB + t] ^ PYs[j * TN + u];
+                const int i0 = d0 ? m - (63 - __clzll((long long)d0)) / bp : (int)tl[j * kEvalQB + t];
+                pr0 *= T[j * M1 + i0];
+            }
+            const double prod = pr0 * pr1;
 #pragma unroll
             for (int f = 0; f < kEvalFB; ++f) acc[f] = fma(cs[f * TN + u], prod, acc[f]);
         }
@@ -589,11 +603,20 @@ int run_spline_eval(dwt_plan_s* P, const void* c, int batch, long long ld, const
         k_eval_pack<<<grid_sp((long long)s * N), 256, 0, st>>>(Y, (long long)s * N, p, m, PY);
     }
     DWT_CK_LAUNCH("k_eval_pack");
-    if ((rc = smem_limit_max(k_spline_eval))) { cleanup(); return rc; }
     {
+        auto kern = k_spline_eval<2>;
+        switch (p) {
+            case 3: kern = k_spline_eval<3>; break;
+            case 5: kern = k_spline_eval<5>; break;
+            case 7: kern = k_spline_eval<7>; break;
+            case 11: kern = k_spline_eval<11>; break;
+            case 13: kern = k_spline_eval<13>; break;
+            default: break;
+        }
+        if ((rc = smem_limit_max(kern))) { cleanup(); return rc; }
         LaunchScope ls("spline_eval", st);
-        k_spline_eval<<<dim3((unsigned)qb, (unsigned)fb, (unsigned)nch), kEvalQB, smem, st>>>(
-            PY, N, reinterpret_cast<const double*>(c), (p == 2 ? 1 : 2) * ld, p == 2 ? 1 : 2, batch, X, Q, s, p, m, M,
+        kern<<<dim3((unsigned)qb, (unsigned)fb, (unsigned)nch), kEvalQB, smem, st>>>(
+            PY, N, reinterpret_cast<const double*>(c), (p == 2 ? 1 : 2) * ld, p == 2 ? 1 : 2, batch, X, Q, s, m, M,
             dT, chunk, TN, part);
     }
     DWT_CK_LAUNCH("k_spline_eval");
