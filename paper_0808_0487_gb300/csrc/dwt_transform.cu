@@ -5,12 +5,13 @@
 // The transform of Sec. 2.2 is the Kronecker power over the m index digits of
 // the p-point DFT F[h][n] = omega^{-hn}: the sum over digit n_r touches nothing
 // but digit r, and the sums over different digits commute.  Digits are
-// therefore processed in passes of b digits each; a pass holds a tile of p^b
+// therefore processed in passes of b digits each; a pass covers a tile of p^b
 // "rows" (one per value of its digits) times Wc "columns" (consecutive values
-// of the digits below the pass) in shared memory, runs its b stages there, and
-// writes back.  Inside a tile every thread takes p^K elements that differ only
-// in K consecutive digits and runs those K stages in registers; groups of K
-// digits follow one another through shared memory.
+// of the digits below the pass).  Inside a tile every thread takes p^K elements
+// that differ only in K consecutive digits and runs those K stages in
+// registers; groups of K digits follow one another through shared memory, the
+// first read straight from global memory and the last, where the rows allow,
+// written straight back.
 #include <string.h>
 
 #include <type_traits>
@@ -175,69 +176,11 @@ template <int P, int NK, int SGN, typename T> struct RegStages<P, NK, NK, SGN, T
     static __device__ __forceinline__ void run(T*, const Tw&) {}
 };
 
-// stages on row digits g0 .. g0+K-1 of a tile of R rows x Wc columns in smem
-template <int P, int K, int SGN, typename T>
-__device__ __forceinline__ void group_stage(T* sm, int g0, int R, int wlog, const Tw& tw) {
-    constexpr int NK = cpow(P, K);
-    int Pg0 = 1;
-    for (int i = 0; i < g0; ++i) Pg0 *= P;
-    const int ntask = (R / NK) << wlog;
-    const int cmask = (1 << wlog) - 1;
-    for (int t = threadIdx.x; t < ntask; t += blockDim.x) {
-        const int c = t & cmask;
-        const int q = t >> wlog;
-        const int rl = q % Pg0, rh = q / Pg0;
-        const int r0 = rl + rh * Pg0 * NK;
-        T v[NK];
-#pragma unroll
-        for (int i = 0; i < NK; ++i) v[i] = sm[spad<T>(((r0 + i * Pg0) << wlog) + c)];
-        RegStages<P, NK, 1, SGN, T>::run(v, tw);
-#pragma unroll
-        for (int i = 0; i < NK; ++i) sm[spad<T>(((r0 + i * Pg0) << wlog) + c)] = v[i];
-    }
-}
-
-template <int P, int SGN, typename T, int KMAX>
-__device__ void tile_stages(T* sm, int b, int R, int wlog, const Tw& tw) {
-    int g0 = 0;
-    while (g0 < b) {
-        const int k = min(KMAX, b - g0);
-        switch (k) {
-            case 1: group_stage<P, 1, SGN, T>(sm, g0, R, wlog, tw); break;
-            case 2: if constexpr (KMAX >= 2) group_stage<P, 2, SGN, T>(sm, g0, R, wlog, tw); break;
-            case 3: if constexpr (KMAX >= 3) group_stage<P, 3, SGN, T>(sm, g0, R, wlog, tw); break;
-            case 4: if constexpr (KMAX >= 4) group_stage<P, 4, SGN, T>(sm, g0, R, wlog, tw); break;
-            case 5: if constexpr (KMAX >= 5) group_stage<P, 5, SGN, T>(sm, g0, R, wlog, tw); break;
-            default: break;
-        }
-        __syncthreads();
-        g0 += k;
-    }
-}
-
+// digits per register group: p^K elements per thread (27 complex FP32 at p = 3)
 template <int P, typename T> struct KMax {
     static constexpr int v = P == 2 ? (sizeof(T) == 8 ? 4 : 5)
                                     : (sizeof(T) == 8 ? (P == 3 ? 3 : P == 5 ? 2 : 1) : (P == 3 ? 2 : 1));
 };
-
-// global -> shared tile copy with 8 loads in flight per thread
-template <typename T, typename TI>
-__device__ __forceinline__ void load_tile(T* sm, const TI* in, int nel, int wlog, int cmask, int ncols, long long S) {
-    for (int e0 = threadIdx.x; e0 < nel; e0 += 8 * blockDim.x) {
-        T tmp[8];
-#pragma unroll
-        for (int u = 0; u < 8; ++u) {
-            const int e = e0 + u * blockDim.x;
-            const int r = e >> wlog, c = e & cmask;
-            tmp[u] = (e < nel && c < ncols) ? promote<T, TI>(in[c + (long long)r * S]) : zero_of<T>();
-        }
-#pragma unroll
-        for (int u = 0; u < 8; ++u) {
-            const int e = e0 + u * blockDim.x;
-            if (e < nel) sm[spad<T>(e)] = tmp[u];
-        }
-    }
-}
 
 // ---------------------------------------------------------------------------
 struct PassArgs {
