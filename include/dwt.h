@@ -20,6 +20,13 @@
  *  - Complex data (DWT_C64, DWT_C128) is interleaved (re, im).
  *  - Calls are asynchronous on "stream" (a cudaStream_t, NULL = legacy
  *    default stream) unless stated otherwise.  dwt_plan_create synchronises.
+ *  - CUDA graphs: dwt_forward, dwt_inverse, dwt_interpolate (FP32 algorithm)
+ *    and dwt_effdim only enqueue kernels on "stream"; once an ordinary call
+ *    of the same shape has grown the plan's workspace they neither allocate
+ *    nor synchronise, so such a call can be captured into a graph (stream
+ *    capture) and replayed, with the same results.  The tensor-core
+ *    algorithm, the spline calls, the host-buffer call and the serving engine
+ *    allocate or synchronise and are not for capture.
  *  - Status codes are returned, never thrown.  After a failed call the outputs
  *    are unspecified and the plan stays usable, except after DWT_ECUDA, which
  *    reports a sticky CUDA error.  dwt_last_error() gives a message for the

@@ -215,3 +215,42 @@ def test_interpolate_p_odd_unweighted(dwt, dev, orc, p, m, s):
     assert np.allclose(v[0], vt, rtol=1e-5, atol=1e-14 * vt[-1])
     assert np.allclose(v[1], vs, rtol=1e-5, atol=1e-14 * vt[-1])
     _check_dims(_np(dim)[0], dt, ds, vt, vs)
+
+
+@pytest.mark.parametrize("p,m,s,B", [(2, 18, 6, 3), (3, 9, 4, 2), (2, 12, 4, 2)])
+def test_cuda_graph_replay_matches_calls(dwt, dev, orc, p, m, s, B):
+    """dwt_interpolate and dwt_forward only enqueue work, so after one ordinary
+    call (which sizes the plan's workspace) they can be captured into a CUDA
+    graph; a replay gives the ordinary call's results bit for bit."""
+    N = p ** m
+    C = S.small_net(p, m, s, index=80 + m)
+    plan = dwt.dwt_plan_create(p, m, s, C)
+    Y = orc.net_points(p, m, C)
+    coefs = S.uniform(S.stream_seed(29, S.P_COEFFS, m), B * s).reshape(B, s)
+    fs = np.stack([orc.eval_product(p, m, Y, coefs[b]) for b in range(B)])
+    f = torch.tensor(fs.astype(np.float32), device=dev)
+    cl = N if p == 2 else 2 * N
+    c = torch.empty((B, cl), device=dev)
+    var = torch.empty((B, 2, s + 1), dtype=torch.float64, device=dev)
+    dim = torch.empty((B, 2), dtype=torch.int32, device=dev)
+    g_out = torch.empty((B, cl), device=dev)
+    out_t = dwt.DWT_F32 if p == 2 else dwt.DWT_C64
+
+    def calls(st):
+        dwt.dwt_interpolate(plan, f, c, None, B, N, dwt.DWT_F32, dwt.DWT_WEIGHT_INV_SQ_WAVENUMBER, var=var, dim=dim,
+                            stream=st)
+        dwt.dwt_forward(plan, f, g_out, B, N, N, dwt.DWT_F32, out_t, stream=st)
+
+    calls(torch.cuda.current_stream())
+    torch.cuda.synchronize()
+    ref = [t.clone() for t in (c, var, dim, g_out)]
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph):
+        calls(torch.cuda.current_stream())
+    for t in (c, var, g_out):
+        t.zero_()
+    dim.fill_(-1)
+    graph.replay()
+    torch.cuda.synchronize()
+    for got, want in zip((c, var, dim, g_out), ref):
+        assert torch.equal(got, want)
