@@ -356,7 +356,8 @@ def run_other_configs(dwt, dev, stream, timed, steps):
     p, m, s = w["p"], w["m"], w["s"]
     N = p ** m
     ld = (N + 3) // 4 * 4
-    plan = dwt.dwt_plan_create(p, m, s, w["C"], dwt.DWT_PLAN_TRANSFORM_ONLY)
+    # the pass split measured on this GPU (DWT_PLAN_TUNE); plan time is not timed
+    plan = dwt.dwt_plan_create(p, m, s, w["C"], dwt.DWT_PLAN_TRANSFORM_ONLY | dwt.DWT_PLAN_TUNE)
     x = torch.ones((1, ld), dtype=torch.float32, device=dev)
     y = torch.empty((1, ld), dtype=torch.complex64, device=dev)
     z = torch.empty_like(y)
@@ -383,6 +384,7 @@ def run_other_configs(dwt, dev, stream, timed, steps):
         r[k + "_points_per_s"] = N * 10 * reps / (ms / 1e3)
         ms, _ = timed(fn, steps)
         r[k + "_direct_calls_points_per_s"] = N * steps / (ms / 1e3)
+    r["passes"] = dwt.dwt_plan_passes(plan, 8)
     out["p3_m13_s8"] = r
     return out
 

@@ -61,6 +61,7 @@ typedef enum { DWT_WEIGHT_NONE = 0, DWT_WEIGHT_INV_SQ_WAVENUMBER = 1 } dwt_weigh
 /* plan flags */
 #define DWT_PLAN_TRANSFORM_ONLY 1u  /* build no K(C) tables: forward/inverse/points/k->H only */
 #define DWT_PLAN_KEEP_INDEX_MAP 2u  /* keep the coset tables needed by dwt_index_to_wavenumber */
+#define DWT_PLAN_TUNE 4u            /* time the candidate pass splits of the generic transform, keep the fastest */
 
 typedef struct dwt_plan_s *dwt_plan_t;
 
@@ -79,6 +80,14 @@ typedef struct dwt_plan_s *dwt_plan_t;
  * rows of C do not span F_p^m, DWT_EUNSUPPORTED (plan still created) when a
  * least nu reaches 255 or a weight denominator exceeds 64 bits.  On any other
  * failure *plan is NULL.  Synchronises "stream".
+ * DWT_PLAN_TUNE: the digits of the generic transform passes (used for p > 2,
+ * and for p = 2 outside 12 <= m <= 14, 16 <= m <= 24) may be grouped in any
+ * way (Sec. 2.2); with this flag the plan times the candidate groupings of the
+ * FP32 form (real in, complex out for p > 2) on a scratch function of N
+ * points and keeps the fastest, for N (4 + element size) <= 1 GiB.  Results
+ * are kept per process and per device, and appended to the file named by the
+ * environment variable DWT_TUNE_CACHE when it is set (one JSON object per
+ * line), from which later processes read them instead of measuring again.
  */
 int dwt_plan_create(int p, int m, int s, const uint8_t *C, unsigned flags, void *stream, dwt_plan_t *plan);
 
@@ -96,6 +105,12 @@ int dwt_plan_destroy_async(dwt_plan_t plan, void *stream);
  * DWT_ESPAN, DWT_EUNSUPPORTED, or -1 when built with TRANSFORM_ONLY). Any
  * output pointer may be NULL. */
 int dwt_plan_info(dwt_plan_t plan, int *p, int *m, int *s, long long *N, int *tables_status);
+
+/* The digit split of the generic passes for elements of elem_bytes (4: FP32
+ * or int32, 8: complex FP32 or FP64, 16: complex FP64): *q passes, digits[t]
+ * digits and wc[t] columns (consecutive low indices per row) in pass t, from
+ * the lowest digits up.  digits and wc: host int [32]. */
+int dwt_plan_passes(dwt_plan_t plan, int elem_bytes, int *q, int *digits, int *wc);
 
 /* Device pointers to the plan's tables: W[N] (float) and cls[N][2] (uint8, max
  * support then support size).  Owned by the plan; valid until destroy. */

@@ -36,6 +36,7 @@ DWT_WEIGHT_NONE, DWT_WEIGHT_INV_SQ_WAVENUMBER = 0, 1
 # plan flags
 DWT_PLAN_TRANSFORM_ONLY = 1
 DWT_PLAN_KEEP_INDEX_MAP = 2
+DWT_PLAN_TUNE = 4
 
 _lib = None
 
@@ -68,6 +69,7 @@ _SIGS = {
     "dwt_plan_destroy": (_I, [_VP]),
     "dwt_plan_destroy_async": (_I, [_VP, _VP]),
     "dwt_plan_info": (_I, [_VP, _VP, _VP, _VP, _VP, _VP]),
+    "dwt_plan_passes": (_I, [_VP, _I, _VP, _VP, _VP]),
     "dwt_plan_tables": (_I, [_VP, ctypes.POINTER(_VP), ctypes.POINTER(_VP)]),
     "dwt_points": (_I, [_VP, _VP, _LL, _VP]),
     "dwt_wavenumber_to_index": (_I, [_VP, _VP, _VP, _LL, _VP]),
@@ -206,6 +208,15 @@ def dwt_plan_info(plan):
     _check(lib().dwt_plan_info(plan.handle, ctypes.byref(p), ctypes.byref(m), ctypes.byref(s), ctypes.byref(N),
                                ctypes.byref(t)))
     return dict(p=p.value, m=m.value, s=s.value, N=N.value, tables_status=t.value)
+
+
+def dwt_plan_passes(plan, elem_bytes):
+    """The digit split of the generic passes for elements of elem_bytes: [(digits, columns), ...]."""
+    q = _I()
+    d = (_I * 32)()
+    w = (_I * 32)()
+    _check(lib().dwt_plan_passes(plan.handle, elem_bytes, ctypes.byref(q), d, w))
+    return [(d[t], w[t]) for t in range(q.value)]
 
 
 def dwt_plan_tables(plan):

@@ -5,10 +5,12 @@
 #include <stdio.h>
 #include <string.h>
 
+#include <algorithm>
 #include <atomic>
 #include <map>
 #include <mutex>
 #include <unordered_set>
+#include <vector>
 
 #include <cmath>
 
@@ -136,61 +138,114 @@ static int pass_wc(long long R, long long S, long long cap, int wc_max) {
     return wc;
 }
 
-// Fewest passes first.  Among the splits with that many passes, the one whose
-// narrowest high pass has the widest rows (wide rows keep the strided passes
-// coalesced), then the one with the longest contiguous low pass.  A high pass
-// then halves its rows (down to 64 bytes) while it has fewer than min_tiles
-// tiles per function.
-static void make_pass_plan(int p, int m, int elem, long long min_tiles, dwt::PassPlan& pp) {
-    const long long cap = (long long)(kTileBudget / (size_t)elem);
-    const int wc_min = std::max(1, 64 / elem);    // 64-byte rows at least in a high pass
-    const int wc_max = std::max(1, 256 / elem);   // 256-byte rows at most
-    int blo = 0;
-    while (dwt::ipow_ll(p, blo + 1) <= cap) ++blo;
-    int bhi = 0;
-    while (dwt::ipow_ll(p, bhi + 1) * wc_min <= cap) ++bhi;
-    int b[32];
-    pp.q = 0;
-    if (m <= blo) {
-        b[0] = m;
-        pp.q = 1;
-    } else {
-        const int nh = (m - blo + bhi - 1) / bhi;
-        int best_wc = -1;
-        for (int lo = blo; lo >= std::max(1, m - nh * bhi); --lo) {
-            const int rest = m - lo;
-            if (rest < nh) continue;
-            int bt[32], wc_lo = 1 << 30, d = lo;
-            bt[0] = lo;
-            for (int t = 0; t < nh; ++t) {
-                bt[t + 1] = rest / nh + (t < rest % nh ? 1 : 0);
-                const int wc = pass_wc(dwt::ipow_ll(p, bt[t + 1]), dwt::ipow_ll(p, d), cap, wc_max);
-                wc_lo = std::min(wc_lo, wc);
-                d += bt[t + 1];
-            }
-            if (wc_lo > best_wc) {
-                best_wc = wc_lo;
-                for (int t = 0; t <= nh; ++t) b[t] = bt[t];
-                pp.q = nh + 1;
-            }
-        }
-    }
+struct PassLimits {
+    long long cap;   // elements per tile
+    int wc_min, wc_max, blo, bhi;
+};
+static PassLimits pass_limits(int p, int elem) {
+    PassLimits L;
+    L.cap = (long long)(kTileBudget / (size_t)elem);
+    L.wc_min = std::max(1, 64 / elem);    // 64-byte rows at least in a high pass
+    L.wc_max = std::max(1, 256 / elem);   // 256-byte rows at most
+    L.blo = 0;
+    while (dwt::ipow_ll(p, L.blo + 1) <= L.cap) ++L.blo;
+    L.bhi = 0;
+    while (dwt::ipow_ll(p, L.bhi + 1) * L.wc_min <= L.cap) ++L.bhi;
+    return L;
+}
+
+// Geometry of the passes of a digit split b[0..q): pass 0 the low b[0] digits,
+// then the others upward.  Each high pass takes the widest rows its tile
+// allows, divided by wc_div, and halves them further (down to 64 bytes) while
+// it has fewer than min_tiles tiles per function.
+void pass_geometry(int p, int m, int elem, const int* b, int q, long long min_tiles, int wc_div, PassPlan& pp) {
+    const PassLimits L = pass_limits(p, elem);
     const long long N = dwt::ipow_ll(p, m);
+    pp.q = q;
     int d = 0;
-    for (int t = 0; t < pp.q; ++t) {
+    for (int t = 0; t < q; ++t) {
         PassGeom& g = pp.g[t];
         g.d0 = d;
         g.b = b[t];
         d += b[t];
         g.S = dwt::ipow_ll(p, g.d0);
         g.R = (int)dwt::ipow_ll(p, g.b);
-        g.Wc = g.d0 > 0 ? pass_wc(g.R, g.S, cap, wc_max) : 1;
-        while (g.Wc > wc_min && ((g.S + g.Wc - 1) / g.Wc) * (N / (g.S * g.R)) < min_tiles) g.Wc /= 2;
+        g.Wc = g.d0 > 0 ? pass_wc(g.R, g.S, L.cap, L.wc_max) : 1;
+        for (int k = 1; k < wc_div && g.Wc > L.wc_min; k *= 2) g.Wc /= 2;
+        while (g.Wc > L.wc_min && ((g.S + g.Wc - 1) / g.Wc) * (N / (g.S * g.R)) < min_tiles) g.Wc /= 2;
         g.wlog = 0;
         while ((1 << g.wlog) < g.Wc) ++g.wlog;
         g.nlo = (g.S + g.Wc - 1) / g.Wc;
         g.ntile = g.nlo * (N / (g.S * g.R));
     }
+}
+
+// Candidate digit splits within the tile budget: with the fewest passes, every
+// low-pass length that leaves the rest to the high passes (shared evenly), and
+// one more pass shared evenly.  The heuristic's split is among them.
+void pass_splits(int p, int m, int elem, std::vector<std::vector<int>>& out) {
+    const PassLimits L = pass_limits(p, elem);
+    out.clear();
+    if (m <= L.blo) {
+        out.push_back({m});
+        if (m >= 2) {
+            const int lo = (m + 1) / 2;
+            if (m - lo <= L.bhi) out.push_back({lo, m - lo});
+        }
+        return;
+    }
+    const int nh = (m - L.blo + L.bhi - 1) / L.bhi;
+    for (int lo = L.blo; lo >= std::max(1, m - nh * L.bhi); --lo) {
+        const int rest = m - lo;
+        if (rest < nh) continue;
+        std::vector<int> bt{lo};
+        for (int t = 0; t < nh; ++t) bt.push_back(rest / nh + (t < rest % nh ? 1 : 0));
+        out.push_back(bt);
+    }
+    // one more pass, all passes as even as the limits allow
+    const int q = nh + 2;
+    std::vector<int> bt(q);
+    for (int t = 0; t < q; ++t) bt[t] = m / q + (t < m % q ? 1 : 0);
+    std::sort(bt.begin(), bt.end(), [](int a, int c) { return a > c; });   // the longest first (the low pass)
+    bool ok = bt[0] <= L.blo;
+    for (int t = 1; t < q; ++t) ok = ok && bt[t] <= L.bhi && bt[t] >= 1;
+    if (ok) out.push_back(bt);
+}
+
+// Fewest passes first.  Among the splits with that many passes, the one whose
+// narrowest high pass has the widest rows (wide rows keep the strided passes
+// coalesced), then the one with the longest contiguous low pass.  A high pass
+// then halves its rows (down to 64 bytes) while it has fewer than min_tiles
+// tiles per function.
+static void make_pass_plan(int p, int m, int elem, long long min_tiles, dwt::PassPlan& pp) {
+    const PassLimits L = pass_limits(p, elem);
+    int b[32];
+    int q = 0;
+    if (m <= L.blo) {
+        b[0] = m;
+        q = 1;
+    } else {
+        const int nh = (m - L.blo + L.bhi - 1) / L.bhi;
+        int best_wc = -1;
+        for (int lo = L.blo; lo >= std::max(1, m - nh * L.bhi); --lo) {
+            const int rest = m - lo;
+            if (rest < nh) continue;
+            int bt[32], wc_lo = 1 << 30, d = lo;
+            bt[0] = lo;
+            for (int t = 0; t < nh; ++t) {
+                bt[t + 1] = rest / nh + (t < rest % nh ? 1 : 0);
+                const int wc = pass_wc(dwt::ipow_ll(p, bt[t + 1]), dwt::ipow_ll(p, d), L.cap, L.wc_max);
+                wc_lo = std::min(wc_lo, wc);
+                d += bt[t + 1];
+            }
+            if (wc_lo > best_wc) {
+                best_wc = wc_lo;
+                for (int t = 0; t <= nh; ++t) b[t] = bt[t];
+                q = nh + 1;
+            }
+        }
+    }
+    pass_geometry(p, m, elem, b, q, min_tiles, 1, pp);
 }
 
 const PassPlan& pass_plan(dwt_plan_s* P, int elem_bytes) {
@@ -275,7 +330,7 @@ int dwt_plan_create(int p, int m, int s, const uint8_t* C, unsigned flags, void*
         set_error("p^m = %d^%d exceeds 2^31", p, m);
         return DWT_EINVAL;
     }
-    if (flags & ~(DWT_PLAN_TRANSFORM_ONLY | DWT_PLAN_KEEP_INDEX_MAP)) {
+    if (flags & ~(DWT_PLAN_TRANSFORM_ONLY | DWT_PLAN_KEEP_INDEX_MAP | DWT_PLAN_TUNE)) {
         set_error("unknown plan flags 0x%x", flags);
         return DWT_EINVAL;
     }
@@ -303,6 +358,7 @@ int dwt_plan_create(int p, int m, int s, const uint8_t* C, unsigned flags, void*
         make_pass_plan(p, m, 4, 2ll * sms, P->passes[0]);
         make_pass_plan(p, m, 8, 2ll * sms, P->passes[1]);
         make_pass_plan(p, m, 16, 2ll * sms, P->passes[2]);
+        P->min_tiles = 2ll * sms;
     }
     // row coset labels and column point contributions
     std::vector<uint32_t> R((size_t)s * m), col((size_t)s * m);
@@ -335,6 +391,10 @@ int dwt_plan_create(int p, int m, int s, const uint8_t* C, unsigned flags, void*
         set_error("plan upload failed: %s", cudaGetErrorString(cudaGetLastError()));
         return fail(DWT_ECUDA);
     }
+    if (flags & DWT_PLAN_TUNE) {
+        const int trc = tune_passes(P, P->min_tiles, st);
+        if (trc) return fail(trc);
+    }
     if (!(flags & DWT_PLAN_TRANSFORM_ONLY)) {
         rc = build_coset_tables(P, st);
         if (rc == DWT_ESPAN || rc == DWT_EUNSUPPORTED) {
@@ -354,6 +414,20 @@ int dwt_plan_create(int p, int m, int s, const uint8_t* C, unsigned flags, void*
     }
     *out = P;
     return rc;
+}
+
+int dwt_plan_passes(dwt_plan_t P, int elem_bytes, int* q, int* digits, int* wc) {
+    if (!P || !q || !digits || !wc || (elem_bytes != 4 && elem_bytes != 8 && elem_bytes != 16)) {
+        set_error("dwt_plan_passes: bad arguments");
+        return DWT_EINVAL;
+    }
+    const PassPlan& pp = pass_plan(P, elem_bytes);
+    *q = pp.q;
+    for (int t = 0; t < pp.q; ++t) {
+        digits[t] = pp.g[t].b;
+        wc[t] = pp.g[t].Wc;
+    }
+    return DWT_OK;
 }
 
 int dwt_plan_destroy(dwt_plan_t P) {

@@ -88,6 +88,7 @@ struct dwt_plan_s {
     size_t ws_bytes = 0;
     // pass decompositions by element size (4, 8, 16 bytes)
     dwt::PassPlan passes[3];
+    long long min_tiles = 1;        // tiles per function the high passes aim for (two per SM)
     // device slots, streams and events of dwt_interpolate_host (first use)
     dwt::HostStage* host = nullptr;
     // kernel spline tables (dwt_spline_prepare): W_K [N], then R~_d - [H=0] and E~_j, [2s][N], FP64
@@ -104,6 +105,10 @@ int ensure_workspace(dwt_plan_s* P, size_t bytes, cudaStream_t st);
 int dmalloc(void** p, size_t bytes, cudaStream_t st);
 void dfree(void* p, cudaStream_t st);
 const PassPlan& pass_plan(dwt_plan_s* P, int elem_bytes);
+void pass_geometry(int p, int m, int elem, const int* b, int q, long long min_tiles, int wc_div, PassPlan& pp);
+void pass_splits(int p, int m, int elem, std::vector<std::vector<int>>& out);
+int tune_passes(dwt_plan_s* P, long long min_tiles, cudaStream_t st);
+bool p2_fast_ok(int m);
 
 // kernels' host entry points (implemented in the .cu files)
 int run_transform(dwt_plan_s* P, const void* in, void* out, int batch, long long ld_in, long long ld_out,

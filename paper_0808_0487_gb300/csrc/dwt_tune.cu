@@ -1,0 +1,236 @@
+// dwt_tune.cu -- measured choice of the digit split of the generic passes.
+//
+// Any grouping of the m digits into passes computes the same transform
+// (Sec. 2.2: the digit sums commute); what differs is the time.  With
+// DWT_PLAN_TUNE the plan times every candidate split of the FP32 form (real to
+// complex for p > 2), each with the heuristic row width and with half of it,
+// on a scratch function of the plan's size, and keeps the fastest.  Results
+// are cached per process and, when the environment variable DWT_TUNE_CACHE
+// names a file, in that file (one JSON object per line: device, p, m, element
+// size, digits and row widths of the passes), so a shape is measured once per
+// device.
+#include <stdio.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <map>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "dwt_internal.cuh"
+
+namespace dwt {
+
+namespace {
+
+struct TunedSplit {
+    std::vector<int> b, wc;
+};
+
+std::mutex g_mu;
+std::map<std::string, TunedSplit> g_cache;
+bool g_file_read = false;
+
+std::string cache_key(const std::string& dev, int p, int m, int elem) {
+    char buf[64];
+    snprintf(buf, sizeof buf, "|%d|%d|%d", p, m, elem);
+    return dev + buf;
+}
+
+// integers of the JSON array that follows "name": [ in line
+bool json_ints(const char* line, const char* name, std::vector<int>& out) {
+    const char* k = strstr(line, name);
+    if (!k) return false;
+    const char* a = strchr(k, '[');
+    const char* z = a ? strchr(a, ']') : nullptr;
+    if (!a || !z) return false;
+    out.clear();
+    for (const char* c = a + 1; c < z;) {
+        char* e = nullptr;
+        const long v = strtol(c, &e, 10);
+        if (e == c) {
+            ++c;
+            continue;
+        }
+        out.push_back((int)v);
+        c = e;
+    }
+    return true;
+}
+
+bool json_int(const char* line, const char* name, int* v) {
+    const char* k = strstr(line, name);
+    if (!k) return false;
+    k = strchr(k, ':');
+    if (!k) return false;
+    *v = (int)strtol(k + 1, nullptr, 10);
+    return true;
+}
+
+void read_cache_file() {
+    const char* path = getenv("DWT_TUNE_CACHE");
+    if (!path || !*path) return;
+    FILE* fh = fopen(path, "r");
+    if (!fh) return;
+    char line[1024];
+    while (fgets(line, sizeof line, fh)) {
+        const char* d = strstr(line, "\"device\": \"");
+        if (!d) continue;
+        d += strlen("\"device\": \"");
+        const char* de = strchr(d, '"');
+        if (!de) continue;
+        int p = 0, m = 0, elem = 0;
+        TunedSplit ts;
+        if (!json_int(line, "\"p\"", &p) || !json_int(line, "\"m\"", &m) || !json_int(line, "\"elem\"", &elem) ||
+            !json_ints(line, "\"digits\"", ts.b) || !json_ints(line, "\"wc\"", ts.wc) || ts.b.size() != ts.wc.size())
+            continue;
+        g_cache[cache_key(std::string(d, de), p, m, elem)] = ts;
+    }
+    fclose(fh);
+}
+
+void append_cache_file(const std::string& dev, int p, int m, int elem, const TunedSplit& ts) {
+    const char* path = getenv("DWT_TUNE_CACHE");
+    if (!path || !*path) return;
+    FILE* fh = fopen(path, "a");
+    if (!fh) return;
+    fprintf(fh, "{\"device\": \"%s\", \"p\": %d, \"m\": %d, \"elem\": %d, \"digits\": [", dev.c_str(), p, m, elem);
+    for (size_t i = 0; i < ts.b.size(); ++i) fprintf(fh, "%s%d", i ? ", " : "", ts.b[i]);
+    fprintf(fh, "], \"wc\": [");
+    for (size_t i = 0; i < ts.wc.size(); ++i) fprintf(fh, "%s%d", i ? ", " : "", ts.wc[i]);
+    fprintf(fh, "]}\n");
+    fclose(fh);
+}
+
+// a plan from a cached split: the digits, and row widths as measured
+bool apply_split(int p, int m, int elem, const TunedSplit& ts, PassPlan& pp) {
+    int sum = 0;
+    for (int v : ts.b) sum += v;
+    if (sum != m || ts.b.empty() || ts.b.size() > 32) return false;
+    pass_geometry(p, m, elem, ts.b.data(), (int)ts.b.size(), 0, 1, pp);
+    const long long N = ipow_ll(p, m);
+    for (int t = 0; t < pp.q; ++t) {
+        PassGeom& g = pp.g[t];
+        const int wc = ts.wc[t];
+        if (wc < 1 || (wc & (wc - 1)) || (long long)g.R * wc * elem > 64 * 1024 || (t == 0 && wc != 1)) return false;
+        g.Wc = wc;
+        g.wlog = 0;
+        while ((1 << g.wlog) < g.Wc) ++g.wlog;
+        g.nlo = (g.S + g.Wc - 1) / g.Wc;
+        g.ntile = g.nlo * (N / (g.S * g.R));
+    }
+    return true;
+}
+
+}  // namespace
+
+int tune_passes(dwt_plan_s* P, long long min_tiles, cudaStream_t st) {
+    const int p = P->p, m = P->m;
+    const long long N = P->N;
+    // the FP32 form that runs on the generic passes: real -> complex for p > 2,
+    // FP32 for p = 2 outside the register-tile range
+    if (p == 2 && p2_fast_ok(m)) return DWT_OK;
+    const int elem = p == 2 ? 4 : 8;
+    const int idx = p == 2 ? 0 : 1;
+    const size_t scratch = (size_t)N * (4 + (size_t)elem);
+    if (scratch > ((size_t)1 << 30)) return DWT_OK;   // above 1 GiB of scratch the heuristic split stays
+    int dev = 0;
+    cudaDeviceProp prop;
+    DWT_CK(cudaGetDevice(&dev));
+    DWT_CK(cudaGetDeviceProperties(&prop, dev));
+    char devbuf[300];
+    snprintf(devbuf, sizeof devbuf, "%s/%d", prop.name, prop.multiProcessorCount);
+    const std::string devname(devbuf);
+    const std::string key = cache_key(devname, p, m, elem);
+    {
+        std::lock_guard<std::mutex> lk(g_mu);
+        if (!g_file_read) {
+            read_cache_file();
+            g_file_read = true;
+        }
+        auto it = g_cache.find(key);
+        if (it != g_cache.end()) {
+            PassPlan pp;
+            if (apply_split(p, m, elem, it->second, pp)) {
+                P->passes[idx] = pp;
+                return DWT_OK;
+            }
+        }
+    }
+    // candidates: every split, with the heuristic row widths and with half
+    std::vector<std::vector<int>> splits;
+    pass_splits(p, m, elem, splits);
+    std::vector<PassPlan> cands;
+    cands.push_back(P->passes[idx]);   // the heuristic plan first
+    for (const auto& b : splits)
+        for (int div : {1, 2}) {
+            PassPlan pp;
+            pass_geometry(p, m, elem, b.data(), (int)b.size(), min_tiles, div, pp);
+            bool dup = false;
+            for (const PassPlan& c : cands) {
+                bool same = c.q == pp.q;
+                for (int t = 0; same && t < pp.q; ++t) same = c.g[t].b == pp.g[t].b && c.g[t].Wc == pp.g[t].Wc;
+                dup = dup || same;
+            }
+            if (!dup) cands.push_back(pp);
+        }
+    void* in = nullptr;
+    void* out = nullptr;
+    int rc = dmalloc(&in, (size_t)N * 4, st);
+    if (!rc) rc = dmalloc(&out, (size_t)N * elem, st);
+    if (rc) {
+        dfree(in, st);
+        return rc;
+    }
+    DWT_CK(cudaMemsetAsync(in, 0, (size_t)N * 4, st));
+    cudaEvent_t e0, e1;
+    DWT_CK(cudaEventCreate(&e0));
+    DWT_CK(cudaEventCreate(&e1));
+    const PassPlan keep = P->passes[idx];
+    int best = 0;
+    float best_ms = 1e30f;
+    for (size_t c = 0; c < cands.size() && !rc; ++c) {
+        P->passes[idx] = cands[c];
+        float t_min = 1e30f;
+        for (int rep = 0; rep < 4 && !rc; ++rep) {   // the first run warms up
+            cudaEventRecord(e0, st);
+            rc = run_transform(P, in, out, 1, N, N, DWT_F32, p == 2 ? DWT_F32 : DWT_C64, -1, st);
+            cudaEventRecord(e1, st);
+            if (rc) break;
+            if (cudaEventSynchronize(e1) != cudaSuccess) {
+                rc = cuda_fail(cudaGetLastError(), "tuning run", __FILE__, __LINE__);
+                break;
+            }
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            if (rep > 0) t_min = std::min(t_min, ms);
+        }
+        if (!rc && t_min < best_ms) {
+            best_ms = t_min;
+            best = (int)c;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    dfree(in, st);
+    dfree(out, st);
+    if (rc) {
+        P->passes[idx] = keep;
+        return rc;
+    }
+    P->passes[idx] = cands[best];
+    TunedSplit ts;
+    for (int t = 0; t < cands[best].q; ++t) {
+        ts.b.push_back(cands[best].g[t].b);
+        ts.wc.push_back(cands[best].g[t].Wc);
+    }
+    std::lock_guard<std::mutex> lk(g_mu);
+    if (!g_cache.count(key)) {
+        g_cache[key] = ts;
+        append_cache_file(devname, p, m, elem, ts);
+    }
+    return DWT_OK;
+}
+
+}  // namespace dwt
