@@ -112,6 +112,13 @@ int dwt_plan_info(dwt_plan_t plan, int *p, int *m, int *s, long long *N, int *ta
  * the lowest digits up.  digits and wc: host int [32]. */
 int dwt_plan_passes(dwt_plan_t plan, int elem_bytes, int *q, int *digits, int *wc);
 
+/* The heuristic split that dwt_plan_create gives a plan (before any tuning),
+ * computed on the host without a device: fewest passes within the 64 KB tile
+ * budget, then the widest rows of the narrowest high pass, then the longest
+ * low pass; high-pass rows halve (down to 64 bytes) while a function has
+ * fewer than min_tiles tiles (a plan uses two per SM).  Outputs as above. */
+int dwt_pass_plan_for(int p, int m, int elem_bytes, long long min_tiles, int *q, int *digits, int *wc);
+
 /* Device pointers to the plan's tables: W[N] (float) and cls[N][2] (uint8, max
  * support then support size).  Owned by the plan; valid until destroy. */
 int dwt_plan_tables(dwt_plan_t plan, const float **W, const uint8_t **cls);

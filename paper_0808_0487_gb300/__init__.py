@@ -70,6 +70,7 @@ _SIGS = {
     "dwt_plan_destroy_async": (_I, [_VP, _VP]),
     "dwt_plan_info": (_I, [_VP, _VP, _VP, _VP, _VP, _VP]),
     "dwt_plan_passes": (_I, [_VP, _I, _VP, _VP, _VP]),
+    "dwt_pass_plan_for": (_I, [_I, _I, _I, _LL, _VP, _VP, _VP]),
     "dwt_plan_tables": (_I, [_VP, ctypes.POINTER(_VP), ctypes.POINTER(_VP)]),
     "dwt_points": (_I, [_VP, _VP, _LL, _VP]),
     "dwt_wavenumber_to_index": (_I, [_VP, _VP, _VP, _LL, _VP]),
@@ -216,6 +217,15 @@ def dwt_plan_passes(plan, elem_bytes):
     d = (_I * 32)()
     w = (_I * 32)()
     _check(lib().dwt_plan_passes(plan.handle, elem_bytes, ctypes.byref(q), d, w))
+    return [(d[t], w[t]) for t in range(q.value)]
+
+
+def dwt_pass_plan_for(p, m, elem_bytes, min_tiles=304):
+    """The heuristic pass split for (p, m, element size), host only: [(digits, columns), ...]."""
+    q = _I()
+    d = (_I * 32)()
+    w = (_I * 32)()
+    _check(lib().dwt_pass_plan_for(p, m, elem_bytes, min_tiles, ctypes.byref(q), d, w))
     return [(d[t], w[t]) for t in range(q.value)]
 
 

@@ -416,6 +416,22 @@ int dwt_plan_create(int p, int m, int s, const uint8_t* C, unsigned flags, void*
     return rc;
 }
 
+int dwt_pass_plan_for(int p, int m, int elem_bytes, long long min_tiles, int* q, int* digits, int* wc) {
+    if (!is_prime_small(p) || m < 1 || ipow_ll(p, m) > (1ll << 31) || !q || !digits || !wc ||
+        (elem_bytes != 4 && elem_bytes != 8 && elem_bytes != 16) || min_tiles < 0) {
+        set_error("dwt_pass_plan_for: bad arguments");
+        return DWT_EINVAL;
+    }
+    PassPlan pp;
+    make_pass_plan(p, m, elem_bytes, min_tiles, pp);
+    *q = pp.q;
+    for (int t = 0; t < pp.q; ++t) {
+        digits[t] = pp.g[t].b;
+        wc[t] = pp.g[t].Wc;
+    }
+    return DWT_OK;
+}
+
 int dwt_plan_passes(dwt_plan_t P, int elem_bytes, int* q, int* digits, int* wc) {
     if (!P || !q || !digits || !wc || (elem_bytes != 4 && elem_bytes != 8 && elem_bytes != 16)) {
         set_error("dwt_plan_passes: bad arguments");
