@@ -179,9 +179,9 @@ int tune_passes(dwt_plan_s* P, long long min_tiles, cudaStream_t st) {
     void* out = nullptr;
     int rc = dmalloc(&in, (size_t)N * 4, st);
     if (!rc) rc = dmalloc(&out, (size_t)N * elem, st);
-    if (rc) {
+    if (rc) {   // no room for the scratch: the heuristic split stays
         dfree(in, st);
-        return rc;
+        return DWT_OK;
     }
     DWT_CK(cudaMemsetAsync(in, 0, (size_t)N * 4, st));
     cudaEvent_t e0, e1;
