@@ -106,7 +106,10 @@ void append_cache_file(const std::string& dev, int p, int m, int elem, const Tun
 // a plan from a cached split: the digits, and row widths as measured
 bool apply_split(int p, int m, int elem, const TunedSplit& ts, PassPlan& pp) {
     int sum = 0;
-    for (int v : ts.b) sum += v;
+    for (int v : ts.b) {
+        if (v < 1) return false;
+        sum += v;
+    }
     if (sum != m || ts.b.empty() || ts.b.size() > 32) return false;
     pass_geometry(p, m, elem, ts.b.data(), (int)ts.b.size(), 0, 1, pp);
     const long long N = ipow_ll(p, m);
