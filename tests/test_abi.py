@@ -58,3 +58,13 @@ def test_no_cpu_fallback_in_package():
             if f.endswith((".py", ".cu", ".cuh", ".h")):
                 txt = open(os.path.join(dirpath, f)).read()
                 assert "import oracle" not in txt and "from oracle" not in txt and "oracle.c" not in txt, f
+
+
+def test_missing_library_fails_loudly(dwtlib, monkeypatch, tmp_path):
+    """Without the built library every call raises: there is no other path."""
+    monkeypatch.setattr(dwtlib, "_lib", None)
+    monkeypatch.setattr(dwtlib, "LIB_PATH", str(tmp_path / "libdwt.so"))
+    with pytest.raises(dwtlib.DwtError):
+        dwtlib.dwt_strerror(0)
+    with pytest.raises(dwtlib.DwtError):
+        dwtlib.dwt_plan_create(2, 4, 1, np.zeros((1, 4, 4), dtype=np.uint8))
