@@ -404,6 +404,7 @@ int dwt_plan_create(int p, int m, int s, const uint8_t* C, unsigned flags, void*
         } else {
             P->tables_status = DWT_OK;
             rc = p2_build_tiled_tables(P, st);
+            if (!rc) rc = p2i_build_tables(P, st);
             if (rc) return fail(rc);
         }
     }
@@ -458,6 +459,10 @@ int dwt_plan_destroy(dwt_plan_t P) {
     cudaFree(P->d_cls);
     cudaFree(P->d_Wt);
     cudaFree(P->d_clst);
+    cudaFree(P->d_tq);
+    cudaFree(P->d_tw);
+    cudaFree(P->d_tkt);
+    cudaFree(P->d_tks);
     cudaFree(P->d_T);
     cudaFree(P->d_D);
     cudaFree(P->d_ws);
@@ -477,6 +482,10 @@ int dwt_plan_destroy_async(dwt_plan_t P, void* stream) {
     dfree(P->d_cls, st);
     dfree(P->d_Wt, st);
     dfree(P->d_clst, st);
+    dfree(P->d_tq, st);
+    dfree(P->d_tw, st);
+    dfree(P->d_tkt, st);
+    dfree(P->d_tks, st);
     dfree(P->d_T, st);
     dfree(P->d_D, st);
     dfree(P->d_ws, st);

@@ -79,8 +79,16 @@ struct dwt_plan_s {
     // coset tables
     float* d_W = nullptr;         // [N]
     uint8_t* d_cls = nullptr;     // [N][2]
-    float* d_Wt = nullptr;        // W in the tile-major order of the fused p = 2 pass
+    float* d_Wt = nullptr;        // W in the tile-major order of the fused p = 2 pass (16 <= m <= 19)
     uint8_t* d_clst = nullptr;    // cls in the same order
+    // tables of the p = 2 top pass for 20 <= m <= 24, in its read order:
+    // compact ((Q - 1) | (|supp| << 11) and max supp) or full (W 2^-m, both classes)
+    uint16_t* d_tq = nullptr;
+    float* d_tw = nullptr;
+    uint8_t* d_tkt = nullptr;
+    uint8_t* d_tks = nullptr;
+    int* h_err = nullptr;         // process-wide host-mapped status word of the top pass (bounded waits)
+    int* d_err = nullptr;         // its device address on the plan's device
     uint8_t* d_T = nullptr;       // [(s+1)][N] least-nu tables (kept only with KEEP_INDEX_MAP)
     uint8_t* d_D = nullptr;       // [s][N] smallest optimal nu(k_j) per coordinate (ditto)
     // per-call workspace (grown on demand, owned by the plan)
@@ -109,6 +117,11 @@ void pass_geometry(int p, int m, int elem, const int* b, int q, long long min_ti
 void pass_splits(int p, int m, int elem, std::vector<std::vector<int>>& out);
 int tune_passes(dwt_plan_s* P, long long min_tiles, cudaStream_t st);
 bool p2_fast_ok(int m);
+bool p2i_ok(int m, int s);
+int p2i_build_tables(dwt_plan_s* P, cudaStream_t st);
+int p2i_table_bytes_per_point(dwt_plan_s* P);
+int p2i_interpolate(dwt_plan_s* Pl, const float* f, float* c, float* coef, int batch, long long ld, bool weighted,
+                    bool tc, double** part_out, long long* ntile_out, cudaStream_t st);
 
 // kernels' host entry points (implemented in the .cu files)
 int run_transform(dwt_plan_s* P, const void* in, void* out, int batch, long long ld_in, long long ld_out,

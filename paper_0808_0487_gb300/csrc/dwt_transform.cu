@@ -813,6 +813,15 @@ int run_interpolate(dwt_plan_s* Pl, const void* f, void* c, void* coef, int batc
         set_error("the tensor-core interpolation needs p = 2, 18 <= m <= 24 and 16-byte aligned rows");
         return DWT_EUNSUPPORTED;
     }
+    if (fast && Pl->d_tkt) {
+        double* part = nullptr;
+        long long ntile = 0;
+        int rc = p2i_interpolate(Pl, (const float*)f, (float*)c, (float*)coef, batch, ld,
+                                 weight == DWT_WEIGHT_INV_SQ_WAVENUMBER, algo == DWT_ALGO_TC_SPLIT_BF16, &part, &ntile,
+                                 st);
+        if (rc) return rc;
+        return finalize(Pl, part, ntile, batch, thr, var, dim, st);
+    }
     if (fast) {
         double* part = nullptr;
         long long ntile = 0;
