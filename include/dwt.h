@@ -19,7 +19,7 @@
  *    function start gives the fastest path, any ld works).
  *  - Complex data (DWT_C64, DWT_C128) is interleaved (re, im).
  *  - Calls are asynchronous on "stream" (a cudaStream_t, NULL = legacy
- *    default stream) unless stated otherwise.  dwt_plan_create synchronises.
+ *    default stream) unless stated otherwise.  dwt_plan (dwt_plan_create) synchronises.
  *  - CUDA graphs: dwt_forward, dwt_inverse, dwt_interpolate (FP32 algorithm)
  *    and dwt_effdim only enqueue kernels on "stream"; once an ordinary call
  *    of the same shape has grown the plan's workspace they neither allocate
@@ -66,7 +66,7 @@ typedef enum { DWT_WEIGHT_NONE = 0, DWT_WEIGHT_INV_SQ_WAVENUMBER = 1 } dwt_weigh
 typedef struct dwt_plan_s *dwt_plan_t;
 
 /*
- * Build a plan for the digital net P(C) of Def. 1.1 (eq. defy).
+ * dwt_plan: build a plan for the digital net P(C) of Def. 1.1 (eq. defy).
  *   p: prime, 2 <= p <= 13;  m >= 1 with p^m <= 2^31;  1 <= s <= 255.
  *   C: HOST array uint8 [s][m][m], C[j][i][c] in 0..p-1.  Row i of C_j gives
  *      the point digit y_{j,n,i+1}; column c multiplies the index digit n_c.
@@ -89,6 +89,8 @@ typedef struct dwt_plan_s *dwt_plan_t;
  * environment variable DWT_TUNE_CACHE when it is set (one JSON object per
  * line), from which later processes read them instead of measuring again.
  */
+int dwt_plan(int p, int m, int s, const uint8_t *C, unsigned flags, void *stream, dwt_plan_t *plan);
+/* The same call under its earlier name (identical arguments and behaviour). */
 int dwt_plan_create(int p, int m, int s, const uint8_t *C, unsigned flags, void *stream, dwt_plan_t *plan);
 
 /* Free a plan and its device tables (synchronises the device). NULL is ignored. */
@@ -302,11 +304,28 @@ int dwt_spline_eval(dwt_plan_t plan, const void *c, int batch, long long ld, con
 
 /*
  * Effective dimension of given coefficients g (Sec. 4), the variance and
- * threshold part of dwt_interpolate alone.  coef: device, type DWT_F32
- * (p = 2) or DWT_C64, ld elements per function.  var/dim as above (device).
+ * threshold part of dwt_interpolate alone.  g defines the finite Walsh series
+ * sum_H g(H) wal_{k(H)}; its ANOVA effect u collects the H with supp k(H) = u
+ * and has variance sum |g(H)|^2 over them (H != 0).
+ *   coef: device, DWT_F32 (p = 2) or DWT_C64 (p > 2), ld elements per function.
+ *   var_trc, var_sup: device double [batch][s+1] or NULL:
+ *     var_trc[b][d] = sum over H != 0 with max{j : k_j != 0} <= d of |g|^2
+ *     (the truncation variance), var_sup[b][d] the same over |supp k| <= d
+ *     (the superposition variance).
+ *   d_trc, d_sup: device int [batch] or NULL: the least d with
+ *     var(d) >= threshold * var(s) (threshold in (0, 1], the paper uses 0.99),
+ *     0 when the total variance is 0.
  */
-int dwt_effdim(dwt_plan_t plan, const void *coef, int batch, long long ld, dwt_dtype t, double *var,
-               int *dim, double threshold, void *stream);
+int dwt_effdim(dwt_plan_t plan, const void *coef, int batch, long long ld, dwt_dtype t, double *var_trc,
+               double *var_sup, int *d_trc, int *d_sup, double threshold, void *stream);
+
+/*
+ * dwt_effdim with the packed outputs of dwt_interpolate: var device double
+ * [batch][2][s+1] (truncation, then superposition), dim device int [batch][2]
+ * (d_trc, d_sup); either may be NULL.
+ */
+int dwt_effdim_packed(dwt_plan_t plan, const void *coef, int batch, long long ld, dwt_dtype t, double *var,
+                      int *dim, double threshold, void *stream);
 
 /*
  * dwt_effdim_static: dwt_effdim that allocates nothing.  (The paper has no
@@ -319,7 +338,7 @@ int dwt_effdim(dwt_plan_t plan, const void *coef, int batch, long long ld, dwt_d
  * grows with cudaMalloc; this call keeps them in one fixed 8 MiB array
  * compiled into the library (every GPU that loads the library holds it until
  * the process exits), and calls no allocating routine.
- * Arguments, results and tolerance are those of dwt_effdim.
+ * Arguments, results and tolerance are those of dwt_effdim_packed.
  * Limit: one function may need at most 2^20 partials, i.e.
  * 2 (s+1) (ceil(N / 8192) + 1) <= 1048576 (for s = 32, N <= 2^27); larger
  * requests return DWT_EINVAL with a message.  Batches go through the array in
@@ -410,6 +429,11 @@ int dwt_selftest_bounded_wait(void *stream);
 
 /* Number of kernels this library has launched in this process. */
 long long dwt_launch_count(void);
+
+/* Number of device (and page-locked host) allocations the library has made in
+ * this process, over all threads: plans, workspaces, scratch, serving slots.
+ * A diagnostic, like dwt_launch_count (no counterpart in the paper). */
+long long dwt_alloc_count(void);
 
 /*
  * Optional per-kernel timing with CUDA events recorded on the launching stream

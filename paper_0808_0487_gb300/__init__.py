@@ -84,7 +84,9 @@ _SIGS = {
     "dwt_spline": (_I, [_VP, _VP, _VP, _I, _LL, _VP, _VP, _VP, ctypes.c_double, _VP]),
     "dwt_spline_values_shifted": (_I, [_VP, _VP, _VP, _I, _VP, _I, _LL, _VP, _VP, _VP]),
     "dwt_spline_eval": (_I, [_VP, _VP, _I, _LL, _VP, _I, _I, _VP, _LL, _VP]),
-    "dwt_effdim": (_I, [_VP, _VP, _I, _LL, _I, _VP, _VP, ctypes.c_double, _VP]),
+    "dwt_plan": (_I, [_I, _I, _I, _VP, ctypes.c_uint, _VP, ctypes.POINTER(_VP)]),
+    "dwt_effdim": (_I, [_VP, _VP, _I, _LL, _I, _VP, _VP, _VP, _VP, ctypes.c_double, _VP]),
+    "dwt_effdim_packed": (_I, [_VP, _VP, _I, _LL, _I, _VP, _VP, ctypes.c_double, _VP]),
     "dwt_effdim_static": (_I, [_VP, _VP, _I, _LL, _I, _VP, _VP, ctypes.c_double, _VP]),
     "dwt_eval_product": (_I, [_VP, _VP, _VP, _I, _LL, _I, _VP]),
     "dwt_eval_exp": (_I, [_VP, _VP, _I, _LL, _I, _VP]),
@@ -98,6 +100,7 @@ _SIGS = {
     "dwt_strerror": (ctypes.c_char_p, [_I]),
     "dwt_last_error": (ctypes.c_char_p, []),
     "dwt_launch_count": (_LL, []),
+    "dwt_alloc_count": (_LL, []),
     "dwt_profile_enable": (_I, [_I]),
     "dwt_profile_reset": (_I, []),
     "dwt_profile_query": (_I, [ctypes.c_char_p, ctypes.POINTER(_LL), ctypes.POINTER(ctypes.c_double)]),
@@ -181,8 +184,19 @@ class Plan:
             pass
 
 
+def dwt_plan(p, m, s, C, flags=0, stream=None):
+    """``dwt_plan``: C is a host array uint8 [s][m][m] (numpy)."""
+    C = np.ascontiguousarray(C, dtype=np.uint8)
+    if C.shape != (s, m, m):
+        raise ValueError("C must have shape (s, m, m)")
+    h = _VP()
+    st = lib().dwt_plan(p, m, s, C.ctypes.data, flags, _stream(stream), ctypes.byref(h))
+    _check(st, allow=(DWT_ESPAN, DWT_EUNSUPPORTED))
+    return Plan(h.value, p, m, s, st)
+
+
 def dwt_plan_create(p, m, s, C, flags=0, stream=None):
-    """``dwt_plan_create``: C is a host array uint8 [s][m][m] (numpy)."""
+    """``dwt_plan_create``, the earlier name of ``dwt_plan``."""
     C = np.ascontiguousarray(C, dtype=np.uint8)
     if C.shape != (s, m, m):
         raise ValueError("C must have shape (s, m, m)")
@@ -300,13 +314,19 @@ def dwt_spline_eval(plan, c, batch, ld, X, Q, M, values, ldv=None, stream=None):
                                         Q if ldv is None else ldv, _stream(stream)))
 
 
-def dwt_effdim(plan, coef, batch, ld, t, var=None, dim=None, threshold=0.99, stream=None):
-    return _check(lib().dwt_effdim(plan.handle, _ptr(coef), batch, ld, t, _ptr(var), _ptr(dim), threshold,
+def dwt_effdim(plan, coef, batch, ld, t, var_trc=None, var_sup=None, d_trc=None, d_sup=None, threshold=0.99,
+               stream=None):
+    return _check(lib().dwt_effdim(plan.handle, _ptr(coef), batch, ld, t, _ptr(var_trc), _ptr(var_sup), _ptr(d_trc),
+                                   _ptr(d_sup), threshold, _stream(stream)))
+
+
+def dwt_effdim_packed(plan, coef, batch, ld, t, var=None, dim=None, threshold=0.99, stream=None):
+    return _check(lib().dwt_effdim_packed(plan.handle, _ptr(coef), batch, ld, t, _ptr(var), _ptr(dim), threshold,
                                    _stream(stream)))
 
 
 def dwt_effdim_static(plan, coef, batch, ld, t, var=None, dim=None, threshold=0.99, stream=None):
-    """dwt_effdim without any device allocation (fixed in-library scratch; see include/dwt.h)."""
+    """dwt_effdim_packed without any device allocation (fixed in-library scratch; see include/dwt.h)."""
     return _check(lib().dwt_effdim_static(plan.handle, _ptr(coef), batch, ld, t, _ptr(var), _ptr(dim), threshold,
                                           _stream(stream)))
 
@@ -329,6 +349,10 @@ def dwt_last_error():
 
 def dwt_launch_count():
     return lib().dwt_launch_count()
+
+
+def dwt_alloc_count():
+    return lib().dwt_alloc_count()
 
 
 def dwt_profile_enable(on=True):

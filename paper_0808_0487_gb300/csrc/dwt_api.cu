@@ -20,6 +20,7 @@ namespace dwt {
 
 static thread_local char g_err[512] = "";
 static std::atomic<long long> g_launches{0};
+static std::atomic<long long> g_allocs{0};
 
 void set_error(const char* fmt, ...) {
     va_list ap;
@@ -94,9 +95,12 @@ int smem_limit_max_ptr(const void* kern) {
 }
 
 // ---- workspace ----------------------------------------------------------------
+void count_host_alloc() { g_allocs.fetch_add(1, std::memory_order_relaxed); }
+
 int dmalloc(void** p, size_t bytes, cudaStream_t st) {
     *p = nullptr;
     if (bytes == 0) bytes = 16;
+    g_allocs.fetch_add(1, std::memory_order_relaxed);
     cudaError_t e = cudaMallocAsync(p, bytes, st);
     if (e != cudaSuccess) {
         cudaGetLastError();
@@ -279,6 +283,8 @@ const char* dwt_last_error(void) { return g_err; }
 
 long long dwt_launch_count(void) { return g_launches.load(); }
 
+long long dwt_alloc_count(void) { return g_allocs.load(); }
+
 int dwt_profile_enable(int on) {
     std::lock_guard<std::mutex> lk(g_prof_mu);
     g_prof_on = on != 0;
@@ -415,6 +421,10 @@ int dwt_plan_create(int p, int m, int s, const uint8_t* C, unsigned flags, void*
     }
     *out = P;
     return rc;
+}
+
+int dwt_plan(int p, int m, int s, const uint8_t* C, unsigned flags, void* stream, dwt_plan_t* out) {
+    return dwt_plan_create(p, m, s, C, flags, stream, out);
 }
 
 int dwt_pass_plan_for(int p, int m, int elem_bytes, long long min_tiles, int* q, int* digits, int* wc) {
@@ -693,10 +703,10 @@ int dwt_spline(dwt_plan_t P, const double* f, void* c, int batch, long long ld, 
     return run_spline(P, f, c, batch, ld, var_trc, var_sup, dim, thr, (cudaStream_t)stream);
 }
 
-int dwt_effdim(dwt_plan_t P, const void* coef, int batch, long long ld, dwt_dtype t, double* var, int* dim, double thr,
-               void* stream) {
+static int effdim_check(dwt_plan_t P, const void* coef, int batch, long long ld, dwt_dtype t, double thr,
+                        const char* who) {
     if (!P || batch < 0 || (batch > 0 && !coef) || ld < P->N || !(thr > 0.0 && thr <= 1.0)) {
-        set_error("dwt_effdim: bad arguments");
+        set_error("%s: bad arguments", who);
         return DWT_EINVAL;
     }
     if (P->tables_status != DWT_OK) {
@@ -704,11 +714,31 @@ int dwt_effdim(dwt_plan_t P, const void* coef, int batch, long long ld, dwt_dtyp
         return P->tables_status > 0 ? P->tables_status : DWT_EUNSUPPORTED;
     }
     if (P->p == 2 ? t != DWT_F32 : t != DWT_C64) {
-        set_error("dwt_effdim: coefficients are F32 (p = 2) or C64 (p > 2)");
+        set_error("%s: coefficients are F32 (p = 2) or C64 (p > 2)", who);
         return DWT_EUNSUPPORTED;
     }
-    if (batch == 0) return DWT_OK;
-    return run_effdim(P, coef, batch, ld, t, var, dim, thr, (cudaStream_t)stream);
+    return DWT_OK;
+}
+
+int dwt_effdim(dwt_plan_t P, const void* coef, int batch, long long ld, dwt_dtype t, double* var_trc, double* var_sup,
+               int* d_trc, int* d_sup, double thr, void* stream) {
+    int rc = effdim_check(P, coef, batch, ld, t, thr, "dwt_effdim");
+    if (rc || batch == 0) return rc;
+    EffOut o;
+    o.vt = var_trc;
+    o.vs = var_sup;
+    o.vstride = P->s + 1;
+    o.dt = d_trc;
+    o.ds = d_sup;
+    o.dstride = 1;
+    return run_effdim(P, coef, batch, ld, t, o, thr, (cudaStream_t)stream);
+}
+
+int dwt_effdim_packed(dwt_plan_t P, const void* coef, int batch, long long ld, dwt_dtype t, double* var, int* dim,
+                      double thr, void* stream) {
+    int rc = effdim_check(P, coef, batch, ld, t, thr, "dwt_effdim_packed");
+    if (rc || batch == 0) return rc;
+    return run_effdim(P, coef, batch, ld, t, eff_packed(var, dim, P->s + 1), thr, (cudaStream_t)stream);
 }
 
 int dwt_eval_product(dwt_plan_t P, const double* coef, void* f, int batch, long long ld, dwt_dtype t, void* stream) {

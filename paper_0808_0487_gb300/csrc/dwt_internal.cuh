@@ -111,6 +111,8 @@ namespace dwt {
 int ensure_workspace(dwt_plan_s* P, size_t bytes, cudaStream_t st);
 // stream-ordered device allocations (no device-wide synchronisation)
 int dmalloc(void** p, size_t bytes, cudaStream_t st);
+// counts a page-locked host allocation in dwt_alloc_count
+void count_host_alloc();
 void dfree(void* p, cudaStream_t st);
 const PassPlan& pass_plan(dwt_plan_s* P, int elem_bytes);
 void pass_geometry(int p, int m, int elem, const int* b, int q, long long min_tiles, int wc_div, PassPlan& pp);
@@ -128,8 +130,30 @@ int run_transform(dwt_plan_s* P, const void* in, void* out, int batch, long long
                   dwt_dtype in_t, dwt_dtype out_t, int sgn, cudaStream_t st);
 int run_interpolate(dwt_plan_s* P, const void* f, void* c, void* coef, int batch, long long ld, dwt_dtype f_t,
                     dwt_weight weight, dwt_algo algo, double* var, int* dim, double thr, cudaStream_t st);
-int run_effdim(dwt_plan_s* P, const void* coef, int batch, long long ld, dwt_dtype t, double* var, int* dim,
-               double thr, cudaStream_t st);
+// outputs of the effective-dimension step: cumulative truncation / superposition
+// variances (row stride vstride doubles per function) and d_trc / d_sup (stride
+// dstride ints); any pointer may be NULL
+struct EffOut {
+    double* vt = nullptr;
+    double* vs = nullptr;
+    long long vstride = 0;
+    int* dt = nullptr;
+    int* ds = nullptr;
+    long long dstride = 0;
+};
+// the packed layout var [batch][2][nb], dim [batch][2]
+static inline EffOut eff_packed(double* var, int* dim, int nb) {
+    EffOut o;
+    o.vt = var;
+    o.vs = var ? var + nb : nullptr;
+    o.vstride = 2ll * nb;
+    o.dt = dim;
+    o.ds = dim ? dim + 1 : nullptr;
+    o.dstride = 2;
+    return o;
+}
+int run_effdim(dwt_plan_s* P, const void* coef, int batch, long long ld, dwt_dtype t, const EffOut& o, double thr,
+               cudaStream_t st);
 // tensor-core low pass (p = 2, low 14 digits): one job of ntiles tiles of
 // 2^14 elements, tpf per function, result times scale
 struct TcJob {

@@ -12,6 +12,9 @@
 // The array lives in the library image: every GPU on which the library is
 // loaded holds it (8 MiB) until the process exits.  Every call on a device
 // shares that one array, and it keeps whatever the last call left in it.
+#include <cuda.h>
+
+#include <map>
 #include <mutex>
 
 #include "dwt_internal.cuh"
@@ -25,26 +28,70 @@ int effdim_into_scratch(dwt_plan_s* Pl, const void* coef, int batch, long long l
 static constexpr long long kEffdimScratchDoubles = 1ll << 20;   // 8 MiB
 static __device__ __align__(256) double g_effdim_scratch[kEffdimScratchDoubles];
 
-static std::mutex g_scratch_mu;
-static double* g_scratch_addr[128];
+// The array's device address belongs to the CUDA context the library's module
+// was loaded in: it is looked up once per context (with that context current)
+// and cached under the context's unique id, which a later context never
+// reuses (so a cudaDeviceReset or a second context on the same device gets its
+// own lookup).  Without the driver's context-id call the cache is keyed by
+// the device index.
+typedef CUresult (*CtxCurrentFn)(CUcontext*);
+typedef CUresult (*CtxIdFn)(CUcontext, unsigned long long*);
 
-// Device address of the array for the current device, looked up once per device.
+static std::mutex g_scratch_mu;
+static std::map<unsigned long long, double*> g_scratch_addr;
+static CtxCurrentFn g_ctx_current = nullptr;
+static CtxIdFn g_ctx_id = nullptr;
+static bool g_ctx_fns_looked_up = false;
+
+static bool context_key(unsigned long long* key) {
+    if (!g_ctx_fns_looked_up) {
+        g_ctx_fns_looked_up = true;
+        void* f1 = nullptr;
+        void* f2 = nullptr;
+        cudaDriverEntryPointQueryResult q1, q2;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f1, 12000, cudaEnableDefault, &q1) == cudaSuccess &&
+            q1 == cudaDriverEntryPointSuccess &&
+            cudaGetDriverEntryPointByVersion("cuCtxGetId", &f2, 12000, cudaEnableDefault, &q2) == cudaSuccess &&
+            q2 == cudaDriverEntryPointSuccess) {
+            g_ctx_current = reinterpret_cast<CtxCurrentFn>(f1);
+            g_ctx_id = reinterpret_cast<CtxIdFn>(f2);
+        }
+        cudaGetLastError();
+    }
+    if (!g_ctx_current || !g_ctx_id) return false;
+    CUcontext ctx = nullptr;
+    if (g_ctx_current(&ctx) != CUDA_SUCCESS || !ctx) return false;
+    return g_ctx_id(ctx, key) == CUDA_SUCCESS;
+}
+
+// Device address of the array in the current context.
 static int scratch_address(double** out) {
-    int dev = 0;
-    cudaError_t e = cudaGetDevice(&dev);
-    if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice", __FILE__, __LINE__);
-    if (dev < 0 || dev >= 128) {
-        set_error("device index %d out of range", dev);
-        return DWT_EINVAL;
-    }
     std::lock_guard<std::mutex> lk(g_scratch_mu);
-    if (!g_scratch_addr[dev]) {
+    unsigned long long key = 0;
+    bool have_key = context_key(&key);
+    if (!have_key) {
+        // no context current yet, or no context-id call: the lookup below makes the
+        // device's primary context current; then key by context, else by device
         void* p = nullptr;
-        e = cudaGetSymbolAddress(&p, g_effdim_scratch);
+        cudaError_t e = cudaGetSymbolAddress(&p, g_effdim_scratch);
         if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress", __FILE__, __LINE__);
-        g_scratch_addr[dev] = static_cast<double*>(p);
+        have_key = context_key(&key);
+        if (!have_key) {
+            int dev = 0;
+            e = cudaGetDevice(&dev);
+            if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice", __FILE__, __LINE__);
+            key = ~0ull - (unsigned long long)dev;
+        }
+        g_scratch_addr[key] = static_cast<double*>(p);
     }
-    *out = g_scratch_addr[dev];
+    auto it = g_scratch_addr.find(key);
+    if (it == g_scratch_addr.end()) {
+        void* p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, g_effdim_scratch);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress", __FILE__, __LINE__);
+        it = g_scratch_addr.emplace(key, static_cast<double*>(p)).first;
+    }
+    *out = it->second;
     return DWT_OK;
 }
 

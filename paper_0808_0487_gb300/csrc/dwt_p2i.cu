@@ -598,6 +598,7 @@ static std::mutex g_status_mu;
 static int status_word(int** host, int** dev) {
     std::lock_guard<std::mutex> lk(g_status_mu);
     if (!g_status) {
+        count_host_alloc();
         if (cudaHostAlloc((void**)&g_status, sizeof(int), cudaHostAllocMapped | cudaHostAllocPortable) != cudaSuccess) {
             cudaGetLastError();
             g_status = nullptr;

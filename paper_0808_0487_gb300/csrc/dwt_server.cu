@@ -133,6 +133,8 @@ static void worker_main(dwt_server_s* S) {
     cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
     double* var_h = nullptr;
     int* dim_h = nullptr;
+    count_host_alloc();
+    count_host_alloc();
     cudaMallocHost(&var_h, 2 * 256 * sizeof(double));
     cudaMallocHost(&dim_h, 2 * sizeof(int));
     for (;;) {

@@ -517,8 +517,8 @@ __global__ void __launch_bounds__(256) k_effdim_classes(const double* __restrict
 }
 
 // per-class totals -> cumulative truncation / superposition variances and dimensions
-__global__ void __launch_bounds__(32) k_effdim_finalize(const double* __restrict__ csum, int nb, double thr,
-                                                         double* __restrict__ var, int* __restrict__ dim, int batch) {
+__global__ void __launch_bounds__(32) k_effdim_finalize(const double* __restrict__ csum, int nb, double thr, EffOut o,
+                                                         int batch) {
     // one warp per function: the class totals come into shared memory together,
     // then lane 0 forms the cumulative sums in class order
     __shared__ double c[2 * 256];
@@ -536,19 +536,15 @@ __global__ void __launch_bounds__(32) k_effdim_finalize(const double* __restrict
     for (int d = 0; d < nb; ++d) {
         ct += c[d];
         cs += c[nb + d];
-        if (var) {
-            var[((long long)fn * 2 + 0) * nb + d] = ct;
-            var[((long long)fn * 2 + 1) * nb + d] = cs;
-        }
+        if (o.vt) o.vt[(long long)fn * o.vstride + d] = ct;
+        if (o.vs) o.vs[(long long)fn * o.vstride + d] = cs;
         if (tot > 0.0) {
             if (!ft && ct >= thr * tot) { dt = d; ft = true; }
             if (!fs && cs >= thr * tot) { ds = d; fs = true; }
         }
     }
-    if (dim) {
-        dim[(long long)fn * 2 + 0] = dt;
-        dim[(long long)fn * 2 + 1] = ds;
-    }
+    if (o.dt) o.dt[(long long)fn * o.dstride] = dt;
+    if (o.ds) o.ds[(long long)fn * o.dstride] = ds;
 }
 
 // ---------------------------------------------------------------------------
@@ -710,9 +706,9 @@ static int bins_warps(size_t tile_bytes, int nb2, size_t budget = 227 * 1024, in
     return (int)std::max<size_t>(1, std::min<size_t>(maxw, std::min(avail, budget) / per_warp));
 }
 
-static int finalize(dwt_plan_s* Pl, const double* part, long long nchunk, int batch, double thr, double* var, int* dim,
+static int finalize(dwt_plan_s* Pl, const double* part, long long nchunk, int batch, double thr, const EffOut& o,
                     cudaStream_t st) {
-    if (!var && !dim) return DWT_OK;
+    if (!o.vt && !o.vs && !o.dt && !o.ds) return DWT_OK;
     const int nb = Pl->s + 1, nb2 = 2 * nb;
     // per-class totals go right after the partials in the workspace
     double* csum = const_cast<double*>(part) + (size_t)batch * nb2 * nchunk;
@@ -725,7 +721,7 @@ static int finalize(dwt_plan_s* Pl, const double* part, long long nchunk, int ba
     DWT_CK_LAUNCH("k_effdim_classes");
     {
         LaunchScope ls("effdim_finalize", st);
-        k_effdim_finalize<<<batch, 32, 0, st>>>(csum, nb, thr, var, dim, batch);
+        k_effdim_finalize<<<batch, 32, 0, st>>>(csum, nb, thr, o, batch);
     }
     DWT_CK_LAUNCH("k_effdim_finalize");
     return DWT_OK;
@@ -803,7 +799,7 @@ static int interpolate_t(dwt_plan_s* Pl, const void* f, void* c, void* coef, int
             if (rc) return rc;
         }
     }
-    return finalize(Pl, part, ntile, batch, thr, var, dim, st);
+    return finalize(Pl, part, ntile, batch, thr, eff_packed(var, dim, nb), st);
 }
 
 int run_interpolate(dwt_plan_s* Pl, const void* f, void* c, void* coef, int batch, long long ld, dwt_dtype f_t,
@@ -820,7 +816,7 @@ int run_interpolate(dwt_plan_s* Pl, const void* f, void* c, void* coef, int batc
                                  weight == DWT_WEIGHT_INV_SQ_WAVENUMBER, algo == DWT_ALGO_TC_SPLIT_BF16, &part, &ntile,
                                  st);
         if (rc) return rc;
-        return finalize(Pl, part, ntile, batch, thr, var, dim, st);
+        return finalize(Pl, part, ntile, batch, thr, eff_packed(var, dim, Pl->s + 1), st);
     }
     if (fast) {
         double* part = nullptr;
@@ -829,7 +825,7 @@ int run_interpolate(dwt_plan_s* Pl, const void* f, void* c, void* coef, int batc
                                 weight == DWT_WEIGHT_INV_SQ_WAVENUMBER ? Pl->d_W : nullptr,
                                 algo == DWT_ALGO_TC_SPLIT_BF16, &part, &ntile, st);
         if (rc) return rc;
-        return finalize(Pl, part, ntile, batch, thr, var, dim, st);
+        return finalize(Pl, part, ntile, batch, thr, eff_packed(var, dim, Pl->s + 1), st);
     }
     switch (Pl->p) {
         case 2: return interpolate_t<2, float, float>(Pl, f, c, coef, batch, ld, weight, var, dim, thr, st);
@@ -853,7 +849,7 @@ int run_interpolate(dwt_plan_s* Pl, const void* f, void* c, void* coef, int batc
 }
 
 template <typename T>
-static int effdim_t(dwt_plan_s* Pl, const void* coef, int batch, long long ld, double* var, int* dim, double thr,
+static int effdim_t(dwt_plan_s* Pl, const void* coef, int batch, long long ld, const EffOut& o, double thr,
                     cudaStream_t st) {
     const int nb = Pl->s + 1, nb2 = 2 * nb;
     const long long nchunk = (Pl->N + 8191) / 8192;
@@ -876,7 +872,7 @@ static int effdim_t(dwt_plan_s* Pl, const void* coef, int batch, long long ld, d
             (const T*)coef + (long long)f0 * ld, ld, Pl->N, Pl->d_cls, nb, nchunk, part + (long long)f0 * nchunk * nb2);
     }
     DWT_CK_LAUNCH("k_effdim_bins");
-    return finalize(Pl, part, nchunk, batch, thr, var, dim, st);
+    return finalize(Pl, part, nchunk, batch, thr, o, st);
 }
 
 // The class sums of effdim_t, with the partials and totals in a scratch array
@@ -907,8 +903,9 @@ static int effdim_scratch_t(dwt_plan_s* Pl, const void* coef, int batch, long lo
                 (const T*)coef + (long long)f0 * ld, ld, Pl->N, Pl->d_cls, nb, nchunk, scratch);
         }
         DWT_CK_LAUNCH("k_effdim_bins");
-        rc = finalize(Pl, scratch, nchunk, nf, thr, var ? var + (long long)f0 * 2 * nb : nullptr,
-                      dim ? dim + (long long)f0 * 2 : nullptr, st);
+        rc = finalize(Pl, scratch, nchunk, nf, thr, eff_packed(var ? var + (long long)f0 * 2 * nb : nullptr,
+                                                                dim ? dim + (long long)f0 * 2 : nullptr, nb),
+                      st);
         if (rc) return rc;
     }
     return DWT_OK;
@@ -920,10 +917,10 @@ int effdim_into_scratch(dwt_plan_s* Pl, const void* coef, int batch, long long l
     return effdim_scratch_t<float2>(Pl, coef, batch, ld, var, dim, thr, scratch, cap, st);
 }
 
-int run_effdim(dwt_plan_s* Pl, const void* coef, int batch, long long ld, dwt_dtype t, double* var, int* dim,
-               double thr, cudaStream_t st) {
-    if (t == DWT_F32) return effdim_t<float>(Pl, coef, batch, ld, var, dim, thr, st);
-    return effdim_t<float2>(Pl, coef, batch, ld, var, dim, thr, st);
+int run_effdim(dwt_plan_s* Pl, const void* coef, int batch, long long ld, dwt_dtype t, const EffOut& o, double thr,
+               cudaStream_t st) {
+    if (t == DWT_F32) return effdim_t<float>(Pl, coef, batch, ld, o, thr, st);
+    return effdim_t<float2>(Pl, coef, batch, ld, o, thr, st);
 }
 
 }  // namespace dwt

@@ -50,6 +50,18 @@ def test_strerror_and_host_checks(dwtlib):
         dwtlib.dwt_plan_create(2, 32, 1, np.zeros((1, 32, 32), dtype=np.uint8))
 
 
+def test_plan_and_plan_create_are_one_call(dwtlib):
+    """dwt_plan is the plan call of the boundary; dwt_plan_create keeps the same
+    behaviour (here: the host-side argument checks, no device work)."""
+    for bad in ((4, 3, 1, np.zeros((1, 3, 3), dtype=np.uint8)),      # p not prime
+                (2, 3, 1, np.full((1, 3, 3), 2, dtype=np.uint8)),     # entry >= p
+                (2, 3, 0, np.zeros((0, 3, 3), dtype=np.uint8))):      # s < 1
+        for call in (dwtlib.dwt_plan, dwtlib.dwt_plan_create):
+            with pytest.raises(dwtlib.DwtError) as e:
+                call(*bad)
+            assert e.value.status == dwtlib.DWT_EINVAL
+
+
 def test_no_cpu_fallback_in_package():
     """The product package never imports the oracle."""
     pkg = os.path.join(ROOT, "paper_0808_0487_gb300")

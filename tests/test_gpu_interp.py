@@ -124,7 +124,15 @@ def test_effdim_standalone(dwt, dev, orc, p, m, s):
         t = dwt.DWT_C64
     var = torch.empty((B, 2, s + 1), dtype=torch.float64, device=dev)
     dim = torch.empty((B, 2), dtype=torch.int32, device=dev)
-    dwt.dwt_effdim(plan, gin, B, N if p == 2 else N, t, var=var, dim=dim, threshold=0.9)
+    dwt.dwt_effdim_packed(plan, gin, B, N if p == 2 else N, t, var=var, dim=dim, threshold=0.9)
+    # the same sums in the separate-array layout of dwt_effdim
+    vtr = torch.full((B, s + 1), -1.0, dtype=torch.float64, device=dev)
+    vsu = torch.full((B, s + 1), -1.0, dtype=torch.float64, device=dev)
+    dtr = torch.full((B,), -1, dtype=torch.int32, device=dev)
+    dsu = torch.full((B,), -1, dtype=torch.int32, device=dev)
+    dwt.dwt_effdim(plan, gin, B, N, t, var_trc=vtr, var_sup=vsu, d_trc=dtr, d_sup=dsu, threshold=0.9)
+    assert np.array_equal(_np(vtr), _np(var)[:, 0]) and np.array_equal(_np(vsu), _np(var)[:, 1])
+    assert np.array_equal(_np(dtr), _np(dim)[:, 0]) and np.array_equal(_np(dsu), _np(dim)[:, 1])
     for b in range(B):
         vt, vs, dt, ds = orc.effdim(gref[b], tab["cls"], s, 0.9)
         assert np.allclose(_np(var)[b, 0], vt, rtol=1e-5)

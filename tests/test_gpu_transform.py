@@ -112,6 +112,37 @@ def test_p3_m13_complex(dwt, dev, orc):
     assert np.abs(gb.imag).max() < 1e-5 * np.abs(f).max()
 
 
+# the inverse on its own (Algorithm 2 / Lemma 3.1), fed with given coefficients,
+# against the oracle's FP64 Algorithm 2 of the same (FP32-rounded) coefficients,
+# function by function; p = 2 at the register-tile sizes (m = 20 in a batch of
+# 3 with a padded ld, m = 24 in a batch of 2) and p = 3, m = 13 (complex)
+@pytest.mark.parametrize("p,m,B,pad", [(2, 20, 3, 4), (2, 24, 2, 0), (3, 13, 2, 1)])
+def test_inverse_alone_vs_oracle(dwt, dev, orc, p, m, B, pad):
+    N = p ** m
+    ld = N + pad
+    plan = dwt.dwt_plan_create(p, m, 1, S.small_net(p, m, 1, index=7), dwt.DWT_PLAN_TRANSFORM_ONLY)
+    if p == 2:
+        g = (S.uniform(S.stream_seed(25, S.P_VALUES, m), B * ld) - 0.5).astype(np.float32).reshape(B, ld)
+        x = torch.tensor(g, device=dev)
+        y = torch.full_like(x, 7.0)
+        dwt.dwt_inverse(plan, x, y, B, ld, ld, dwt.DWT_F32, dwt.DWT_F32)
+        yh = _np(y)
+        for b in range(B):
+            ref = orc.fiwt(p, m, g[b, :N].astype(np.float64)).real
+            assert rel_l2(yh[b, :N], ref) < TOL32, b
+            assert np.all(yh[b, N:] == 7.0)          # the padding of ld is not written
+    else:
+        g = (S.uniform(S.stream_seed(25, S.P_VALUES, m), 2 * B * ld) - 0.5).astype(np.float32).reshape(B, 2 * ld)
+        x = torch.tensor(g, device=dev)
+        y = torch.empty_like(x)
+        dwt.dwt_inverse(plan, x, y, B, ld, ld, dwt.DWT_C64, dwt.DWT_C64)
+        yh = _cplx(y)
+        for b in range(B):
+            cin = g[b, 0:2 * N:2].astype(np.float64) + 1j * g[b, 1:2 * N:2].astype(np.float64)
+            ref = orc.fiwt(p, m, cin)
+            assert rel_l2(yh[b, :N], ref) < TOL32, b
+
+
 # sizes chosen so that the pass decomposition has 1, 2 and 3 passes and ragged tiles
 @pytest.mark.parametrize("p,m", [(2, 1), (2, 14), (2, 15), (2, 25), (3, 1), (3, 9), (5, 3), (5, 10), (7, 2), (7, 8),
                                  (11, 1), (11, 5), (13, 2), (13, 5)])
