@@ -61,21 +61,27 @@ def rank_requests(count, rank):
 
 
 class ClockSampler:
-    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+    """nvidia-smi clocks and throttle reasons sampled every 20 ms while the timed
+    region runs.  Samples carry the host time they were read; ``mark`` records
+    the timed region's bounds, so the summary reports the samples inside it and
+    those of the whole sampled window (the timed region padded by untimed
+    replays of the same step before and after it)."""
     Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
          "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
          "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+    PERIOD_MS = 20
 
     def __init__(self, index):
         self.index = index
         self.proc = None
         self.lines = []
+        self.region = None
 
     def __enter__(self):
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.Q, "--format=csv,noheader,nounits",
-                 "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+                 "-lms", str(self.PERIOD_MS)], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.t = threading.Thread(target=self._read, daemon=True)
             self.t.start()
             # the sampler is running (first line read) before the timed region starts
@@ -89,7 +95,10 @@ class ClockSampler:
 
     def _read(self):
         for line in self.proc.stdout:
-            self.lines.append(line.strip())
+            self.lines.append((time.perf_counter(), line.strip()))
+
+    def mark(self, t0, t1):
+        self.region = (t0, t1)
 
     def __exit__(self, *a):
         if self.proc:
@@ -99,10 +108,11 @@ class ClockSampler:
             except subprocess.TimeoutExpired:
                 self.proc.kill()
 
-    def summary(self):
+    @staticmethod
+    def _parse(lines):
         sm, mx, reasons = [], None, set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for ln in self.lines:
+        for ln in lines:
             parts = [x.strip() for x in ln.split(",")]
             if len(parts) < 9:
                 continue
@@ -114,8 +124,20 @@ class ClockSampler:
             for nm, v in zip(names, parts[5:9]):
                 if v.lower().startswith("active"):
                     reasons.add(nm)
-        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx,
-                "reasons": sorted(reasons), "samples": len(sm)}
+        return sm, mx, reasons
+
+    def summary(self):
+        sm, mx, reasons = self._parse([ln for _, ln in self.lines])
+        inside = [ln for _, ln in self.lines]
+        if self.region:
+            # a sample read at host time t describes the GPU during the preceding period
+            t0, t1 = self.region
+            inside = [ln for t, ln in self.lines if t0 < t <= t1 + self.PERIOD_MS / 1e3]
+        smi, _, reasons_i = self._parse(inside)
+        return {"sm_mhz": statistics.median(smi) if smi else (statistics.median(sm) if sm else None),
+                "sm_max_mhz": mx, "reasons": sorted(reasons | reasons_i), "samples": len(smi),
+                "samples_window": len(sm), "period_ms": self.PERIOD_MS,
+                "window": "the timed region padded by about 0.3 s of untimed replays of the same step on each side"}
 
 
 def _bind_to_gpu_node(local):
@@ -194,7 +216,11 @@ def run_reference(args):
         "steps": len(times), "warmup": 0, "ms_per_step": t * 1e3, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": "p2_m24_s32_b32", "p": 2, "m": 24, "s": 32, "global_batch": 32,
-                   "l2": "inputs larger than L2"},
+                   "l2": "inputs larger than L2",
+                   "subsample": {"functions_per_step": threads, "of_batch": 32, "steps": len(times),
+                                 "steps_asked": args.steps, "warmup": 0,
+                                 "tables": "K(C) weight and class tables replaced by constants (plan time is "
+                                           "excluded on both arms; the timed arithmetic does not depend on them)"}},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
                          "sample": "%d of the 32 functions (N=2^24) per step, one per thread, forward+weight+class "
                                    "sums+inverse in FP64; K(C) tables replaced by constants" % threads},
@@ -203,11 +229,12 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
-def cpu_baseline_sample():
+def cpu_baseline_sample(acc_in=None):
     """Oracle time on a bounded sample of the workload: one function on one thread,
     then one function per thread on every host core this process may use (the
     oracle's C routines release the interpreter lock, so the threads run in
-    parallel).  About 10-20 s in total."""
+    parallel).  About 10-20 s in total.  With acc_in (GPU outputs for function 0
+    of the workload) it also returns their deviation from the FP64 oracle."""
     import concurrent.futures as cf
 
     import numpy as np
@@ -231,10 +258,35 @@ def cpu_baseline_sample():
         t0 = time.perf_counter()
         list(ex.map(lambda _: oracle.interpolate(p, m, f, W, cls, s)[3], range(threads)))
         tn = time.perf_counter() - t0
+    acc = accuracy_vs_oracle(acc_in, f) if acc_in is not None else None
     return {"value": threads * N / tn, "unit": UNIT, "cores": threads, "kind": "oracle",
-            "single_thread_value": N / t1,
+            "single_thread_value": N / t1, "accuracy_vs_oracle": acc,
             "sample": "%d functions of the batch (N=2^24 each), one per thread, forward+weight+class sums+inverse "
                       "in FP64; K(C) tables replaced by constants (plan time excluded on both arms)" % threads}
+
+
+def accuracy_vs_oracle(acc_in, f):
+    """Relative L2 of the GPU results of function 0 of the timed workload against
+    the FP64 oracle (Algorithm 1 of the oracle's own f), per path, and the int32
+    path's bit-exactness on one function of the p = 2, m = 20 int32 workload."""
+    import numpy as np
+
+    import oracle
+    import synthetic as S
+
+    def rel(a, b):
+        return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+    ref = oracle.fwt(2, 24, f).real
+    out = {"function": "0 of p2_m24_s32_b32 (N = 2^24), oracle FP64",
+           "forward_f32_butterfly_rel_l2": rel(acc_in["fwd_f32"], ref),
+           "forward_split_bf16_tc_rel_l2": rel(acc_in["fwd_tc"], ref),
+           "round_trip_f32_rel_l2": rel(acc_in["round_trip_f32"], f),
+           "tolerance_f32": 1e-5}
+    w20 = S.workload_p2_m20()
+    v = S.int_values(w20["int_seed"], 1, 1 << 20)[0].astype(np.int64)
+    out["forward_i32_m20_bit_exact"] = bool(np.array_equal(acc_in["fwd_i32_m20"], oracle.fwt_i64(20, v)))
+    return out
 
 
 # DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) of the
@@ -243,9 +295,10 @@ def cpu_baseline_sample():
 # with the SHA-256 of the kernel source they were taken from.  Any change to
 # that source makes the figures stale: they are then reported as null.
 MEASURED_TRAFFIC = {
-    "source": "paper_0808_0487_gb300/csrc/dwt_p2.cu",
-    "sha256": "d5817a54e3488a2523e3eed1b9f7d1425cde7ecd87e8f31c62971d3a0567a276",
-    "bytes_per_launch": {"interp_top": 155.6e6, "interp_inv_fwd": 146.4e6},
+    "source": "paper_0808_0487_gb300/csrc/dwt_p2i.cu",
+    "sha256": "ff8d3c25a64fbece2da25680f6fa7bcfdb8b4a3583aa88ee7ae4af65719cfa35",
+    # top pass: mean of three launches (87.3, 83.2, 106.7 MB); paired low pass: one launch
+    "bytes_per_launch": {"interp_top": 92.4e6, "interp_inv_fwd": 139.6e6},
 }
 
 
@@ -258,6 +311,77 @@ def _traffic(family):
     if hashlib.sha256(src).hexdigest() != MEASURED_TRAFFIC["sha256"]:
         return None
     return MEASURED_TRAFFIC["bytes_per_launch"].get(family)
+
+
+# Algorithmic bytes of one launch of each kernel family of dwt_interpolate at
+# p = 2 (batch B, N points per function), from the per-point figures of the
+# method: the whole interpolation moves f in and c out once (8 B per point) plus
+# the weight and class tables once per batch (6 B per point / B).  The fused top
+# pass carries one function's step (its share of the tables included); the
+# paired low pass (interp_inv_fwd) reads one function's input and writes another
+# function's result, 8 B per point; a lone low pass moves one of the two, 4 B.
+def launch_bytes(family, N, B):
+    per = {"interp_top": (8.0 + 6.0 / B) * N, "interp_inv_fwd": 8.0 * N, "interp_fwd": 4.0 * N,
+           "interp_inv": 4.0 * N}
+    return per.get(family)
+
+
+# The launch's own loads and stores (what it touches, L2 included): the top pass
+# reads and writes the intermediate and reads its 3-byte tables; a low pass
+# reads and writes one function.
+def launch_touched_bytes(family, N):
+    per = {"interp_top": 11.0 * N, "interp_inv_fwd": 16.0 * N, "interp_fwd": 8.0 * N, "interp_inv": 8.0 * N}
+    return per.get(family)
+
+
+def roofline(dom, fams, N, B, peak, peak_kind):
+    n, tot = fams[dom]
+    avg_s = tot / n / 1e3
+    alg = launch_bytes(dom, N, B)
+    if alg is None:
+        return None
+    ach = alg / avg_s / 1e9
+    roof = {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
+            "traffic": _traffic(dom), "kernel": dom, "peak_kind": peak_kind, "avg_launch_us": avg_s * 1e6,
+            "launches": n, "algorithmic_bytes_per_launch": alg,
+            "touched_bytes_per_launch": launch_touched_bytes(dom, N),
+            "touched_gbs": launch_touched_bytes(dom, N) / avg_s / 1e9}
+    if roof["traffic"]:
+        roof["dram_gbs"] = roof["traffic"] / avg_s / 1e9
+        roof["dram_frac"] = roof["dram_gbs"] / peak
+        roof["dram_bytes_per_point"] = roof["traffic"] / N
+    return roof
+
+
+def memory_floor(f, c, B, N, stream, peak):
+    """Time of the dwt_interpolate traffic pattern per function with no arithmetic:
+    three torch copies per function (f_b into an L2-sized buffer, that buffer
+    read and written in place, the buffer into c_b).  The step cannot be faster
+    than its memory traffic; this shows where that floor lies on this GPU."""
+    import torch
+    buf = torch.empty(N, dtype=torch.float32, device=f.device)
+
+    def one_pass():
+        for b in range(B):
+            buf.copy_(f[b])
+            buf.mul_(1.0000001)
+            c[b].copy_(buf)
+
+    with torch.cuda.stream(torch.cuda.ExternalStream(stream.cuda_stream)):
+        one_pass()
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(3):
+            one_pass()
+        e1.record()
+        torch.cuda.synchronize()
+    us = e0.elapsed_time(e1) * 1e3 / (3 * B)
+    return {"us_per_function": us, "points_per_s": N / (us / 1e6),
+            "step_hbm_frac_at_floor": N * (8.0 + 6.0 / B) / (us / 1e6) / 1e9 / peak,
+            "how": "per function: copy f_b to a 64 MB buffer, buffer *= 1 in place, copy to c_b (torch kernels), "
+                   "CUDA events over 3 passes of the batch"}
 
 
 def run_other_configs(dwt, dev, stream, timed, steps):
@@ -427,6 +551,8 @@ def run_gpu(args):
         dwt.dwt_interpolate(plan, f, c, None, B, N, dwt.DWT_F32, dwt.DWT_WEIGHT_INV_SQ_WAVENUMBER,
                             var=var, dim=dim, stream=stream if st_ is None else st_)
 
+    region = {}
+
     def timed(fn, K):
         for _ in range(args.warmup):
             fn()
@@ -436,11 +562,13 @@ def run_gpu(args):
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         l0 = dwt.dwt_launch_count()
+        t0 = time.perf_counter()
         e0.record(stream)
         for _ in range(K):
             fn()
         e1.record(stream)
         torch.cuda.synchronize()
+        region["t"] = (t0, time.perf_counter())
         launches = dwt.dwt_launch_count() - l0
         if pg:
             pg.barrier()
@@ -463,8 +591,20 @@ def run_gpu(args):
     def gstep():
         graph.replay()
 
+    def pad(seconds):
+        # untimed replays of the same step, so that the clock sampler also sees the
+        # GPU under this load just before and after the (short) timed region
+        t_end = time.perf_counter() + seconds
+        while time.perf_counter() < t_end:
+            for _ in range(4):
+                gstep()
+            torch.cuda.synchronize()
+
     with ClockSampler(local) as clk:
+        pad(0.3)
         ms, _ = timed(gstep, args.steps)
+        clk.mark(*region["t"])
+        pad(0.3)
     launches = launches_per_step * args.steps
     clocks = clk.summary()
     value = whole_job_rate(B * N * args.steps, ws, ms)
@@ -501,9 +641,25 @@ def run_gpu(args):
     torch.cuda.synchronize()
     tc_rel = float((torch.linalg.vector_norm((c_tc - c).double()) / torch.linalg.vector_norm(c.double())).item())
     tc_max = float(((c_tc - c).abs().max() / c.abs().max()).item())
+    # outputs of function 0 of the timed workload for the comparison with the FP64
+    # oracle in the CPU leg: FP32 forward, split-BF16 forward, FP32 round trip
+    acc_in = {"fwd_f32": c[0].cpu().numpy().astype(np.float64), "fwd_tc": c_tc[0].cpu().numpy().astype(np.float64)}
+    dwt.dwt_inverse(plan, c, c_tc, B, N, N, dwt.DWT_F32, dwt.DWT_F32, stream=stream)
+    torch.cuda.synchronize()
+    acc_in["round_trip_f32"] = c_tc[0].cpu().numpy().astype(np.float64)
     del c_tc
+    # int32 forward (bit-exact path) of one p = 2, m = 20 function of the int32 workload
+    w20 = S.workload_p2_m20()
+    plan20 = dwt.dwt_plan_create(2, 20, w20["s"], w20["C"], dwt.DWT_PLAN_TRANSFORM_ONLY)
+    vi = torch.from_numpy(S.int_values(w20["int_seed"], 1, 1 << 20)).to(dev)
+    vo = torch.empty_like(vi)
+    dwt.dwt_forward(plan20, vi, vo, 1, 1 << 20, 1 << 20, dwt.DWT_I32, dwt.DWT_I32, stream=stream)
+    torch.cuda.synchronize()
+    acc_in["fwd_i32_m20"] = vo[0].cpu().numpy().astype(np.int64)
+    del vi, vo, plan20
 
-    # per-kernel durations of the same step with events around every launch
+    # per-kernel durations of the same step with events around every launch (on
+    # the launching stream)
     dwt.dwt_profile_reset()
     dwt.dwt_profile_enable(True)
     ms_prof, _ = timed(step, args.steps)
@@ -514,24 +670,13 @@ def run_gpu(args):
         if n:
             fams[name] = (n, tot)
     dom = max(fams, key=lambda k: fams[k][1]) if fams else None
-    # algorithmic bytes per point of the launch's own inputs and outputs: a low pass
-    # reads and writes 4 B per point; the fused top pass also reads the weight (4 B)
-    # and class (2 B) tables; interp_inv_fwd holds two low passes (2N points).
-    bytes_per_point = {"interp_fwd": 8.0, "interp_top": 14.0, "interp_inv": 8.0, "interp_inv_fwd": 8.0}
-    points_per_launch = {"interp_inv_fwd": 2 * N}
-    roof = None
-    if dom in bytes_per_point:
-        n, tot = fams[dom]
-        avg_s = tot / n / 1e3
-        ach = bytes_per_point[dom] * points_per_launch.get(dom, N) / avg_s / 1e9
-        roof = {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
-                "traffic": _traffic(dom), "kernel": dom, "peak_kind": peak_kind,
-                "avg_launch_us": avg_s * 1e6, "launches": n,
-                "bytes_per_point": bytes_per_point[dom]}
-        if roof["traffic"]:
-            roof["dram_gbs"] = roof["traffic"] / avg_s / 1e9
-            roof["dram_frac"] = roof["dram_gbs"] / peak
+    roof = roofline(dom, fams, N, B, peak, peak_kind) if dom else None
     dwt.dwt_profile_reset()
+
+    # memory floor of the three-pass schedule on this GPU: the same traffic per
+    # function with no arithmetic (torch copies: f_b -> an L2-sized buffer, the
+    # buffer read and written in place, the buffer -> c_b), for comparison
+    floor = memory_floor(f, c, B, N, stream, peak)
 
     # end to end: pinned host f -> device, the step, c and the variances back
     host_cpus = _bind_to_gpu_node(local)
@@ -552,9 +697,24 @@ def run_gpu(args):
 
     others = run_other_configs(dwt, dev, stream, timed, args.steps) if not args.no_others else None
 
+    # a bounded serving leg: the request mix of the serving workload (own nets,
+    # plan build included), saturated and at 0.9 of the saturated rate
+    serving = None
+    if args.serve_requests > 0:
+        del fh, ch
+        torch.cuda.synchronize()
+        runs = serve_runs(dwt, rank_requests(args.serve_requests, rank), args.slots, (0.9,))
+        r9 = runs[-1]
+        serving = {"requests": args.serve_requests, "slots": args.slots, "rate_req_s": r9["rate_req_s"],
+                   "p50_ms": r9["p50_ms"], "p99_ms": r9["p99_ms"], "req_per_s": r9["req_per_s"],
+                   "points_per_s": r9["points_per_s"], "plan_p50_ms": r9["plan_p50_ms"],
+                   "plan_p99_ms": r9["plan_p99_ms"], "service_p99_ms": r9["service_p99_ms"],
+                   "saturated": {k: runs[0][k] for k in ("req_per_s", "points_per_s", "plan_p50_ms", "plan_p99_ms")},
+                   "latency": "submit to results on the host, queueing and plan build included"}
+
     cpu = None
     if rank == 0 and not args.no_cpu:
-        cpu = cpu_baseline_sample()
+        cpu = cpu_baseline_sample(acc_in)
 
     if rank == 0:
         line = {
@@ -565,6 +725,13 @@ def run_gpu(args):
                        "N": N, "weight": "prod_j (1+k_j)^-2", "l2": "inputs larger than L2 (2 GiB per rank)",
                        "parallelism": "replicas" if ws > 1 else "single", "host_cpus": host_cpus},
             "roofline": roof,
+            "step_roofline": {"bound": "hbm", "unit": "GB/s", "peak": peak, "peak_kind": peak_kind,
+                              "bytes_per_point": 8 + 6.0 / B,
+                              "achieved": B * N * (8 + 6.0 / B) * args.steps / (ms / 1e3) / 1e9,
+                              "frac": B * N * (8 + 6.0 / B) * args.steps / (ms / 1e3) / 1e9 / peak},
+            "memory_floor": floor,
+            "accuracy_vs_oracle": cpu.get("accuracy_vs_oracle") if cpu else None,
+            "serving": serving,
             "cpu_baseline": cpu,
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": B * N * 4,
                     "d2h_bytes_per_step": B * N * 4 + B * 2 * (s + 1) * 8 + B * 2 * 4},
@@ -591,22 +758,16 @@ def run_gpu(args):
         pg.destroy_process_group()
 
 
-def run_serve(args):
-    """The serving workload: requests with their own nets, Poisson arrivals, continuous batching."""
+def serve_runs(dwt, reqs, slots, fracs):
+    """The serving mix: all arrivals at t = 0 (saturated rate R_sat), then Poisson
+    arrivals at each fraction of R_sat.  Latency includes queueing and plan build."""
     import numpy as np
 
-    import paper_0808_0487_gb300 as dwt
     import synthetic as S
-
-    ws, rank, local = _dist()
-    import torch
-    torch.cuda.set_device(local)
-    dwt.lib()
-    reqs = rank_requests(args.requests, rank)
     warm = S.serving_requests(16, first=10 ** 6)
 
     def run(rate, label):
-        srv = dwt.dwt_server_create(0, slots=args.slots, max_queue=1 << 20)
+        srv = dwt.dwt_server_create(0, slots=slots, max_queue=1 << 20)
         for r in warm:
             dwt.dwt_server_wait(srv, dwt.dwt_server_submit(srv, r["p"], r["m"], r["s"], r["C"], r["coef"]))
         t_arr = None if rate is None else S.poisson_arrivals(len(reqs), rate)
@@ -645,8 +806,21 @@ def run_serve(args):
 
     sat = run(None, "saturated")
     runs = [sat]
-    for frac in (0.5, 0.9):
+    for frac in fracs:
         runs.append(run(frac * sat["req_per_s"], "poisson_%.1f" % frac))
+    return runs
+
+
+def run_serve(args):
+    """The serving workload: requests with their own nets, Poisson arrivals, continuous batching."""
+    import paper_0808_0487_gb300 as dwt
+
+    ws, rank, local = _dist()
+    import torch
+    torch.cuda.set_device(local)
+    dwt.lib()
+    reqs = rank_requests(args.requests, rank)
+    runs = serve_runs(dwt, reqs, args.slots, (0.5, 0.9))
     if rank == 0:
         line = {"metric": "served p99 latency (ms), 10k-request mix p in {2,3,5}, N 2^10..2^22, s 2..64",
                 "value": runs[-1]["p99_ms"], "unit": "ms", "n_gpus": ws, "higher_is_better": False,
@@ -667,6 +841,8 @@ def main():
     ap.add_argument("--serve", action="store_true", help="run the serving workload instead")
     ap.add_argument("--requests", type=int, default=10000)
     ap.add_argument("--slots", type=int, default=8)
+    ap.add_argument("--serve-requests", type=int, default=2000,
+                    help="requests of the bounded serving leg of the default run (0: skip)")
     args = ap.parse_args()
     if args.serve:
         run_serve(args)

@@ -18,13 +18,37 @@ def _line(sm, mx, hw="Not Active", hwt="Not Active", swt="Not Active", cap="Not 
 
 def test_clock_summary_median_and_reasons():
     cs = bench.ClockSampler(0)
-    cs.lines = [_line(2070, 2070), _line(2055, 2070, cap="Active"), _line(1980, 2070), "garbage", "0, N/A, 2070"]
+    lines = [_line(2070, 2070), _line(2055, 2070, cap="Active"), _line(1980, 2070), "garbage", "0, N/A, 2070"]
+    cs.lines = [(1.0 + 0.01 * i, ln) for i, ln in enumerate(lines)]
     s = cs.summary()
     assert s["samples"] == 3 and s["sm_mhz"] == 2055 and s["sm_max_mhz"] == 2070
     assert s["reasons"] == ["sw_power_cap"]
-    cs.lines = [_line(1500, 2070, hw="Active", swt="Active")]
+    cs.lines = [(1.0, _line(1500, 2070, hw="Active", swt="Active"))]
     assert bench.ClockSampler(0).summary()["samples"] == 0
     assert cs.summary()["reasons"] == ["hw_slowdown", "sw_thermal_slowdown"]
+
+
+def test_clock_summary_counts_the_timed_region():
+    # samples read 20 ms apart; the timed region covers host times 1.05 .. 1.095:
+    # the samples read inside it or within one period after its end (1.06, 1.08,
+    # 1.10) are the in-region ones, the rest belong to the padded window
+    cs = bench.ClockSampler(0)
+    cs.lines = [(1.0 + 0.02 * i, _line(2070 - i, 2070)) for i in range(10)]
+    cs.mark(1.05, 1.095)
+    s = cs.summary()
+    assert s["samples"] == 3 and s["samples_window"] == 10
+    assert s["sm_mhz"] == 2066          # median of 2067, 2066, 2065 (read at 1.06, 1.08, 1.10)
+
+
+def test_algorithmic_bytes_of_the_interpolation_launches():
+    N, B = 1 << 24, 32
+    assert bench.launch_bytes("interp_top", N, B) == (8 + 6 / 32) * N
+    assert bench.launch_bytes("interp_inv_fwd", N, B) == 8 * N
+    assert bench.launch_bytes("effdim_classes", N, B) is None
+    fams = {"interp_top": (32, 32 * 0.05)}          # 32 launches of 50 us
+    r = bench.roofline("interp_top", fams, N, B, 6000.0, "measured")
+    assert abs(r["achieved"] - (8 + 6 / 32) * N / 50e-6 / 1e9) < 1e-6
+    assert abs(r["frac"] - r["achieved"] / 6000.0) < 1e-12
 
 
 def test_whole_job_rate_counts_every_rank():
