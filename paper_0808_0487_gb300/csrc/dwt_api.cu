@@ -257,7 +257,10 @@ const PassPlan& pass_plan(dwt_plan_s* P, int elem_bytes) {
     return P->passes[idx];
 }
 
-static bool is_prime_small(int p) { return p == 2 || p == 3 || p == 5 || p == 7 || p == 11 || p == 13; }
+static bool is_prime_small(int p) {
+    return p == 2 || p == 3 || p == 5 || p == 7 || p == 11 || p == 13 || p == 17 || p == 19 || p == 23 ||
+           p == 29 || p == 31;
+}
 
 }  // namespace dwt
 
@@ -325,7 +328,7 @@ int dwt_plan_create(int p, int m, int s, const uint8_t* C, unsigned flags, void*
     }
     *out = nullptr;
     if (!is_prime_small(p)) {
-        set_error("p = %d: supported primes are 2, 3, 5, 7, 11, 13", p);
+        set_error("p = %d: supported primes are those below 32", p);
         return DWT_EINVAL;
     }
     if (m < 1 || s < 1 || s > 255 || !C) {

@@ -619,6 +619,11 @@ int build_coset_tables(dwt_plan_s* Pl, cudaStream_t st) {
         case 7: return small ? coset_tables_small<7>(Pl, st) : coset_tables_p<7>(Pl, st);
         case 11: return small ? coset_tables_small<11>(Pl, st) : coset_tables_p<11>(Pl, st);
         case 13: return small ? coset_tables_small<13>(Pl, st) : coset_tables_p<13>(Pl, st);
+        case 17: return small ? coset_tables_small<17>(Pl, st) : coset_tables_p<17>(Pl, st);
+        case 19: return small ? coset_tables_small<19>(Pl, st) : coset_tables_p<19>(Pl, st);
+        case 23: return small ? coset_tables_small<23>(Pl, st) : coset_tables_p<23>(Pl, st);
+        case 29: return small ? coset_tables_small<29>(Pl, st) : coset_tables_p<29>(Pl, st);
+        case 31: return small ? coset_tables_small<31>(Pl, st) : coset_tables_p<31>(Pl, st);
         default: return DWT_EUNSUPPORTED;
     }
 }
@@ -663,6 +668,11 @@ int run_h_to_k(dwt_plan_s* Pl, const uint32_t* H, uint32_t* k, long long cnt, cu
         case 7: return h_to_k_p<7>(Pl, H, k, cnt, st);
         case 11: return h_to_k_p<11>(Pl, H, k, cnt, st);
         case 13: return h_to_k_p<13>(Pl, H, k, cnt, st);
+        case 17: return h_to_k_p<17>(Pl, H, k, cnt, st);
+        case 19: return h_to_k_p<19>(Pl, H, k, cnt, st);
+        case 23: return h_to_k_p<23>(Pl, H, k, cnt, st);
+        case 29: return h_to_k_p<29>(Pl, H, k, cnt, st);
+        case 31: return h_to_k_p<31>(Pl, H, k, cnt, st);
         default: return DWT_EUNSUPPORTED;
     }
 }
@@ -678,6 +688,11 @@ int run_points(dwt_plan_s* Pl, uint32_t* Y, long long ldY, cudaStream_t st) {
             case 7: k_points<7><<<grid, 256, 0, st>>>(Pl->d_C, Pl->d_col, Pl->m, Pl->N, Y, ldY); break;
             case 11: k_points<11><<<grid, 256, 0, st>>>(Pl->d_C, Pl->d_col, Pl->m, Pl->N, Y, ldY); break;
             case 13: k_points<13><<<grid, 256, 0, st>>>(Pl->d_C, Pl->d_col, Pl->m, Pl->N, Y, ldY); break;
+            case 17: k_points<17><<<grid, 256, 0, st>>>(Pl->d_C, Pl->d_col, Pl->m, Pl->N, Y, ldY); break;
+            case 19: k_points<19><<<grid, 256, 0, st>>>(Pl->d_C, Pl->d_col, Pl->m, Pl->N, Y, ldY); break;
+            case 23: k_points<23><<<grid, 256, 0, st>>>(Pl->d_C, Pl->d_col, Pl->m, Pl->N, Y, ldY); break;
+            case 29: k_points<29><<<grid, 256, 0, st>>>(Pl->d_C, Pl->d_col, Pl->m, Pl->N, Y, ldY); break;
+            case 31: k_points<31><<<grid, 256, 0, st>>>(Pl->d_C, Pl->d_col, Pl->m, Pl->N, Y, ldY); break;
         }
     }
     DWT_CK_LAUNCH("k_points");
@@ -695,6 +710,11 @@ int run_k_to_h(dwt_plan_s* Pl, const uint32_t* k, uint32_t* H, long long cnt, cu
             case 7: k_k_to_h<7><<<g, 256, 0, st>>>(Pl->d_C, Pl->d_R, Pl->m, Pl->s, k, H, cnt); break;
             case 11: k_k_to_h<11><<<g, 256, 0, st>>>(Pl->d_C, Pl->d_R, Pl->m, Pl->s, k, H, cnt); break;
             case 13: k_k_to_h<13><<<g, 256, 0, st>>>(Pl->d_C, Pl->d_R, Pl->m, Pl->s, k, H, cnt); break;
+            case 17: k_k_to_h<17><<<g, 256, 0, st>>>(Pl->d_C, Pl->d_R, Pl->m, Pl->s, k, H, cnt); break;
+            case 19: k_k_to_h<19><<<g, 256, 0, st>>>(Pl->d_C, Pl->d_R, Pl->m, Pl->s, k, H, cnt); break;
+            case 23: k_k_to_h<23><<<g, 256, 0, st>>>(Pl->d_C, Pl->d_R, Pl->m, Pl->s, k, H, cnt); break;
+            case 29: k_k_to_h<29><<<g, 256, 0, st>>>(Pl->d_C, Pl->d_R, Pl->m, Pl->s, k, H, cnt); break;
+            case 31: k_k_to_h<31><<<g, 256, 0, st>>>(Pl->d_C, Pl->d_R, Pl->m, Pl->s, k, H, cnt); break;
         }
     }
     DWT_CK_LAUNCH("k_k_to_h");

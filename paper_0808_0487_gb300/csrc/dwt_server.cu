@@ -208,7 +208,8 @@ int dwt_server_submit(dwt_server_t S, const dwt_request* q, unsigned long long* 
         set_error("dwt_server_submit: bad arguments");
         return DWT_EINVAL;
     }
-    if (!(q->p == 2 || q->p == 3 || q->p == 5 || q->p == 7 || q->p == 11 || q->p == 13) || q->m < 1 || q->s < 1 ||
+    if (!(q->p == 2 || q->p == 3 || q->p == 5 || q->p == 7 || q->p == 11 || q->p == 13 || q->p == 17 ||
+          q->p == 19 || q->p == 23 || q->p == 29 || q->p == 31) || q->m < 1 || q->s < 1 ||
         q->s > 255 ||
         ipow_ll(q->p, q->m) > (1ll << 31) || !(q->threshold > 0.0 && q->threshold <= 1.0)) {
         set_error("dwt_server_submit: bad request shape");

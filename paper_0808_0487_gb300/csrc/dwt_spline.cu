@@ -272,12 +272,12 @@ __global__ void k_spline_sse_final(const double* __restrict__ part, long long nt
 // only on the position i of the first nonzero digit of the difference: the
 // first digit (of m) where x_j and the net point differ, or, when the top m
 // digits agree, the first nonzero digit of x_j below them (0 if none).  With
-// the base-p digits packed BP bits each (1, 2, 3, 4 bits for p = 2, 3, 5 / 7,
-// 11 / 13), the first differing digit is the highest set bit of an XOR.
+// the base-p digits packed BP bits each (1, 2, 3, 4, 5 bits for p = 2, 3, 5 / 7,
+// 11 / 13, 17 .. 31), the first differing digit is the highest set bit of an XOR.
 constexpr int kEvalQB = 128;   // points per block, one per thread
 constexpr int kEvalFB = 8;     // functions per block
 
-__host__ __device__ inline int eval_bits(int p) { return p == 2 ? 1 : p == 3 ? 2 : p <= 7 ? 3 : 4; }
+__host__ __device__ inline int eval_bits(int p) { return p == 2 ? 1 : p == 3 ? 2 : p <= 7 ? 3 : p <= 15 ? 4 : 5; }
 
 __device__ __forceinline__ unsigned long long pack_digits(uint32_t v, int p, int m, int bp) {
     unsigned long long r = 0;
@@ -320,7 +320,7 @@ __global__ void __launch_bounds__(kEvalQB) k_spline_eval(const unsigned long lon
     const int q = blockIdx.x * kEvalQB + t;
     const int f0 = blockIdx.y * kEvalFB;
     const int nf = min(kEvalFB, batch - f0);
-    constexpr int bp = P == 2 ? 1 : P == 3 ? 2 : P <= 7 ? 3 : 4;   // eval_bits(P)
+    constexpr int bp = P == 2 ? 1 : P == 3 ? 2 : P <= 7 ? 3 : P <= 15 ? 4 : 5;   // eval_bits(P)
     for (int e = t; e < s * M1; e += blockDim.x) T[e] = Tg[e];
     {
         uint32_t up = 1;
@@ -611,6 +611,11 @@ int run_spline_eval(dwt_plan_s* P, const void* c, int batch, long long ld, const
             case 7: kern = k_spline_eval<7>; break;
             case 11: kern = k_spline_eval<11>; break;
             case 13: kern = k_spline_eval<13>; break;
+            case 17: kern = k_spline_eval<17>; break;
+            case 19: kern = k_spline_eval<19>; break;
+            case 23: kern = k_spline_eval<23>; break;
+            case 29: kern = k_spline_eval<29>; break;
+            case 31: kern = k_spline_eval<31>; break;
             default: break;
         }
         if ((rc = smem_limit_max(kern))) { cleanup(); return rc; }

@@ -34,8 +34,8 @@ static bool aligned16(const void* p, long long ld, int elem) {
 // ---------------------------------------------------------------------------
 // element helpers
 struct Tw {
-    float c[16], s[16];   // cos, sin of 2 pi e / p, e < p <= 13
-    double cd[16], sd[16];
+    float c[32], s[32];   // cos, sin of 2 pi e / p, e < p <= 31
+    double cd[32], sd[32];
 };
 
 template <typename T> struct IsCplx : std::false_type {};
@@ -281,8 +281,14 @@ __device__ __forceinline__ void rgroup_k(int k, int mode, T* sm, const TI* gin, 
 // bytes; otherwise it writes shared memory and the tile leaves in element
 // order.  In place is safe: a tile is read in full before any of it is written
 // (a one-group pass reads and writes the same elements per thread).
+// Register cap: 96 x 512 threads fit the register file; a single digit of a
+// prime above 13 holds p complex elements and the p-point sums, so those
+// passes get 160 registers and at most 384 threads.
+template <int P> constexpr int pass_maxnreg() { return P > 13 ? 160 : 96; }
+template <int P> constexpr long long pass_max_threads() { return P > 13 ? 384 : 512; }
+
 template <int P, typename T, typename TI, int SGN, int KM>
-__global__ void __maxnreg__(96) k_pass(PassArgs a) {   // 96 x 512 threads fit the register file
+__global__ void __maxnreg__(pass_maxnreg<P>()) k_pass(PassArgs a) {
     extern __shared__ __align__(16) unsigned char smraw[];
     T* sm = reinterpret_cast<T*>(smraw);
     const long long fn = blockIdx.y;
@@ -551,7 +557,7 @@ __global__ void __launch_bounds__(32) k_effdim_finalize(const double* __restrict
 // host side
 static Tw make_tw(int p) {
     Tw t;
-    for (int e = 0; e < 16; ++e) {
+    for (int e = 0; e < 32; ++e) {
         double ang = e < p ? 2.0 * 3.14159265358979323846 * e / p : 0.0;
         t.cd[e] = cos(ang);
         t.sd[e] = sin(ang);
@@ -596,7 +602,7 @@ static int pass_threads(const PassGeom& g) {
     const int k0 = std::min(KM, g.b);
     long long tasks = ((long long)g.R / ipow_ll(P, k0)) << g.wlog;
     tasks = (tasks + 31) / 32 * 32;
-    return (int)std::min(512ll, std::max(32ll, tasks));
+    return (int)std::min(pass_max_threads<P>(), std::max(32ll, tasks));
 }
 
 template <int P, typename T, typename TI, int SGN, int KM>
@@ -692,6 +698,11 @@ int run_transform(dwt_plan_s* Pl, const void* in, void* out, int batch, long lon
         case 7: return transform_p<7>(Pl, in, out, batch, ld_in, ld_out, in_t, out_t, sgn, st);
         case 11: return transform_p<11>(Pl, in, out, batch, ld_in, ld_out, in_t, out_t, sgn, st);
         case 13: return transform_p<13>(Pl, in, out, batch, ld_in, ld_out, in_t, out_t, sgn, st);
+        case 17: return transform_p<17>(Pl, in, out, batch, ld_in, ld_out, in_t, out_t, sgn, st);
+        case 19: return transform_p<19>(Pl, in, out, batch, ld_in, ld_out, in_t, out_t, sgn, st);
+        case 23: return transform_p<23>(Pl, in, out, batch, ld_in, ld_out, in_t, out_t, sgn, st);
+        case 29: return transform_p<29>(Pl, in, out, batch, ld_in, ld_out, in_t, out_t, sgn, st);
+        case 31: return transform_p<31>(Pl, in, out, batch, ld_in, ld_out, in_t, out_t, sgn, st);
         default: set_error("unsupported p"); return DWT_EUNSUPPORTED;
     }
 }
@@ -844,6 +855,21 @@ int run_interpolate(dwt_plan_s* Pl, const void* f, void* c, void* coef, int batc
         case 13:
             return f_t == DWT_F32 ? interpolate_t<13, float2, float>(Pl, f, c, coef, batch, ld, weight, var, dim, thr, st)
                                   : interpolate_t<13, float2, float2>(Pl, f, c, coef, batch, ld, weight, var, dim, thr, st);
+        case 17:
+            return f_t == DWT_F32 ? interpolate_t<17, float2, float>(Pl, f, c, coef, batch, ld, weight, var, dim, thr, st)
+                                  : interpolate_t<17, float2, float2>(Pl, f, c, coef, batch, ld, weight, var, dim, thr, st);
+        case 19:
+            return f_t == DWT_F32 ? interpolate_t<19, float2, float>(Pl, f, c, coef, batch, ld, weight, var, dim, thr, st)
+                                  : interpolate_t<19, float2, float2>(Pl, f, c, coef, batch, ld, weight, var, dim, thr, st);
+        case 23:
+            return f_t == DWT_F32 ? interpolate_t<23, float2, float>(Pl, f, c, coef, batch, ld, weight, var, dim, thr, st)
+                                  : interpolate_t<23, float2, float2>(Pl, f, c, coef, batch, ld, weight, var, dim, thr, st);
+        case 29:
+            return f_t == DWT_F32 ? interpolate_t<29, float2, float>(Pl, f, c, coef, batch, ld, weight, var, dim, thr, st)
+                                  : interpolate_t<29, float2, float2>(Pl, f, c, coef, batch, ld, weight, var, dim, thr, st);
+        case 31:
+            return f_t == DWT_F32 ? interpolate_t<31, float2, float>(Pl, f, c, coef, batch, ld, weight, var, dim, thr, st)
+                                  : interpolate_t<31, float2, float2>(Pl, f, c, coef, batch, ld, weight, var, dim, thr, st);
         default: set_error("unsupported p"); return DWT_EUNSUPPORTED;
     }
 }

@@ -74,7 +74,8 @@ def test_tables_bit_exact(dwt, dev, orc, name, p, m, s):
 
 
 @pytest.mark.parametrize("p,m,s,idx", [(2, 3, 3, 1), (2, 4, 2, 2), (3, 2, 3, 1), (5, 1, 3, 2), (3, 3, 2, 3), (2, 2, 4, 1),
-                                       (11, 1, 3, 1), (13, 1, 2, 2)])
+                                       (11, 1, 3, 1), (13, 1, 2, 2), (17, 1, 3, 1), (19, 1, 2, 2), (23, 1, 2, 1),
+                                       (29, 1, 2, 3), (31, 1, 3, 2), (17, 2, 2, 4)])
 def test_dense_nets_vs_bruteforce(dwt, dev, orc, p, m, s, idx):
     C = S.dense_matrices(p, m, s, index=idx)
     st, kmap = orc.coset_leaders_bruteforce(p, m, C)
@@ -122,7 +123,8 @@ def test_rank_deficient_plan(dwt, dev):
 # Nets with N <= 2^16 build their tables in one CTA, larger ones with one launch
 # per (coordinate, digit); these sizes sit on both sides of that boundary, with
 # the largest s the small path takes.
-@pytest.mark.parametrize("p,m,s", [(2, 16, 64), (2, 17, 6), (3, 10, 24), (5, 7, 5), (7, 5, 40), (2, 10, 2)])
+@pytest.mark.parametrize("p,m,s", [(2, 16, 64), (2, 17, 6), (3, 10, 24), (5, 7, 5), (7, 5, 40), (2, 10, 2),
+                                   (17, 3, 6), (19, 4, 4), (23, 3, 5), (29, 3, 3), (31, 3, 4), (31, 4, 3)])
 def test_tables_small_large_boundary(dwt, dev, orc, p, m, s):
     C = S.small_net(p, m, s, index=m + s)
     N = p ** m

@@ -78,14 +78,18 @@ def test_interpolate_m20_batch(dwt, dev, orc):
 
 # p3_m11_s40: the top pass bins in one warp (40 coordinates: 82 classes);
 # p7_m6: a top pass of two digits with seven binning warps; p5_m7: lo 5 + top 2
-@pytest.mark.parametrize("which", ["p3_m13", "p11_m4", "p13_m4", "p3_m11_s40", "p7_m6", "p5_m7"])
+# p17_m4 .. p31_m3: primes above 13 (one digit per register group, the
+# p-point sums in conjugate pairs)
+@pytest.mark.parametrize("which", ["p3_m13", "p11_m4", "p13_m4", "p3_m11_s40", "p7_m6", "p5_m7", "p17_m4", "p19_m3",
+                                   "p23_m3", "p29_m3", "p31_m3"])
 def test_interpolate_p_odd(dwt, dev, orc, which):
     if which == "p3_m13":
         w = S.workload_p3_m13()
         p, m, s, C = w["p"], w["m"], w["s"], w["C"]
     else:
         p, m, s = {"p11_m4": (11, 4, 5), "p13_m4": (13, 4, 3), "p3_m11_s40": (3, 11, 40), "p7_m6": (7, 6, 5),
-                   "p5_m7": (5, 7, 4)}[which]
+                   "p5_m7": (5, 7, 4), "p17_m4": (17, 4, 4), "p19_m3": (19, 3, 5), "p23_m3": (23, 3, 3),
+                   "p29_m3": (29, 3, 4), "p31_m3": (31, 3, 6)}[which]
         C = S.small_net(p, m, s, index=90 + p)
     N = p ** m
     plan = dwt.dwt_plan_create(p, m, s, C)
@@ -106,7 +110,7 @@ def test_interpolate_p_odd(dwt, dev, orc, which):
     _check_dims(_np(dim)[0], dt, ds, vt, vs)
 
 
-@pytest.mark.parametrize("p,m,s", [(2, 12, 4), (5, 5, 3), (7, 4, 6), (11, 3, 4), (13, 3, 3)])
+@pytest.mark.parametrize("p,m,s", [(2, 12, 4), (5, 5, 3), (7, 4, 6), (11, 3, 4), (13, 3, 3), (17, 2, 4), (31, 2, 3)])
 def test_effdim_standalone(dwt, dev, orc, p, m, s):
     C = S.workload_pr1()["C"] if p == 2 else S.small_net(p, m, s, index=5)
     N = p ** m

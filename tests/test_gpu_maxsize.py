@@ -1,5 +1,5 @@
-"""The largest transforms a plan allows (p^m <= 2^31): p = 2, m = 31 and
-p = 3, m = 19, on characters of the digit group, whose transforms are known
+"""The largest transforms a plan allows (p^m <= 2^31): p = 2, m = 31,
+p = 3, m = 19 and p = 31, m = 6, on characters of the digit group, whose transforms are known
 exactly.  For p = 2 the input f_n = (-1)^(n . h*) keeps every intermediate of
 the butterflies at 0 or +-2^k, so the forward result is the unit vector at h*
 bit for bit, and the inverse gives f back bit for bit (Sec. 2.2: the Walsh
@@ -43,21 +43,21 @@ def test_p2_m31_walsh_function_exact(dwt, dev):
     assert bool(torch.equal(g, f))
 
 
-def test_p3_m19_character(dwt, dev):
-    p, m = 3, 19
+@pytest.mark.parametrize("p,m", [(3, 19), (31, 6)])
+def test_p_odd_max_character(dwt, dev, p, m):
     N = p ** m
     ld = (N + 3) // 4 * 4
     free, _ = torch.cuda.mem_get_info()
     if free < 3 * 8 * ld:
         pytest.skip("needs about 30 GB of device memory")
-    hd = S.integers(S.stream_seed(71, S.P_SAMPLE, 0), m, 0, p - 1)      # digits of h*
+    hd = S.integers(S.stream_seed(71, S.P_SAMPLE, p), m, 0, p - 1)      # digits of h*
     hd[0] = 1
     h = int(sum(int(d) * p ** i for i, d in enumerate(hd)))
     plan = dwt.dwt_plan_create(p, m, 1, S.small_net(p, m, 1, index=4), dwt.DWT_PLAN_TRANSFORM_ONLY)
-    # f_n = omega^(n . h*), omega = exp(2 pi i / 3): its forward transform (omega^(-n . h)) is the unit vector at h*
+    # f_n = omega^(n . h*), omega = exp(2 pi i / p): its forward transform (omega^(-n . h)) is the unit vector at h*
     f = torch.zeros(2 * ld, dtype=torch.float32, device=dev)
     fc = f.view(torch.complex64)
-    w = torch.exp(2j * np.pi * torch.arange(3, dtype=torch.float64, device=dev) / 3).to(torch.complex64)
+    w = torch.exp(2j * np.pi * torch.arange(p, dtype=torch.float64, device=dev) / p).to(torch.complex64)
     for a in range(0, N, CHUNK):
         n = torch.arange(a, min(N, a + CHUNK), dtype=torch.int64, device=dev)
         e = torch.zeros_like(n)

@@ -13,7 +13,8 @@ pytestmark = pytest.mark.gpu
 
 
 @pytest.mark.parametrize("p,m,s,alpha,B,pad", [(2, 10, 4, 2.0, 1, 0), (2, 14, 6, 2.0, 2, 4), (3, 7, 3, 2.0, 1, 0),
-                                              (5, 5, 4, 2.5, 2, 3), (2, 16, 8, 1.7, 3, 0), (7, 4, 3, 2.0, 1, 1)])
+                                              (5, 5, 4, 2.5, 2, 3), (2, 16, 8, 1.7, 3, 0), (7, 4, 3, 2.0, 1, 1),
+                                              (17, 3, 3, 2.0, 1, 1), (31, 2, 3, 2.5, 2, 0)])
 def test_spline_matches_oracle(dwt, dev, orc, p, m, s, alpha, B, pad):
     N = p ** m
     ld = N + pad
@@ -100,7 +101,8 @@ def test_spline_values_shifted(dwt, dev, orc, p, m, s, M, B):
 # two point blocks; (2, 12, 3, 12, 1, 129): M = m (no digits below the net's)
 @pytest.mark.parametrize("p,m,s,M,B,Q", [(2, 10, 4, 14, 2, 300), (2, 12, 3, 12, 1, 129), (3, 6, 3, 9, 1, 200),
                                          (5, 4, 3, 6, 2, 150), (7, 4, 2, 5, 1, 64), (13, 3, 2, 4, 1, 50),
-                                         (2, 8, 40, 20, 9, 130), (3, 5, 2, 20, 3, 257)])
+                                         (2, 8, 40, 20, 9, 130), (3, 5, 2, 20, 3, 257), (17, 3, 2, 5, 1, 70),
+                                         (31, 2, 3, 6, 2, 40)])
 def test_spline_eval_matches_oracle(dwt, dev, orc, p, m, s, M, B, Q):
     """Sf at arbitrary points against the oracle's direct sum, both from the
     oracle's coefficients (so only the evaluation is compared)."""

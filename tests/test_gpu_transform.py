@@ -145,7 +145,8 @@ def test_inverse_alone_vs_oracle(dwt, dev, orc, p, m, B, pad):
 
 # sizes chosen so that the pass decomposition has 1, 2 and 3 passes and ragged tiles
 @pytest.mark.parametrize("p,m", [(2, 1), (2, 14), (2, 15), (2, 25), (3, 1), (3, 9), (5, 3), (5, 10), (7, 2), (7, 8),
-                                 (11, 1), (11, 5), (13, 2), (13, 5)])
+                                 (11, 1), (11, 5), (13, 2), (13, 5), (17, 1), (17, 4), (19, 3), (23, 2), (23, 5),
+                                 (29, 3), (31, 1), (31, 4), (31, 5)])
 def test_sizes_and_primes(dwt, dev, orc, p, m):
     N = p ** m
     s = 2

@@ -20,7 +20,7 @@ def _nu(kv, p):
 
 
 TINY = [(2, 3, 3), (2, 4, 2), (3, 2, 3), (3, 2, 2), (2, 2, 4), (5, 1, 3), (3, 3, 2), (5, 2, 2), (2, 3, 4),
-        (11, 1, 3), (13, 1, 2), (7, 2, 2)]
+        (11, 1, 3), (13, 1, 2), (7, 2, 2), (17, 1, 3), (19, 1, 2), (23, 1, 2), (29, 1, 2), (31, 1, 3), (17, 2, 2)]
 
 
 @pytest.mark.parametrize("p,m,s", TINY)

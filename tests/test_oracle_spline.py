@@ -37,7 +37,7 @@ def _wal1(p, m, k, Y):
     return np.exp(2j * np.pi * e / p)
 
 
-@pytest.mark.parametrize("p,m,alpha", [(2, 5, 2.0), (2, 4, 1.5), (3, 3, 2.0), (5, 2, 3.0)])
+@pytest.mark.parametrize("p,m,alpha", [(2, 5, 2.0), (2, 4, 1.5), (3, 3, 2.0), (5, 2, 3.0), (17, 1, 2.0), (19, 2, 2.5)])
 def test_short_forms_equal_walsh_series(orc, p, m, alpha):
     N = p ** m
     for Y in range(1, N):

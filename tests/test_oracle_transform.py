@@ -15,7 +15,8 @@ def _data(p, m, idx=0, cplx=False):
     return v[:N] + 1j * v[N:] if cplx else v[:N]
 
 
-@pytest.mark.parametrize("p,m", [(2, 9), (3, 5), (5, 3), (2, 1), (3, 1), (11, 2), (13, 2), (11, 1)])
+@pytest.mark.parametrize("p,m", [(2, 9), (3, 5), (5, 3), (2, 1), (3, 1), (11, 2), (13, 2), (11, 1), (17, 2), (19, 1),
+                                 (23, 2), (29, 1), (31, 2)])
 def test_fwt_matches_direct_sum(orc, p, m):
     f = _data(p, m, cplx=p > 2)
     a = orc.fwt(p, m, f)
@@ -32,7 +33,8 @@ def test_p2_is_sylvester_hadamard(orc, m):
     assert np.abs(orc.fwt(2, m, f) - ref).max() < 1e-14
 
 
-@pytest.mark.parametrize("p,m", [(3, 6), (5, 4), (3, 2), (11, 3), (13, 2)])
+@pytest.mark.parametrize("p,m", [(3, 6), (5, 4), (3, 2), (11, 3), (13, 2), (17, 3), (19, 2), (23, 2), (29, 2),
+                                 (31, 3)])
 def test_p_odd_is_multidimensional_dft(orc, p, m):
     """F_p^{(x)m} with omega^{-nh}: numpy's forward FFT over an m-axis p x ... x p array."""
     f = _data(p, m, 2, cplx=True)
@@ -40,7 +42,7 @@ def test_p_odd_is_multidimensional_dft(orc, p, m):
     assert np.abs(orc.fwt(p, m, f) - ref).max() < 1e-14
 
 
-@pytest.mark.parametrize("p,m", [(2, 12), (3, 7), (5, 5), (11, 3), (13, 3)])
+@pytest.mark.parametrize("p,m", [(2, 12), (3, 7), (5, 5), (11, 3), (13, 3), (17, 3), (31, 3)])
 def test_inverse_is_identity_and_lemma(orc, p, m):
     """Lemma 3.1 / Alg. 2: c_n = sum_H c~(H) omega^{n.h}; forward then inverse is the identity."""
     f = _data(p, m, 3, cplx=p > 2)
@@ -50,7 +52,8 @@ def test_inverse_is_identity_and_lemma(orc, p, m):
     mm = min(m, 5)
     # inverse direct sum via the forward one: sum_H c(H) w^{+n.h} = N conj(DWT(conj c))
     ref = p ** mm * np.conj(orc.dwt_direct(p, mm, np.conj(ct)))
-    assert np.abs(orc.fiwt(p, mm, ct) - ref).max() < 1e-12
+    # N-term FP64 sums: the bound scales with the size of the result
+    assert np.abs(orc.fiwt(p, mm, ct) - ref).max() < 1e-13 * max(1.0, np.abs(ref).max())
 
 
 @pytest.mark.parametrize("p,m", [(2, 11), (3, 6), (5, 4)])
@@ -63,7 +66,7 @@ def test_parseval_and_linearity(orc, p, m):
     assert np.abs(orc.fwt(p, m, a * f + b * g) - (a * F + b * orc.fwt(p, m, g))).max() < 1e-14
 
 
-@pytest.mark.parametrize("p,m", [(2, 8), (3, 5), (5, 3)])
+@pytest.mark.parametrize("p,m", [(2, 8), (3, 5), (5, 3), (19, 2), (29, 2)])
 def test_shift_theorem(orc, p, m):
     """g_n = f_{n (+) v}  ->  g~(H) = omega^{v.h} f~(H)."""
     N = p ** m
