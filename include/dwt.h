@@ -173,6 +173,24 @@ int dwt_inverse(dwt_plan_t plan, const void *in, void *out, int batch, long long
                 dwt_dtype in_t, dwt_dtype out_t, dwt_algo algo, void *stream);
 
 /*
+ * dwt_forward_digits / dwt_inverse_digits: the stages of Algorithm 1
+ * (Algorithm 2) for the index digits d0 .. d0+nd-1 only, 0 <= d0,
+ * d0 + nd <= m.  The transform is the Kronecker product of one p-point DFT per
+ * digit (Sec. 2.2, the nested-sum form of eq. fdwt), and the stages of
+ * different digits commute, so the stages of any partition of the digits,
+ * applied in any order, compose to dwt_forward (dwt_inverse).  The forward
+ * applies the factor p^-nd (none for I32); the inverse none.  Layout, types
+ * and in-place use as dwt_forward / dwt_inverse (the generic passes only: no
+ * tensor-core form).  This is the building block of a transform split across
+ * processes: the digits below a cut on every process, one all-to-all exchange,
+ * then the digits above the cut.
+ */
+int dwt_forward_digits(dwt_plan_t plan, const void *in, void *out, int batch, long long ld_in, long long ld_out,
+                       dwt_dtype in_t, dwt_dtype out_t, int d0, int nd, void *stream);
+int dwt_inverse_digits(dwt_plan_t plan, const void *in, void *out, int batch, long long ld_in, long long ld_out,
+                       dwt_dtype in_t, dwt_dtype out_t, int d0, int nd, void *stream);
+
+/*
  * Spectral weighting and effective dimension in one call (Sec. 3.2-3.3, Sec. 4):
  *   f~ = forward(f);  g(H) = w(H) f~(H);  c = inverse(g);
  *   var[b][0][d] = sum_{H != 0, max supp k(H) <= d} |g(H)|^2,

@@ -77,6 +77,8 @@ _SIGS = {
     "dwt_index_to_wavenumber": (_I, [_VP, _VP, _VP, _LL, _VP]),
     "dwt_forward": (_I, [_VP, _VP, _VP, _I, _LL, _LL, _I, _I, _I, _VP]),
     "dwt_inverse": (_I, [_VP, _VP, _VP, _I, _LL, _LL, _I, _I, _I, _VP]),
+    "dwt_forward_digits": (_I, [_VP, _VP, _VP, _I, _LL, _LL, _I, _I, _I, _I, _VP]),
+    "dwt_inverse_digits": (_I, [_VP, _VP, _VP, _I, _LL, _LL, _I, _I, _I, _I, _VP]),
     "dwt_interpolate": (_I, [_VP, _VP, _VP, _VP, _I, _LL, _I, _I, _I, _VP, _VP, ctypes.c_double, _VP]),
     "dwt_interpolate_host": (_I, [_VP, _VP, _VP, _I, _LL, _I, _I, _VP, _VP, ctypes.c_double, _VP]),
     "dwt_selftest_bounded_wait": (_I, [_VP]),
@@ -270,6 +272,16 @@ def dwt_forward(plan, inp, out, batch, ld_in, ld_out, in_t, out_t, algo=DWT_ALGO
 def dwt_inverse(plan, inp, out, batch, ld_in, ld_out, in_t, out_t, algo=DWT_ALGO_AUTO, stream=None):
     return _check(lib().dwt_inverse(plan.handle, _ptr(inp), _ptr(out), batch, ld_in, ld_out, in_t, out_t, algo,
                                     _stream(stream)))
+
+
+def dwt_forward_digits(plan, inp, out, batch, ld_in, ld_out, in_t, out_t, d0, nd, stream=None):
+    return _check(lib().dwt_forward_digits(plan.handle, _ptr(inp), _ptr(out), batch, ld_in, ld_out, in_t, out_t, d0, nd,
+                                           _stream(stream)))
+
+
+def dwt_inverse_digits(plan, inp, out, batch, ld_in, ld_out, in_t, out_t, d0, nd, stream=None):
+    return _check(lib().dwt_inverse_digits(plan.handle, _ptr(inp), _ptr(out), batch, ld_in, ld_out, in_t, out_t, d0, nd,
+                                           _stream(stream)))
 
 
 def dwt_interpolate(plan, f, c, coef, batch, ld, f_t, weight, algo=DWT_ALGO_AUTO, var=None, dim=None,

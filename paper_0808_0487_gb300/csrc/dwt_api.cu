@@ -184,6 +184,32 @@ void pass_geometry(int p, int m, int elem, const int* b, int q, long long min_ti
     }
 }
 
+// Passes over the digits d0 .. d0+nd-1 only (the stages of a digit range):
+// from the lowest digit up, each pass as many digits as the tile allows (the
+// low-pass limit when the range starts at digit 0, the high-pass limit above).
+void pass_plan_range(int p, int m, int elem, int d0, int nd, long long min_tiles, PassPlan& pp) {
+    const PassLimits L = pass_limits(p, elem);
+    const long long N = dwt::ipow_ll(p, m);
+    pp.q = 0;
+    int d = d0;
+    while (d < d0 + nd && pp.q < 32) {
+        const int lim = d == 0 ? L.blo : L.bhi;
+        const int b = std::max(1, std::min(lim, d0 + nd - d));
+        PassGeom& g = pp.g[pp.q++];
+        g.d0 = d;
+        g.b = b;
+        g.S = dwt::ipow_ll(p, d);
+        g.R = (int)dwt::ipow_ll(p, b);
+        g.Wc = d > 0 ? pass_wc(g.R, g.S, L.cap, L.wc_max) : 1;
+        while (g.Wc > L.wc_min && ((g.S + g.Wc - 1) / g.Wc) * (N / (g.S * g.R)) < min_tiles) g.Wc /= 2;
+        g.wlog = 0;
+        while ((1 << g.wlog) < g.Wc) ++g.wlog;
+        g.nlo = (g.S + g.Wc - 1) / g.Wc;
+        g.ntile = g.nlo * (N / (g.S * g.R));
+        d += b;
+    }
+}
+
 // Candidate digit splits within the tile budget: with the fewest passes, every
 // low-pass length that leaves the rest to the high passes (shared evenly), and
 // one more pass shared evenly.  The heuristic's split is among them.
@@ -611,6 +637,30 @@ int dwt_forward(dwt_plan_t P, const void* in, void* out, int batch, long long ld
 int dwt_inverse(dwt_plan_t P, const void* in, void* out, int batch, long long ld_in, long long ld_out, dwt_dtype in_t,
                 dwt_dtype out_t, dwt_algo algo, void* stream) {
     return transform_common(P, in, out, batch, ld_in, ld_out, in_t, out_t, algo, stream, +1);
+}
+
+static int digits_common(dwt_plan_t P, const void* in, void* out, int batch, long long ld_in, long long ld_out,
+                         dwt_dtype in_t, dwt_dtype out_t, int d0, int nd, void* stream, int sgn) {
+    if (!P || batch < 0 || (batch > 0 && (!in || !out)) || ld_in < P->N || ld_out < P->N || d0 < 0 || nd < 1 ||
+        d0 + nd > P->m) {
+        set_error("digit stages: bad arguments (batch %d, ld_in %lld, ld_out %lld, digits %d + %d of %d)", batch, ld_in,
+                  ld_out, d0, nd, P ? P->m : 0);
+        return DWT_EINVAL;
+    }
+    int rc = check_transform_types(P, in_t, out_t, sgn);
+    if (rc) return rc;
+    if (batch == 0) return DWT_OK;
+    return run_transform_digits(P, in, out, batch, ld_in, ld_out, in_t, out_t, d0, nd, sgn, (cudaStream_t)stream);
+}
+
+int dwt_forward_digits(dwt_plan_t P, const void* in, void* out, int batch, long long ld_in, long long ld_out,
+                       dwt_dtype in_t, dwt_dtype out_t, int d0, int nd, void* stream) {
+    return digits_common(P, in, out, batch, ld_in, ld_out, in_t, out_t, d0, nd, stream, -1);
+}
+
+int dwt_inverse_digits(dwt_plan_t P, const void* in, void* out, int batch, long long ld_in, long long ld_out,
+                       dwt_dtype in_t, dwt_dtype out_t, int d0, int nd, void* stream) {
+    return digits_common(P, in, out, batch, ld_in, ld_out, in_t, out_t, d0, nd, stream, +1);
 }
 
 int dwt_interpolate(dwt_plan_t P, const void* f, void* c, void* coef, int batch, long long ld, dwt_dtype f_t,

@@ -117,6 +117,7 @@ void dfree(void* p, cudaStream_t st);
 const PassPlan& pass_plan(dwt_plan_s* P, int elem_bytes);
 void pass_geometry(int p, int m, int elem, const int* b, int q, long long min_tiles, int wc_div, PassPlan& pp);
 void pass_splits(int p, int m, int elem, std::vector<std::vector<int>>& out);
+void pass_plan_range(int p, int m, int elem, int d0, int nd, long long min_tiles, PassPlan& pp);
 int tune_passes(dwt_plan_s* P, long long min_tiles, cudaStream_t st);
 bool p2_fast_ok(int m);
 bool p2i_ok(int m, int s);
@@ -128,6 +129,8 @@ int p2i_interpolate(dwt_plan_s* Pl, const float* f, float* c, float* coef, int b
 // kernels' host entry points (implemented in the .cu files)
 int run_transform(dwt_plan_s* P, const void* in, void* out, int batch, long long ld_in, long long ld_out,
                   dwt_dtype in_t, dwt_dtype out_t, int sgn, cudaStream_t st);
+int run_transform_digits(dwt_plan_s* P, const void* in, void* out, int batch, long long ld_in, long long ld_out,
+                         dwt_dtype in_t, dwt_dtype out_t, int d0, int nd, int sgn, cudaStream_t st);
 int run_interpolate(dwt_plan_s* P, const void* f, void* c, void* coef, int batch, long long ld, dwt_dtype f_t,
                     dwt_weight weight, dwt_algo algo, double* var, int* dim, double thr, cudaStream_t st);
 // outputs of the effective-dimension step: cumulative truncation / superposition

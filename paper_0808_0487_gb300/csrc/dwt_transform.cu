@@ -630,9 +630,21 @@ static int launch_pass(const PassGeom& g, const PassArgs& a, int nf, const char*
 static const long long kL2Group = 48ll << 20;
 
 template <int P, typename T, typename TI, int SGN>
+static int transform_pp(dwt_plan_s* Pl, const PassPlan& pp, double scale_by_n, const void* in, void* out, int batch,
+                        long long ld_in, long long ld_out, cudaStream_t st);
+
+template <int P, typename T, typename TI, int SGN>
 static int transform_t(dwt_plan_s* Pl, const void* in, void* out, int batch, long long ld_in, long long ld_out,
                        cudaStream_t st) {
-    const PassPlan& pp = pass_plan(Pl, sizeof(T));
+    return transform_pp<P, T, TI, SGN>(Pl, pass_plan(Pl, sizeof(T)), 1.0 / (double)Pl->N, in, out, batch, ld_in,
+                                       ld_out, st);
+}
+
+// The passes of pp over a batch; a forward (SGN < 0, not int32) scales by
+// scale_by_n in its last pass.
+template <int P, typename T, typename TI, int SGN>
+static int transform_pp(dwt_plan_s* Pl, const PassPlan& pp, double scale_by_n, const void* in, void* out, int batch,
+                        long long ld_in, long long ld_out, cudaStream_t st) {
     const Tw tw = make_tw(P);
     const long long fbytes = Pl->N * (long long)sizeof(T);
     int G = (int)std::max(1ll, kL2Group / fbytes);
@@ -646,12 +658,12 @@ static int transform_t(dwt_plan_s* Pl, const void* in, void* out, int batch, lon
             if (t == 0) {
                 PassArgs a = pass_args(g, (const TI*)in + (long long)f0 * ld_in, (T*)out + (long long)f0 * ld_out,
                                        ld_in, ld_out, tw);
-                if (scale && pp.q == 1) { a.do_scale = 1; a.scale = 1.0 / (double)Pl->N; }
+                if (scale && pp.q == 1) { a.do_scale = 1; a.scale = scale_by_n; }
                 rc = launch_pass<P, T, TI, SGN>(g, a, nf, pass_family(t, pp.q), st);
             } else {
                 PassArgs a = pass_args(g, (const T*)out + (long long)f0 * ld_out, (T*)out + (long long)f0 * ld_out,
                                        ld_out, ld_out, tw);
-                if (scale && t == pp.q - 1) { a.do_scale = 1; a.scale = 1.0 / (double)Pl->N; }
+                if (scale && t == pp.q - 1) { a.do_scale = 1; a.scale = scale_by_n; }
                 rc = launch_pass<P, T, T, SGN>(g, a, nf, pass_family(t, pp.q), st);
             }
             if (rc) return rc;
@@ -683,6 +695,52 @@ static int transform_p(dwt_plan_s* Pl, const void* in, void* out, int batch, lon
             return in_t == DWT_F64 ? transform_t<P, double2, double, -1>(Pl, in, out, batch, ld_in, ld_out, st)
                                    : transform_t<P, double2, double2, -1>(Pl, in, out, batch, ld_in, ld_out, st);
         return transform_t<P, double2, double2, +1>(Pl, in, out, batch, ld_in, ld_out, st);
+    }
+}
+
+// Stages of the digits d0 .. d0+nd-1 (generic passes), forward scaled by p^-nd.
+template <int P>
+static int digits_p(dwt_plan_s* Pl, const void* in, void* out, int batch, long long ld_in, long long ld_out,
+                    dwt_dtype in_t, dwt_dtype out_t, int d0, int nd, int sgn, cudaStream_t st) {
+    auto go = [&](auto tag_t, auto tag_i, auto sgn_c) {
+        using T = decltype(tag_t);
+        using TI = decltype(tag_i);
+        constexpr int SG = decltype(sgn_c)::value;
+        PassPlan pp;
+        pass_plan_range(P, Pl->m, (int)sizeof(T), d0, nd, Pl->min_tiles, pp);
+        return transform_pp<P, T, TI, SG>(Pl, pp, 1.0 / (double)ipow_ll(P, nd), in, out, batch, ld_in, ld_out, st);
+    };
+    using M = std::integral_constant<int, -1>;
+    using Pp = std::integral_constant<int, +1>;
+    if constexpr (P == 2) {
+        if (in_t == DWT_F32) return sgn < 0 ? go(float(), float(), M()) : go(float(), float(), Pp());
+        if (in_t == DWT_F64) return sgn < 0 ? go(double(), double(), M()) : go(double(), double(), Pp());
+        return sgn < 0 ? go(int(), int(), M()) : go(int(), int(), Pp());
+    } else {
+        if (out_t == DWT_C64) {
+            if (sgn < 0) return in_t == DWT_F32 ? go(float2(), float(), M()) : go(float2(), float2(), M());
+            return go(float2(), float2(), Pp());
+        }
+        if (sgn < 0) return in_t == DWT_F64 ? go(double2(), double(), M()) : go(double2(), double2(), M());
+        return go(double2(), double2(), Pp());
+    }
+}
+
+int run_transform_digits(dwt_plan_s* Pl, const void* in, void* out, int batch, long long ld_in, long long ld_out,
+                         dwt_dtype in_t, dwt_dtype out_t, int d0, int nd, int sgn, cudaStream_t st) {
+    switch (Pl->p) {
+        case 2: return digits_p<2>(Pl, in, out, batch, ld_in, ld_out, in_t, out_t, d0, nd, sgn, st);
+        case 3: return digits_p<3>(Pl, in, out, batch, ld_in, ld_out, in_t, out_t, d0, nd, sgn, st);
+        case 5: return digits_p<5>(Pl, in, out, batch, ld_in, ld_out, in_t, out_t, d0, nd, sgn, st);
+        case 7: return digits_p<7>(Pl, in, out, batch, ld_in, ld_out, in_t, out_t, d0, nd, sgn, st);
+        case 11: return digits_p<11>(Pl, in, out, batch, ld_in, ld_out, in_t, out_t, d0, nd, sgn, st);
+        case 13: return digits_p<13>(Pl, in, out, batch, ld_in, ld_out, in_t, out_t, d0, nd, sgn, st);
+        case 17: return digits_p<17>(Pl, in, out, batch, ld_in, ld_out, in_t, out_t, d0, nd, sgn, st);
+        case 19: return digits_p<19>(Pl, in, out, batch, ld_in, ld_out, in_t, out_t, d0, nd, sgn, st);
+        case 23: return digits_p<23>(Pl, in, out, batch, ld_in, ld_out, in_t, out_t, d0, nd, sgn, st);
+        case 29: return digits_p<29>(Pl, in, out, batch, ld_in, ld_out, in_t, out_t, d0, nd, sgn, st);
+        case 31: return digits_p<31>(Pl, in, out, batch, ld_in, ld_out, in_t, out_t, d0, nd, sgn, st);
+        default: set_error("unsupported p"); return DWT_EUNSUPPORTED;
     }
 }
 
