@@ -93,6 +93,14 @@ __device__ __forceinline__ void tma_store_3d(const CUtensorMap* tm, int x, int y
         "r"(x), "r"(y), "r"(z), "r"(src), "l"(pol)
         : "memory");
 }
+__device__ __forceinline__ void bulk_load_1d(uint32_t dst, const void* src, uint32_t bytes, uint32_t bar,
+                                             uint64_t pol) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint [%0], [%1], %2, [%3], %4;" ::"r"(
+            dst),
+        "l"(src), "r"(bytes), "r"(bar), "l"(pol)
+        : "memory");
+}
 __device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
 __device__ __forceinline__ void bulk_wait_read() { asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory"); }
 __device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
@@ -128,6 +136,7 @@ struct TopArgs {
     double* part;           // [fn][class][tile]
     long long ntile;
     int nb;
+    int codes_off;          // compact tables: byte offset of the tile's 16-bit codes in shared memory
     int* err;               // host-mapped: a bounded wait expired
 };
 
@@ -162,8 +171,10 @@ __device__ __forceinline__ float2 weights_of_q(unsigned q0, unsigned q1, float t
     return make_float2(rcp_newton(x.x), rcp_newton(x.y));
 }
 
-constexpr int kTopLT = 14;
-constexpr int kTopNT = 256;
+constexpr int kRowLog = 14;                 // a row of the top pass: the 2^14 points of a low-pass tile
+constexpr int kTopLT = 13;                  // a top-pass tile: 2^13 points (2^B rows of 2^(13-B) columns)
+constexpr int kTopNT = 1 << (kTopLT - 6);   // 64 points per thread
+constexpr int kTopMinBlocks = kTopLT == 13 ? 4 : 2;
 
 template <int B> struct TopGeom {
     using G = HiGeom<kTopLT, B>;
@@ -171,11 +182,11 @@ template <int B> struct TopGeom {
     static constexpr int ROWS = 1 << B;
     static constexpr int BOXR = ROWS < 256 ? ROWS : 256;   // rows per tensor copy
     static constexpr int NBOX = ROWS / BOXR;
-    static constexpr int TILE_BYTES = ROWS * WC * 4;       // 64 KB
+    static constexpr int TILE_BYTES = ROWS * WC * 4;       // 2^kTopLT points
 };
 
 template <int B, bool COMPACT, bool HAS_COEF>
-__global__ void __launch_bounds__(kTopNT, 2) k2i_top(const __grid_constant__ CUtensorMap tm, TopArgs a) {
+__global__ void __launch_bounds__(kTopNT, kTopMinBlocks) k2i_top(const __grid_constant__ CUtensorMap tm, TopArgs a) {
     static_assert(B >= 6 && B <= 10, "top pass of 6 .. 10 digits");
     using G = HiGeom<kTopLT, B>;
     using TG = TopGeom<B>;
@@ -191,49 +202,49 @@ __global__ void __launch_bounds__(kTopNT, 2) k2i_top(const __grid_constant__ CUt
     const long long tile = blockIdx.x;
     const int x0 = (int)(tile * WC);
     const uint64_t keep = policy_evict_last();
+    const long long to = tile << kTopLT;
+    // compact tables: the tile's 16-bit codes (32 KB, contiguous) come into
+    // shared memory with the data tile; full tables are read into registers
+    const uint4* qsm = COMPACT ? reinterpret_cast<const uint4*>(reinterpret_cast<const unsigned char*>(sm) + a.codes_off)
+                               : nullptr;
     if (t == 0) {
         mbar_init1(smem_u32(&bar));
-        mbar_expect_tx(smem_u32(&bar), TG::TILE_BYTES);
+        mbar_expect_tx(smem_u32(&bar), TG::TILE_BYTES + (COMPACT ? (2u << kTopLT) : 0u));
 #pragma unroll
         for (int b = 0; b < TG::NBOX; ++b)
             tma_load_3d(smem_u32(sm + b * TG::BOXR * WC), &tm, x0, b * TG::BOXR, fn, smem_u32(&bar), keep);
-        // this tile's table range (contiguous) from HBM into L2, read after the forward stages
-        const long long o = tile << kTopLT;
-        if (COMPACT) {
-            prefetch_l2(a.tq + o, 2u << kTopLT);
+        if constexpr (COMPACT) {
+            bulk_load_1d(smem_u32(qsm), a.tq + to, 2u << kTopLT, smem_u32(&bar), policy_evict_first());
         } else {
-            prefetch_l2(a.tw + o, 4u << kTopLT);
-            prefetch_l2(a.tks + o, 1u << kTopLT);
+            // this tile's table range (contiguous) from HBM into L2, read after the forward stages
+            prefetch_l2(a.tw + to, 4u << kTopLT);
+            prefetch_l2(a.tks + to, 1u << kTopLT);
         }
-        prefetch_l2(a.tkt + o, 1u << kTopLT);
+    }
+    // the max-support bytes: 16 per thread and table group, all four groups
+    // requested now (compact); full tables: the first group now, then one ahead
+    const uint4* kg = reinterpret_cast<const uint4*>(a.tkt + to) + t;
+    const uint4* qg = reinterpret_cast<const uint4*>(COMPACT ? (const void*)(a.tq + to) : (const void*)(a.tw + to)) + t;
+    const uint4* sg = reinterpret_cast<const uint4*>(a.tks + to) + t;
+    constexpr int NK = COMPACT ? 4 : 2;
+    uint4 tk[NK], tqv[2][5];
+    auto fetch = [&](int g, int slot) {   // full tables
+        tk[slot] = ld_stream16(kg + g * NT);
+#pragma unroll
+        for (int i = 0; i < 4; ++i) tqv[slot][i] = ld_stream16(qg + (4 * g + i) * NT);
+        tqv[slot][4] = ld_stream16(sg + g * NT);
+    };
+    if constexpr (COMPACT) {
+#pragma unroll
+        for (int g = 0; g < 4; ++g) tk[g] = ld_stream16(kg + g * NT);
+    } else {
+        fetch(0, 0);
     }
     __syncthreads();   // barrier initialised before anyone waits on it
     if (!__syncthreads_and(mbar_wait_bounded(smem_u32(&bar), 0) ? 1 : 0)) {
         if (t == 0) atomicExch(a.err, 1);
         return;
     }
-    // table groups of 16 elements (compact: max-support bytes and two uint4 of
-    // 16-bit codes; full: weights, support sizes and max-support bytes): the
-    // first two are requested now, so that they arrive during the forward stages
-    const long long to = tile << kTopLT;
-    const uint4* kg = reinterpret_cast<const uint4*>(a.tkt + to) + t;
-    const uint4* qg = reinterpret_cast<const uint4*>(COMPACT ? (const void*)(a.tq + to) : (const void*)(a.tw + to)) + t;
-    const uint4* sg = reinterpret_cast<const uint4*>(a.tks + to) + t;
-    constexpr int NQ = COMPACT ? 2 : 5;   // uint4 per group besides the max-support bytes
-    uint4 tk[2], tqv[2][NQ];
-    auto fetch = [&](int g, int slot) {
-        tk[slot] = ld_stream16(kg + g * NT);
-        if constexpr (COMPACT) {
-            tqv[slot][0] = ld_stream16(qg + (2 * g) * NT);
-            tqv[slot][1] = ld_stream16(qg + (2 * g + 1) * NT);
-        } else {
-#pragma unroll
-            for (int i = 0; i < 4; ++i) tqv[slot][i] = ld_stream16(qg + (4 * g + i) * NT);
-            tqv[slot][4] = ld_stream16(sg + g * NT);
-        }
-    };
-    fetch(0, 0);
-    if constexpr (COMPACT) fetch(1, 1);
     V v[32];
     // layout A from the dense tile: float4 at 4(t + NT q)
 #pragma unroll
@@ -303,24 +314,22 @@ __global__ void __launch_bounds__(kTopNT, 2) k2i_top(const __grid_constant__ CUt
 #pragma unroll
                 for (int e = 0; e < 2; ++e) {
                     const int el = G::fused_e(t, j + e);
-                    coef[(long long)(el >> G::CB) * (1ll << kTopLT) + x0 + (el & (WC - 1))] = comp(vv, e);
+                    coef[(long long)(el >> G::CB) * (1ll << kRowLog) + x0 + (el & (WC - 1))] = comp(vv, e);
                 }
             }
             bin2(bt, bs, kt0, ks0, kt1, ks1, (j == 0 && has0) ? 0.f : sq.x, sq.y);
         }
     };
-    // compact tables: two groups in flight (group g + 2 requested once g is
-    // consumed); full tables: the next group requested before this one is used
 #pragma unroll
     for (int g = 0; g < 4; ++g) {
-        if constexpr (!COMPACT) {
-            if (g + 1 < 4) fetch(g + 1, (g + 1) & 1);
-        }
-        body(g, tk[g & 1], tqv[g & 1]);
-        asm volatile("" ::: "memory");
         if constexpr (COMPACT) {
-            if (g + 2 < 4) fetch(g + 2, g & 1);
+            const uint4 q2[2] = {qsm[(2 * g) * NT + t], qsm[(2 * g + 1) * NT + t]};
+            body(g, tk[g], q2);
+        } else {
+            if (g + 1 < 4) fetch(g + 1, (g + 1) & 1);
+            body(g, tk[g & 1], tqv[g & 1]);
         }
+        asm volatile("" ::: "memory");
     }
     __syncthreads();
     // per-tile class sums in a fixed order (as the p = 2 high pass): lane l of
@@ -394,7 +403,7 @@ __global__ void __launch_bounds__(kTopNT) k2i_tables(const float* __restrict__ W
     const long long to = tile << kTopLT;
     for (int j = 0; j < 64; ++j) {
         const int el = G::fused_e(t, j);
-        const long long H = (long long)(el >> G::CB) * (1ll << kTopLT) + tile * WC + (el & (WC - 1));
+        const long long H = (long long)(el >> G::CB) * (1ll << kRowLog) + tile * WC + (el & (WC - 1));
         const float w = W[H];
         const int kt = cls[2 * H], ks = cls[2 * H + 1];
         tkt[to + 16 * ((j >> 4) * NT + t) + (j & 15)] = (uint8_t)kt;
@@ -483,8 +492,8 @@ static int top_tensor_map(CUtensorMap* tm, float* base, long long ld, int nf) {
     using TG = TopGeom<B>;
     int rc = tensor_map_fn();
     if (rc) return rc;
-    cuuint64_t dims[3] = {(cuuint64_t)1 << kTopLT, (cuuint64_t)TG::ROWS, (cuuint64_t)nf};
-    cuuint64_t strides[2] = {((cuuint64_t)1 << kTopLT) * 4, (cuuint64_t)ld * 4};
+    cuuint64_t dims[3] = {(cuuint64_t)1 << kRowLog, (cuuint64_t)TG::ROWS, (cuuint64_t)nf};
+    cuuint64_t strides[2] = {((cuuint64_t)1 << kRowLog) * 4, (cuuint64_t)ld * 4};
     cuuint32_t box[3] = {(cuuint32_t)TG::WC, (cuuint32_t)TG::BOXR, 1};
     cuuint32_t estr[3] = {1, 1, 1};
     CUresult r = g_encode(tm, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, base, dims, strides, box, estr,
@@ -502,15 +511,20 @@ static size_t top_bins_bytes(int s) {
     return (nw * nb2 * 32 + nw * nb2) * 4;
 }
 
+// shared memory of the top pass: the mbarrier, the tile / exchange buffer /
+// class bins (aliased; 128-byte aligned), then the compact tables' codes
+static size_t top_region(int s, size_t x) { return (std::max(x, top_bins_bytes(s)) + 127) & ~(size_t)127; }
+static constexpr size_t kCodesBytes = (size_t)2 << kTopLT;
+
 template <int B>
-static size_t top_smem(int s) {
+static size_t top_smem(int s, bool compact) {
     const size_t x = (size_t)HiGeom<kTopLT, B>::SMEM_ELEMS * 4;
-    return ((std::max(x, top_bins_bytes(s)) + 15) & ~(size_t)15) + 16 + 128;   // + mbarrier, tile alignment
+    return 16 + 128 + top_region(s, x) + (compact ? kCodesBytes : 0);
 }
 
 bool p2i_ok(int m, int s) {
     if (m < 20 || m > 24) return false;
-    return top_bins_bytes(s) + 16 + 128 <= 227 * 1024;
+    return 16 + 128 + top_region(s, (size_t)HiGeom<kTopLT, 10>::SMEM_ELEMS * 4) + kCodesBytes <= 227 * 1024;
 }
 
 template <int B, bool COMPACT, bool HAS_COEF>
@@ -521,7 +535,9 @@ static int launch_top_one(const CUtensorMap& tm, const TopArgs& a, int nf, int s
     dim3 grid((unsigned)a.ntile, (unsigned)nf);
     {
         LaunchScope ls("interp_top", st);
-        k<<<grid, kTopNT, top_smem<B>(s), st>>>(tm, a);
+        TopArgs a2 = a;
+        a2.codes_off = (int)top_region(s, (size_t)HiGeom<kTopLT, B>::SMEM_ELEMS * 4);
+        k<<<grid, kTopNT, top_smem<B>(s, COMPACT), st>>>(tm, a2);
     }
     DWT_CK_LAUNCH("k2i_top");
     return DWT_OK;
@@ -577,7 +593,7 @@ static void launch_tables_b(dwt_plan_s* Pl, bool compact, int* flag, cudaStream_
 }
 
 static int launch_tables(dwt_plan_s* Pl, bool compact, int* flag, cudaStream_t st) {
-    switch (Pl->m - kTopLT) {
+    switch (Pl->m - kRowLog) {
         case 6: launch_tables_b<6>(Pl, compact, flag, st); break;
         case 7: launch_tables_b<7>(Pl, compact, flag, st); break;
         case 8: launch_tables_b<8>(Pl, compact, flag, st); break;
@@ -659,7 +675,7 @@ int p2i_interpolate(dwt_plan_s* Pl, const float* f, float* c, float* coef, int b
                     bool tc, double** part_out, long long* ntile_out, cudaStream_t st) {
     const int m = Pl->m;
     const long long N = Pl->N;
-    const int B = m - kTopLT;
+    const int B = m - kRowLog;
     const int nb = Pl->s + 1, nb2 = 2 * nb;
     if (!p2i_ok(m, Pl->s) || !Pl->d_tkt || !Pl->d_err) {
         set_error("shape outside the fused p = 2 top pass");
