@@ -121,6 +121,10 @@ void pass_plan_range(int p, int m, int elem, int d0, int nd, long long min_tiles
 int tune_passes(dwt_plan_s* P, long long min_tiles, cudaStream_t st);
 bool p2_fast_ok(int m);
 bool p2i_ok(int m, int s);
+bool p2i_transform_ok(int m);
+int p2i_transform(dwt_plan_s* Pl, const float* in, float* out, int batch, long long ld_in, long long ld_out, int sgn,
+                  cudaStream_t st);
+int p2i_hi_only(dwt_plan_s* Pl, float* data, int batch, long long ld, int sgn, cudaStream_t st);
 int p2i_build_tables(dwt_plan_s* P, cudaStream_t st);
 int p2i_table_bytes_per_point(dwt_plan_s* P);
 int p2i_interpolate(dwt_plan_s* Pl, const float* f, float* c, float* coef, int batch, long long ld, bool weighted,

@@ -395,6 +395,7 @@ static int p2_transform_t(dwt_plan_s* Pl, const T* in, T* out, int batch, long l
 
 // only the FP32 high pass (digits L .. m-1) over data in place; forward scales by 2^-m
 int p2_hi_only(dwt_plan_s* Pl, float* data, int batch, long long ld, int L, int sgn, cudaStream_t st) {
+    if (L == 14 && p2i_transform_ok(Pl->m)) return p2i_hi_only(Pl, data, batch, ld, sgn, st);
     const int B = Pl->m - L;
     HiArgs a{};
     a.in = data;
@@ -419,6 +420,8 @@ int p2_hi_only(dwt_plan_s* Pl, float* data, int batch, long long ld, int L, int 
 
 int p2_transform(dwt_plan_s* Pl, const void* in, void* out, int batch, long long ld_in, long long ld_out,
                  dwt_dtype t, int sgn, cudaStream_t st) {
+    if (t == DWT_F32 && p2i_transform_ok(Pl->m))
+        return p2i_transform(Pl, (const float*)in, (float*)out, batch, ld_in, ld_out, sgn, st);
     if (t == DWT_F32)
         return p2_transform_t<float>(Pl, (const float*)in, (float*)out, batch, ld_in, ld_out, sgn, st);
     return p2_transform_t<int>(Pl, (const int*)in, (int*)out, batch, ld_in, ld_out, sgn, st);

@@ -176,8 +176,8 @@ constexpr int kTopLT = 13;                  // a top-pass tile: 2^13 points (2^B
 constexpr int kTopNT = 1 << (kTopLT - 6);   // 64 points per thread
 constexpr int kTopMinBlocks = kTopLT == 13 ? 4 : 2;
 
-template <int B> struct TopGeom {
-    using G = HiGeom<kTopLT, B>;
+template <int B, int LT = kTopLT> struct TopGeom {
+    using G = HiGeom<LT, B>;
     static constexpr int WC = 1 << G::CB;                  // columns per tile
     static constexpr int ROWS = 1 << B;
     static constexpr int BOXR = ROWS < 256 ? ROWS : 256;   // rows per tensor copy
@@ -386,6 +386,78 @@ __global__ void __launch_bounds__(kTopNT, kTopMinBlocks) k2i_top(const __grid_co
 }
 
 // ---------------------------------------------------------------------------
+// Plain high pass: the stages of the B digits above the 14 low ones (forward
+// or inverse: for p = 2 the same butterflies), scaled by `scale` when asked
+// (the forward's 2^-m), with the tile moved by the tensor-memory-access unit as
+// in the top pass; in place.
+constexpr int kHiLT = 14;                  // plain high pass: 2^14-point tiles (rows of 2^(14-B) columns)
+constexpr int kHiNT = 1 << (kHiLT - 6);
+
+template <int B>
+__global__ void __launch_bounds__(kHiNT, 3) k2i_hi(const __grid_constant__ CUtensorMap tm, float scale, int do_scale,
+                                                   int* err) {
+    using G = HiGeom<kHiLT, B>;
+    using TG = TopGeom<B, kHiLT>;
+    using V = float2;
+    constexpr int NT = kHiNT, P1 = G::P1, WC = TG::WC;
+    extern __shared__ __align__(16) unsigned char smraw[];
+    uint64_t& bar = *reinterpret_cast<uint64_t*>(smraw);
+    float* sm = reinterpret_cast<float*>((reinterpret_cast<uintptr_t>(smraw) + 16 + 127) & ~(uintptr_t)127);
+    const int t = threadIdx.x;
+    const int fn = blockIdx.y;
+    const int x0 = (int)((long long)blockIdx.x * WC);
+    const uint64_t first = policy_evict_first();
+    if (t == 0) {
+        mbar_init1(smem_u32(&bar));
+        mbar_expect_tx(smem_u32(&bar), TG::TILE_BYTES);
+#pragma unroll
+        for (int b = 0; b < TG::NBOX; ++b)
+            tma_load_3d(smem_u32(sm + b * TG::BOXR * WC), &tm, x0, b * TG::BOXR, fn, smem_u32(&bar), first);
+    }
+    __syncthreads();
+    if (!__syncthreads_and(mbar_wait_bounded(smem_u32(&bar), 0) ? 1 : 0)) {
+        if (t == 0) atomicExch(err, 1);
+        return;
+    }
+    V v[32];
+#pragma unroll
+    for (int q = 0; q < 16; ++q) ld16(sm + 4 * (t + NT * q), v + 2 * q);
+    bfly_range<2, 6>(v);
+    __syncthreads();
+    float* pa = sm + 4 * t;
+#pragma unroll
+    for (int q = 0; q < 16; ++q) st16(pa + q * 4 * NT + G::PADC * (q >> G::QSH), v + 2 * q);
+    __syncthreads();
+    const int ep = (t & ((1 << P1) - 1)) | ((t >> P1) << (P1 + 6));
+    float* pp = sm + ep + G::PADC * (ep >> G::PADSH);
+#pragma unroll
+    for (int j = 0; j < 64; ++j) comp(v[j >> 1], j & 1) = pp[j << P1];
+    bfly_range<G::RLO, G::RHI>(v);
+    if (do_scale) {
+#pragma unroll
+        for (int k = 0; k < 32; ++k) v[k] = pmul(v[k], scale);
+    }
+    __syncthreads();
+#pragma unroll
+    for (int j = 0; j < 64; ++j) pp[j << P1] = comp(v[j >> 1], j & 1);
+    __syncthreads();
+#pragma unroll
+    for (int q = 0; q < 16; ++q) ld16(pa + q * 4 * NT + G::PADC * (q >> G::QSH), v + 2 * q);
+    __syncthreads();
+#pragma unroll
+    for (int q = 0; q < 16; ++q) st16(sm + 4 * (t + NT * q), v + 2 * q);
+    fence_async_smem();
+    __syncthreads();
+    if (t == 0) {
+#pragma unroll
+        for (int b = 0; b < TG::NBOX; ++b)
+            tma_store_3d(&tm, x0, b * TG::BOXR, fn, smem_u32(sm + b * TG::BOXR * WC), first);
+        bulk_commit();
+        bulk_wait_read();
+    }
+}
+
+// ---------------------------------------------------------------------------
 // plan-time tables in the top pass's order: register j of thread t of tile T
 // holds element e = fused_e(t, j) of the tile (row e >> CB, column e & (WC-1)),
 // coefficient index H = row 2^14 + T WC + column.  16-bit codes: 8 per thread
@@ -487,9 +559,9 @@ static int tensor_map_fn() {
 }
 
 // [nf][2^B rows][2^14] FP32 view of a group of functions (row pitch 2^14, function pitch ld), box WC x BOXR
-template <int B>
+template <int B, int LT = kTopLT>
 static int top_tensor_map(CUtensorMap* tm, float* base, long long ld, int nf) {
-    using TG = TopGeom<B>;
+    using TG = TopGeom<B, LT>;
     int rc = tensor_map_fn();
     if (rc) return rc;
     cuuint64_t dims[3] = {(cuuint64_t)1 << kRowLog, (cuuint64_t)TG::ROWS, (cuuint64_t)nf};
@@ -582,6 +654,89 @@ static int launch_lo_i(const LoJobI& a, const LoJobI* b, long long N, const char
     return DWT_OK;
 }
 
+static int status_word(int** host, int** dev);
+static const long long kL2GroupP2i = 48ll << 20;   // functions per L2-resident group
+
+template <int B>
+static int launch_hi_b(float* base, long long ld, int nf, float scale, int do_scale, int* err, cudaStream_t st) {
+    CUtensorMap tm;
+    int rc = top_tensor_map<B, kHiLT>(&tm, base, ld, nf);
+    if (rc) return rc;
+    auto k = k2i_hi<B>;
+    if ((rc = smem_limit_max(k))) return rc;
+    const size_t smem = 16 + 128 + (size_t)HiGeom<kHiLT, B>::SMEM_ELEMS * 4;
+    dim3 grid((unsigned)((1u << kRowLog) / TopGeom<B, kHiLT>::WC), (unsigned)nf);
+    {
+        LaunchScope ls(do_scale ? "p2_hi_fwd" : "p2_hi_inv", st);
+        k<<<grid, kHiNT, smem, st>>>(tm, scale, do_scale, err);
+    }
+    DWT_CK_LAUNCH("k2i_hi");
+    return DWT_OK;
+}
+
+static int launch_hi_i(int B, float* base, long long ld, int nf, float scale, int do_scale, int* err,
+                       cudaStream_t st) {
+    switch (B) {
+        case 6: return launch_hi_b<6>(base, ld, nf, scale, do_scale, err, st);
+        case 7: return launch_hi_b<7>(base, ld, nf, scale, do_scale, err, st);
+        case 8: return launch_hi_b<8>(base, ld, nf, scale, do_scale, err, st);
+        case 9: return launch_hi_b<9>(base, ld, nf, scale, do_scale, err, st);
+        case 10: return launch_hi_b<10>(base, ld, nf, scale, do_scale, err, st);
+        default: set_error("high-pass digits"); return DWT_EUNSUPPORTED;
+    }
+}
+
+bool p2i_transform_ok(int m) { return m >= 20 && m <= 24; }
+
+// The high digits 14 .. m-1 of FP32 data in place (after a low pass over the
+// 14 low digits); the forward (sgn < 0) scales by 2^-m.
+int p2i_hi_only(dwt_plan_s* Pl, float* data, int batch, long long ld, int sgn, cudaStream_t st) {
+    int* err = nullptr;
+    int* herr = nullptr;
+    int rc = status_word(&herr, &err);
+    if (rc) return rc;
+    if (*(volatile int*)herr) {
+        *herr = 0;
+        set_error("an earlier call gave up a bounded wait in a p = 2 tensor-copied pass");
+        return DWT_ETIMEOUT;
+    }
+    const float sc = (float)(1.0 / (double)Pl->N);
+    for (int f0 = 0; f0 < batch; f0 += 65535) {
+        const int nf = std::min(65535, batch - f0);
+        rc = launch_hi_i(Pl->m - kRowLog, data + (long long)f0 * ld, ld, nf, sc, sgn < 0 ? 1 : 0, err, st);
+        if (rc) return rc;
+    }
+    return DWT_OK;
+}
+
+// dwt_forward / dwt_inverse for p = 2, FP32, 20 <= m <= 24: per L2-sized group
+// of functions the low pass (in -> out, the intermediate kept in L2) and the
+// high pass in place.
+int p2i_transform(dwt_plan_s* Pl, const float* in, float* out, int batch, long long ld_in, long long ld_out, int sgn,
+                  cudaStream_t st) {
+    const long long N = Pl->N;
+    int G = (int)std::max(1ll, kL2GroupP2i / (N * 4));
+    G = std::min(G, 65535);
+    for (int f0 = 0; f0 < batch; f0 += G) {
+        const int nf = std::min(G, batch - f0);
+        if (ld_in != ld_out) {
+            // the low pass takes one ld for both sides: run it per function
+            for (int b = 0; b < nf; ++b) {
+                LoJobI a{in + (long long)(f0 + b) * ld_in, out + (long long)(f0 + b) * ld_out, ld_out, 1, 0};
+                int rc = launch_lo_i(a, nullptr, N, sgn < 0 ? "p2_lo_fwd" : "p2_lo_inv", st);
+                if (rc) return rc;
+            }
+        } else {
+            LoJobI a{in + (long long)f0 * ld_in, out + (long long)f0 * ld_out, ld_out, nf, 0};
+            int rc = launch_lo_i(a, nullptr, N, sgn < 0 ? "p2_lo_fwd" : "p2_lo_inv", st);
+            if (rc) return rc;
+        }
+        int rc = p2i_hi_only(Pl, out + (long long)f0 * ld_out, nf, ld_out, sgn, st);
+        if (rc) return rc;
+    }
+    return DWT_OK;
+}
+
 template <int B>
 static void launch_tables_b(dwt_plan_s* Pl, bool compact, int* flag, cudaStream_t st) {
     const unsigned grid = (unsigned)(Pl->N >> kTopLT);
@@ -665,7 +820,6 @@ int p2i_table_bytes_per_point(dwt_plan_s* Pl) {
     return 0;
 }
 
-static const long long kL2GroupP2i = 48ll << 20;
 
 // dwt_interpolate for p = 2, FP32, 20 <= m <= 24: forward low pass (f -> c),
 // fused top pass (c -> c), and the inverse low pass of each group of functions
