@@ -20,10 +20,12 @@
 //
 // Tables are kept in the coordinates of their own coordinate's basis (T^U_j);
 // consecutive coordinates are linked by the F_2-linear map U_j -> U_{j+1}.
-// Linear maps are applied as four 256-entry XOR tables (one per byte).  The
-// tree levels below 2^13 labels live in shared memory per tile; the levels
-// above come from one small CTA.  Nets whose row sets are dependent, and
-// m > 27, use the per-digit programme.
+// Linear maps are applied as four 256-entry XOR tables (one per byte).  Nets
+// of up to 2^13 labels run in one CTA; larger ones in tiles of 2^12 labels
+// (the tiled form below).  Nets whose row sets are dependent, and m > 27, use
+// the per-digit programme.
+#include <stdlib.h>
+
 #include <algorithm>
 #include <vector>
 
@@ -34,7 +36,6 @@ namespace dwt {
 namespace {
 
 constexpr int kLB = 13;          // tile: 2^13 labels (levels 0 .. 13 in shared memory)
-constexpr int kThreads = 512;
 constexpr uint8_t kInfB = 255;
 
 struct Map4 {
@@ -58,181 +59,376 @@ __device__ __forceinline__ void load_map(uint32_t (*sm)[256], const Map4* g) {
     for (int i = threadIdx.x; i < 4 * 256; i += blockDim.x) sm[i >> 8][i & 255] = g->t[i >> 8][i & 255];
 }
 
-// Leaves T'[U] = Tprev[Q(U)] (or, with no Tprev, the start T_{s+1}: 0 at U = 0,
-// infinite elsewhere) of one 2^LB tile and the tile's tree levels 0 .. LB,
-// written to the global level array.
-__global__ void __launch_bounds__(kThreads) k_tree_up(const uint8_t* __restrict__ Tprev, const Map4* __restrict__ Q,
-                                                      uint8_t* lev, long long N, int LB) {
-    __shared__ uint32_t q[4][256];
-    __shared__ uint8_t sl[2 << kLB];
-    const int TS = 1 << LB;
-    const long long base = (long long)blockIdx.x << LB;
-    if (Tprev) load_map(q, Q);
+// ---------------------------------------------------------------------------
+// The tiled form, 14 <= m <= 27.  Tiles of 2^12 labels, one CTA of 256
+// threads per tile, thread t owning the 16 labels 16 t .. 16 t + 15 of its
+// tile ("group" t).
+//
+// Tree storage.  Levels are kept as 32-byte records.  A record of base level L
+// holds the 16 nodes of level L under one node of level L + 4 (bytes 0..15),
+// the 8, 4 and 2 nodes of levels L+1 .. L+3 between (bytes 16..23, 24..27,
+// 28..29) and that node (byte 30).  Records of base level 0 (one per group),
+// 4 (one per 256 labels) and 8 (one per tile) hold the tile's levels 0 .. 12;
+// the tile minima (level 12) also go to a plain array, from which every CTA
+// builds levels 12 .. m in its shared memory.  Reading a representative
+// downwards from level 11 touches at most one record of each base level.
+//
+// Backward sweep, one cooperative launch with two grid-wide waits per
+// coordinate j = s-1 .. 0:
+//   up    leaves T'[U] = T_{j+1}[Q_j(U)] of every tile and their records;
+//   wait
+//   down  the coarse tree, A down to the leaves, T_j = min(T', A_0) and the
+//         digit vector k_j(U) of the representative: top digit d-1, then the
+//         lower digits smallest-first against the same tree (the reading of
+//         the per-digit programme, which depends on U alone); T_j replaces
+//         T_{j+1} in place (its gathers are done) and k_j goes to K[j][U];
+//   wait  (T_j complete before coordinate j-1 gathers from it).
+// Forward reading, one ordinary launch: every label H follows its own chain
+//   U_0 = I_0(H),  k_j = K[j][U_j],  U_{j+1} = Q_j(U_j ^ k_j)
+// (U_j ^ k_j are the coordinates of the label left after coordinate j), and
+// multiplies its weight denominator by (1 + k_j)^2 -- no label waits for
+// another and no tree is read again.
+constexpr int kTL = 12;                    // labels per tile: 2^12
+constexpr int kTT = 256;                   // threads per tile CTA
+constexpr int kRecBytes = 8192 + 512 + 32; // one tile's records
+constexpr int kFwdL = 8;                   // labels per thread of the forward reading
+constexpr unsigned long long kGridWaitNs = 2000000000ull;
+
+struct TileArgs {
+    const Map4* Q;     // Q_j, j = 0 .. s-2
+    uint8_t* T;        // N bytes: T_{j+1} before coordinate j's down pass, T_j after
+    uint32_t* K;       // s x N: k_j(U)
+    uint8_t* rec0;     // N / 16 records
+    uint8_t* rec4;     // N / 256 records
+    uint8_t* rec8;     // N / 4096 records
+    uint8_t* tmin;     // N / 4096 tile minima
+    unsigned* flags;   // [0] max T_0, [1] weight overflow, [2] a wait gave up, [3] arrivals
+    long long N;
+    int m, s;
+};
+
+// byte of node x (any index at that level) of level L + i in a record of base level L
+__device__ __forceinline__ int rec_off(int i, uint32_t x) { return (32 - (32 >> i)) + (int)(x & (15u >> i)); }
+
+// bytes 16..31 of a record from its 16 base nodes (bytes 0..15, four per word)
+__device__ __forceinline__ uint4 rec_upper(uint4 lo) {
+    const uint32_t a0 = __vminu4(__byte_perm(lo.x, lo.y, 0x6420), __byte_perm(lo.x, lo.y, 0x7531));
+    const uint32_t a1 = __vminu4(__byte_perm(lo.z, lo.w, 0x6420), __byte_perm(lo.z, lo.w, 0x7531));
+    const uint32_t b = __vminu4(__byte_perm(a0, a1, 0x6420), __byte_perm(a0, a1, 0x7531));
+    const uint32_t c = __vminu4(__byte_perm(b, 0u, 0x4420), __byte_perm(b, 0u, 0x4431));
+    const uint32_t e = min(c & 255u, (c >> 8) & 255u);
+    return make_uint4(a0, a1, b, (c & 0xffffu) | (e << 16));
+}
+
+__device__ __forceinline__ unsigned byte_of(uint32_t w, int b) { return (w >> (8 * b)) & 255u; }
+
+__device__ __forceinline__ unsigned ld_acquire_gpu(const unsigned* p) {
+    unsigned v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ void red_release_gpu(unsigned* p, unsigned v) {
+    asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+__device__ __forceinline__ unsigned long long global_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Every CTA of the cooperative grid arrives at flags[3]; returns false, with
+// flags[2] set, when the wait gives up after kGridWaitNs or another CTA gave up.
+__device__ bool grid_wait(unsigned* flags, unsigned& target, int* ok) {
     __syncthreads();
-    for (int e = threadIdx.x; e < TS; e += blockDim.x) {
-        const uint32_t U = (uint32_t)(base + e);
-        const uint8_t v = Tprev ? Tprev[apply4(q, U)] : (U == 0 ? 0 : kInfB);
-        sl[e] = v;
-        lev[base + e] = v;
+    if (threadIdx.x == 0) {
+        target += gridDim.x;
+        __threadfence();
+        red_release_gpu(flags + 3, 1u);
+        int good = 1;
+        const unsigned long long t0 = global_ns();
+        while ((int)(ld_acquire_gpu(flags + 3) - target) < 0) {
+            if (*(volatile unsigned*)(flags + 2)) {
+                good = 0;
+                break;
+            }
+            if (global_ns() - t0 > kGridWaitNs) {
+                atomicExch(flags + 2, 1u);
+                good = 0;
+                break;
+            }
+            __nanosleep(32);
+        }
+        __threadfence();
+        *ok = good;
     }
     __syncthreads();
-    for (int i = 1; i <= LB; ++i) {
-        const int n = TS >> i;
-        const uint8_t* src = sl + loff(TS, i - 1);
-        uint8_t* dst = sl + loff(TS, i);
-        for (int v = threadIdx.x; v < n; v += blockDim.x) {
-            const uint8_t x = min(src[2 * v], src[2 * v + 1]);
-            dst[v] = x;
-            lev[loff(N, i) + (base >> i) + v] = x;
+    return *ok != 0;
+}
+
+// up: the leaves of tile `tile` and its records (st4: 256 bytes, st8: 16 bytes
+// of shared staging, both 16-byte aligned)
+__device__ __forceinline__ void tile_up(const TileArgs& a, uint32_t tile, bool first, const uint32_t (*q)[256],
+                                        uint8_t* st4, uint8_t* st8) {
+    const int t = threadIdx.x;
+    const uint32_t g = (tile << 8) | (uint32_t)t;
+    const uint32_t U0 = g << 4;
+    uint32_t w[4];
+    if (first) {
+        // T_{s} in any basis: 0 at label 0, infinite elsewhere
+        w[0] = U0 == 0 ? 0xffffff00u : 0xffffffffu;
+        w[1] = w[2] = w[3] = 0xffffffffu;
+    } else {
+        const uint32_t base = apply4(q, U0);   // Q(U0 ^ e) = Q(U0) ^ Q(e), e < 16
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            uint32_t x = 0;
+#pragma unroll
+            for (int b = 0; b < 4; ++b) x |= (uint32_t)a.T[base ^ q[0][4 * i + b]] << (8 * b);
+            w[i] = x;
         }
-        __syncthreads();
+    }
+    const uint4 lo = make_uint4(w[0], w[1], w[2], w[3]);
+    const uint4 hi = rec_upper(lo);
+    uint4* r0 = reinterpret_cast<uint4*>(a.rec0 + ((size_t)g << 5));
+    r0[0] = lo;
+    r0[1] = hi;
+    st4[t] = (uint8_t)(hi.w >> 16);
+    __syncwarp();
+    if ((t & 15) == 0) {
+        const uint4 l4 = *reinterpret_cast<const uint4*>(st4 + t);
+        const uint4 h4 = rec_upper(l4);
+        uint4* r4 = reinterpret_cast<uint4*>(a.rec4 + ((size_t)(g >> 4) << 5));
+        r4[0] = l4;
+        r4[1] = h4;
+        st8[t >> 4] = (uint8_t)(h4.w >> 16);
+    }
+    __syncthreads();
+    if (t == 0) {
+        const uint4 l8 = *reinterpret_cast<const uint4*>(st8);
+        const uint4 h8 = rec_upper(l8);
+        uint4* r8 = reinterpret_cast<uint4*>(a.rec8 + ((size_t)tile << 5));
+        r8[0] = l8;
+        r8[1] = h8;
+        a.tmin[tile] = (uint8_t)(h8.w >> 16);
     }
 }
 
-// Levels LB+1 .. m of the tree from level LB (one CTA); with want_a, also the
-// top-down minima A for levels m-1 .. LB, stored per level-LB node as
-// (value | d << 8).  Dynamic shared memory: 2 * nLB bytes of levels and
-// 2 * nLB uint16 of A.
-__global__ void __launch_bounds__(1024) k_tree_coarse(uint8_t* lev, uint16_t* Aout, long long N, int m, int LB,
-                                                      int want_a) {
-    extern __shared__ __align__(16) unsigned char sm[];
-    const int nLB = (int)(N >> LB);
-    uint8_t* sl = sm;                                              // levels LB.. : level LB+i at loff(nLB, i)
-    uint16_t* A0 = reinterpret_cast<uint16_t*>(sm + ((2 * nLB + 15) & ~15));
-    uint16_t* A1 = A0 + nLB;
-    const int top = m - LB;                                        // levels above LB
-    for (int v = threadIdx.x; v < nLB; v += blockDim.x) sl[v] = lev[loff(N, LB) + v];
-    __syncthreads();
-    for (int i = 1; i <= top; ++i) {
-        const int n = nLB >> i;
-        const uint8_t* src = sl + loff(nLB, i - 1);
-        uint8_t* dst = sl + loff(nLB, i);
-        for (int v = threadIdx.x; v < n; v += blockDim.x) {
-            const uint8_t x = min(src[2 * v], src[2 * v + 1]);
-            dst[v] = x;
-            lev[loff(N, LB + i) + v] = x;
-        }
-        __syncthreads();
-    }
-    if (!want_a) return;
-    // A at level m: one node, infinite
-    uint16_t* cur = A0;
-    uint16_t* nxt = A1;
-    if (threadIdx.x == 0) cur[0] = kInfB;
-    __syncthreads();
-    for (int i = m - 1; i >= LB; --i) {
-        const int n = (int)(N >> i);
-        const uint8_t* S = sl + loff(nLB, i - LB);
-        for (int v = threadIdx.x; v < n; v += blockDim.x) {
-            const uint16_t par = cur[v >> 1];
-            const unsigned c = sat_add(S[v ^ 1], (unsigned)(i + 1));
-            nxt[v] = c <= (unsigned)(par & 255) ? (uint16_t)(c | ((unsigned)(i + 1) << 8)) : par;
-        }
-        __syncthreads();
-        uint16_t* tmp = cur;
-        cur = nxt;
-        nxt = tmp;
-    }
-    for (int v = threadIdx.x; v < nLB; v += blockDim.x) Aout[v] = cur[v];
-}
-
-// Top-down minima through one tile's levels LB-1 .. 0 and the coordinate's
-// tables in its own basis: TU = min(T', A_0), DU = 0 if T' <= A_0 else d.
-__global__ void __launch_bounds__(kThreads) k_tree_down(const uint8_t* __restrict__ lev,
-                                                        const uint16_t* __restrict__ Acoarse, uint8_t* TU, uint8_t* DU,
-                                                        long long N, int LB) {
-    __shared__ uint8_t sl[2 << kLB];
-    __shared__ uint16_t a0[1 << kLB], a1[1 << kLB];
-    const int TS = 1 << LB;
-    const long long base = (long long)blockIdx.x << LB;
-    for (int i = 0; i < LB; ++i) {
-        const int n = TS >> i;
-        for (int v = threadIdx.x; v < n; v += blockDim.x) sl[loff(TS, i) + v] = lev[loff(N, i) + (base >> i) + v];
-    }
-    if (threadIdx.x == 0) a0[0] = Acoarse[blockIdx.x];
-    __syncthreads();
-    uint16_t* cur = a0;
-    uint16_t* nxt = a1;
-    for (int i = LB - 1; i >= 0; --i) {
-        const int n = TS >> i;
-        const uint8_t* S = sl + loff(TS, i);
-        for (int v = threadIdx.x; v < n; v += blockDim.x) {
-            const uint16_t par = cur[v >> 1];
-            const unsigned c = sat_add(S[v ^ 1], (unsigned)(i + 1));
-            nxt[v] = c <= (unsigned)(par & 255) ? (uint16_t)(c | ((unsigned)(i + 1) << 8)) : par;
-        }
-        __syncthreads();
-        uint16_t* tmp = cur;
-        cur = nxt;
-        nxt = tmp;
-    }
-    for (int e = threadIdx.x; e < TS; e += blockDim.x) {
-        const unsigned t = sl[e], a = cur[e];
-        const bool keep = t <= (a & 255);
-        TU[base + e] = keep ? (uint8_t)t : (uint8_t)(a & 255);
-        DU[base + e] = keep ? 0 : (uint8_t)(a >> 8);
+// one step of the top-down minima: the candidate of level i (sibling value
+// sv, nu = i + 1) against the running minimum (av, ad) of the parent; ties go
+// to the candidate, as in the per-digit sweep
+__device__ __forceinline__ void a_step(unsigned sv, int i, unsigned& av, unsigned& ad) {
+    const unsigned c = sat_add(sv, (unsigned)(i + 1));
+    if (c <= av) {
+        av = c;
+        ad = (unsigned)(i + 1);
     }
 }
 
-// Forward reading of coordinate j for every coset label: g (remaining label),
-// U = U_j(g), tau = TU_j[U], d = DU_j[U]; the top digit of k_j is d-1, then the
-// lower digits smallest-first against the tree of T_{j+1} (lev).
-__global__ void __launch_bounds__(kThreads) k_tree_recon(uint32_t* G, unsigned long long* Pden, uint8_t* cls,
-                                                         int* overflow, const uint8_t* __restrict__ TU,
-                                                         const uint8_t* __restrict__ DU, const uint8_t* __restrict__ lev,
-                                                         const Map4* __restrict__ Ij, const uint32_t* __restrict__ Rj,
-                                                         int j, int m, long long N) {
-    __shared__ uint32_t inv[4][256];
-    __shared__ uint32_t r[32];
-    load_map(inv, Ij);
-    if (threadIdx.x < m) r[threadIdx.x] = Rj[threadIdx.x];
+// down: T_j and k_j of tile `tile`; cl = levels 12 .. m (level 12 + i at
+// loff(nLB, i)); sr = shared staging of kRecBytes bytes
+__device__ __forceinline__ void tile_down(const TileArgs& a, uint32_t tile, int j, const uint8_t* cl, long long nLB,
+                                          uint8_t* sr, unsigned& mx) {
+    const int t = threadIdx.x;
+    const int m = a.m;
+    const long long N = a.N;
+    {
+        const uint4* s0 = reinterpret_cast<const uint4*>(a.rec0 + ((size_t)tile << 13));
+        uint4* d = reinterpret_cast<uint4*>(sr);
+        d[t] = s0[t];
+        d[t + kTT] = s0[t + kTT];
+        if (t < 32) d[512 + t] = reinterpret_cast<const uint4*>(a.rec4 + ((size_t)tile << 9))[t];
+        else if (t < 34) d[544 + t - 32] = reinterpret_cast<const uint4*>(a.rec8 + ((size_t)tile << 5))[t - 32];
+    }
     __syncthreads();
-    for (long long H = blockIdx.x * (long long)blockDim.x + threadIdx.x; H < N; H += (long long)gridDim.x * blockDim.x) {
-        uint32_t g = G[H];
-        uint32_t U = apply4(inv, g);
-        const int tau = TU[U], d = DU[U];
-        if (!d) continue;
-        uint32_t k = 1u << (d - 1);
-        U ^= k;
-        g ^= r[d - 1];
-        for (int i = d - 2; i >= 0; --i) {
-            const int s = lev[loff(N, i) + (U >> i)];
-            if (s + d != tau) {
-                U ^= 1u << i;
-                g ^= r[i];
-                k |= 1u << i;
+    const uint8_t* R0 = sr;          // 256 group records
+    const uint8_t* R4 = sr + 8192;   // 16 block records
+    const uint8_t* R8 = sr + 8704;   // the tile record
+    // A at the tile root, down the coarse tree
+    unsigned av = kInfB, ad = 0;
+    for (int i = m - 1; i >= kTL; --i) a_step(cl[loff(nLB, i - kTL) + ((tile >> (i - kTL)) ^ 1u)], i, av, ad);
+    // levels 11 .. 4: this thread's ancestors, node t >> (i - 4) of level i in the tile
+#pragma unroll
+    for (int i = 11; i >= 8; --i) a_step(R8[rec_off(i - 8, ((uint32_t)t >> (i - 4)) ^ 1u)], i, av, ad);
+#pragma unroll
+    for (int i = 7; i >= 4; --i) a_step(R4[((t >> 4) << 5) + rec_off(i - 4, ((uint32_t)t >> (i - 4)) ^ 1u)], i, av, ad);
+    // levels 3 .. 0 inside the group record
+    const uint4 glo = *reinterpret_cast<const uint4*>(R0 + (t << 5));
+    const uint4 ghi = *reinterpret_cast<const uint4*>(R0 + (t << 5) + 16);
+    const uint32_t gw[8] = {glo.x, glo.y, glo.z, glo.w, ghi.x, ghi.y, ghi.z, ghi.w};
+    unsigned v3[2], d3[2], v2[4], d2[4], v1[8], d1[8];
+#pragma unroll
+    for (int x = 0; x < 2; ++x) {
+        const int b = 28 + (x ^ 1);
+        v3[x] = av;
+        d3[x] = ad;
+        a_step(byte_of(gw[b >> 2], b & 3), 3, v3[x], d3[x]);
+    }
+#pragma unroll
+    for (int x = 0; x < 4; ++x) {
+        const int b = 24 + (x ^ 1);
+        v2[x] = v3[x >> 1];
+        d2[x] = d3[x >> 1];
+        a_step(byte_of(gw[b >> 2], b & 3), 2, v2[x], d2[x]);
+    }
+#pragma unroll
+    for (int x = 0; x < 8; ++x) {
+        const int b = 16 + (x ^ 1);
+        v1[x] = v2[x >> 1];
+        d1[x] = d2[x >> 1];
+        a_step(byte_of(gw[b >> 2], b & 3), 1, v1[x], d1[x]);
+    }
+    const uint32_t U0 = (tile << kTL) | ((uint32_t)t << 4);
+    uint32_t tw[4] = {0u, 0u, 0u, 0u};
+    uint32_t kv[16];
+#pragma unroll
+    for (int e = 0; e < 16; ++e) {
+        unsigned v0 = v1[e >> 1], d0 = d1[e >> 1];
+        a_step(byte_of(gw[(e ^ 1) >> 2], (e ^ 1) & 3), 0, v0, d0);
+        const unsigned leaf = byte_of(gw[e >> 2], e & 3);
+        const bool keep = leaf <= v0;
+        const int tau = (int)(keep ? leaf : v0);
+        const int d = keep ? 0 : (int)d0;
+        tw[e >> 2] |= (uint32_t)tau << (8 * (e & 3));
+        uint32_t k = 0;
+        if (d) {
+            uint32_t U = (U0 + (uint32_t)e) ^ (1u << (d - 1));
+            k = 1u << (d - 1);
+            int i = d - 2;
+            for (; i >= kTL; --i)
+                if ((int)cl[loff(nLB, i - kTL) + (U >> i)] + d != tau) {
+                    U ^= 1u << i;
+                    k |= 1u << i;
+                }
+            if (i >= 8) {
+                const uint32_t tl = U >> kTL;
+                const uint8_t* R = tl == tile ? R8 : a.rec8 + ((size_t)tl << 5);
+                for (; i >= 8; --i)
+                    if ((int)R[rec_off(i - 8, U >> i)] + d != tau) {
+                        U ^= 1u << i;
+                        k |= 1u << i;
+                    }
+            }
+            if (i >= 4) {
+                const uint32_t bl = U >> 8;
+                const uint8_t* R = (bl >> 4) == tile ? R4 + ((bl & 15u) << 5) : a.rec4 + ((size_t)bl << 5);
+                for (; i >= 4; --i)
+                    if ((int)R[rec_off(i - 4, U >> i)] + d != tau) {
+                        U ^= 1u << i;
+                        k |= 1u << i;
+                    }
+            }
+            if (i >= 0) {
+                const uint32_t gr = U >> 4;
+                const uint8_t* R = (gr >> 8) == tile ? R0 + ((gr & 255u) << 5) : a.rec0 + ((size_t)gr << 5);
+                for (; i >= 0; --i)
+                    if ((int)R[rec_off(i, U >> i)] + d != tau) {
+                        U ^= 1u << i;
+                        k |= 1u << i;
+                    }
             }
         }
-        G[H] = g;
-        const unsigned long long q = (unsigned long long)k + 1ull, q2 = q * q;
-        const unsigned long long pd = Pden[H];
-        if (__umul64hi(pd, q2) != 0ull) *overflow = 1;
-        Pden[H] = pd * q2;
-        cls[2 * H] = (uint8_t)(j + 1);
-        cls[2 * H + 1] = (uint8_t)(cls[2 * H + 1] + 1);
+        kv[e] = k;
+        if (j == 0) mx = max(mx, (unsigned)tau);
     }
+    *reinterpret_cast<uint4*>(a.T + U0) = make_uint4(tw[0], tw[1], tw[2], tw[3]);
+    uint4* kd = reinterpret_cast<uint4*>(a.K + (size_t)j * N + U0);
+#pragma unroll
+    for (int i = 0; i < 4; ++i) kd[i] = make_uint4(kv[4 * i], kv[4 * i + 1], kv[4 * i + 2], kv[4 * i + 3]);
 }
 
-__global__ void k_tree_max(const uint8_t* __restrict__ a, long long N, unsigned* out) {
-    unsigned mx = 0;
-    for (long long h = blockIdx.x * (long long)blockDim.x + threadIdx.x; h < N; h += (long long)gridDim.x * blockDim.x)
-        mx = max(mx, (unsigned)a[h]);
+// The backward sweep (cooperative launch; grid <= tiles, every CTA resident).
+// Dynamic shared memory: map 4096 | records kRecBytes | st4 256 | st8 16 |
+// ok 16 | coarse levels 2 nLB.
+__global__ void __launch_bounds__(kTT) k_tiles_bwd(TileArgs a) {
+    extern __shared__ __align__(16) unsigned char sm[];
+    uint32_t (*q)[256] = reinterpret_cast<uint32_t (*)[256]>(sm);
+    uint8_t* sr = sm + 4096;
+    uint8_t* st4 = sr + kRecBytes;
+    uint8_t* st8 = st4 + 256;
+    int* ok = reinterpret_cast<int*>(st8 + 16);
+    uint8_t* cl = st8 + 32;
+    const long long nLB = a.N >> kTL;
+    const int top = a.m - kTL;
+    unsigned target = 0, mx = 0;
+    for (int j = a.s - 1; j >= 0; --j) {
+        const bool first = j == a.s - 1;
+        if (!first) load_map(q, a.Q + j);
+        __syncthreads();
+        for (long long tl = blockIdx.x; tl < nLB; tl += gridDim.x) {
+            tile_up(a, (uint32_t)tl, first, q, st4, st8);
+            __syncthreads();
+        }
+        if (!grid_wait(a.flags, target, ok)) return;
+        // levels 12 .. m of the tree, in every CTA
+        for (long long v = threadIdx.x; v < nLB; v += kTT) cl[v] = a.tmin[v];
+        __syncthreads();
+        for (int i = 1; i <= top; ++i) {
+            const long long n = nLB >> i;
+            const uint8_t* src = cl + loff(nLB, i - 1);
+            uint8_t* dst = cl + loff(nLB, i);
+            for (long long v = threadIdx.x; v < n; v += kTT) dst[v] = min(src[2 * v], src[2 * v + 1]);
+            __syncthreads();
+        }
+        for (long long tl = blockIdx.x; tl < nLB; tl += gridDim.x) {
+            tile_down(a, (uint32_t)tl, j, cl, nLB, sr, mx);
+            __syncthreads();
+        }
+        if (j > 0 && !grid_wait(a.flags, target, ok)) return;
+    }
     for (int o = 16; o > 0; o >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-    if ((threadIdx.x & 31) == 0) atomicMax(out, mx);
+    if ((threadIdx.x & 31) == 0) atomicMax(a.flags, mx);
 }
 
-__global__ void k_tree_init(uint32_t* G, unsigned long long* Pden, uint8_t* cls, long long N) {
-    for (long long H = blockIdx.x * (long long)blockDim.x + threadIdx.x; H < N; H += (long long)gridDim.x * blockDim.x) {
-        G[H] = (uint32_t)H;
-        Pden[H] = 1ull;
-        cls[2 * H] = 0;
-        cls[2 * H + 1] = 0;
+__device__ __forceinline__ uint32_t apply4_ldg(const Map4* M, uint32_t x) {
+    return __ldg(&M->t[0][x & 255]) ^ __ldg(&M->t[1][(x >> 8) & 255]) ^ __ldg(&M->t[2][(x >> 16) & 255]) ^
+           __ldg(&M->t[3][x >> 24]);
+}
+
+// The forward reading: labels H = h0 + l * stride, l < kFwdL, of this thread.
+__global__ void __launch_bounds__(256) k_tiles_fwd(const uint32_t* __restrict__ K, const Map4* __restrict__ I0,
+                                                   const Map4* __restrict__ Q, unsigned* flags, float* W,
+                                                   uint8_t* cls, long long N, int s) {
+    if (flags[0] >= kInfB || flags[2]) return;   // the backward sweep did not finish: nothing to read
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    const long long h0 = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    uint32_t U[kFwdL];
+    unsigned long long pd[kFwdL];
+    uint32_t c[kFwdL];   // last coordinate with k_j != 0 | count << 8
+#pragma unroll
+    for (int l = 0; l < kFwdL; ++l) {
+        const long long H = h0 + l * stride;
+        U[l] = H < N ? apply4_ldg(I0, (uint32_t)H) : 0u;
+        pd[l] = 1ull;
+        c[l] = 0u;
     }
-}
-
-__global__ void k_tree_weights(const unsigned long long* __restrict__ Pden, float* W, long long N) {
-    for (long long H = blockIdx.x * (long long)blockDim.x + threadIdx.x; H < N; H += (long long)gridDim.x * blockDim.x)
-        W[H] = __fdiv_rn(1.0f, __ull2float_rn(Pden[H]));
+    bool over = false;
+    for (int j = 0; j < s; ++j) {
+        const uint32_t* Kj = K + (size_t)j * N;
+        const Map4* Qj = Q + j;
+#pragma unroll
+        for (int l = 0; l < kFwdL; ++l) {
+            if (h0 + l * stride >= N) continue;
+            const uint32_t k = __ldg(Kj + U[l]);
+            if (k) {
+                const unsigned long long qq = (unsigned long long)k + 1ull, q2 = qq * qq;
+                if (__umul64hi(pd[l], q2) != 0ull) over = true;
+                pd[l] *= q2;
+                c[l] = (uint32_t)(j + 1) | (((c[l] >> 8) + 1u) << 8);
+            }
+            if (j + 1 < s) U[l] = apply4_ldg(Qj, U[l] ^ k);
+        }
+    }
+#pragma unroll
+    for (int l = 0; l < kFwdL; ++l) {
+        const long long H = h0 + l * stride;
+        if (H >= N) continue;
+        W[H] = __fdiv_rn(1.0f, __ull2float_rn(pd[l]));
+        cls[2 * H] = (uint8_t)(c[l] & 255u);
+        cls[2 * H + 1] = (uint8_t)(c[l] >> 8);
+    }
+    if (over) atomicExch(flags + 1, 1u);
 }
 
 // The whole construction for a net of N = 2^m <= 2^13 labels in one CTA: both
@@ -409,8 +605,6 @@ uint32_t host_apply(const Map4& M, uint32_t x) {
     return M.t[0][x & 255] ^ M.t[1][(x >> 8) & 255] ^ M.t[2][(x >> 16) & 255] ^ M.t[3][x >> 24];
 }
 
-unsigned grid_n(long long n) { return (unsigned)std::max(1ll, std::min((n + 255) / 256, 8ll * 152)); }
-
 // the one-CTA form for N <= 2^13
 int tree_one(dwt_plan_s* Pl, const std::vector<Map4>& Imap, const std::vector<Map4>& Qmap, cudaStream_t st) {
     const long long N = Pl->N;
@@ -457,13 +651,111 @@ int tree_one(dwt_plan_s* Pl, const std::vector<Map4>& Imap, const std::vector<Ma
     return DWT_OK;
 }
 
+// Largest cooperative grid of the backward sweep: every tile's CTA when the
+// GPU holds them all at once, else as many as it holds (the CTAs then loop
+// over tiles).  DWT_TILE_GRID, if set to a positive number, caps it further
+// (a tuning and testing knob: results do not depend on the grid).
+static int tiles_grid(long long tiles, size_t smem) {
+    int dev = 0, sms = 0, occ = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_tiles_bwd, kTT, smem) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    long long g = std::min(tiles, (long long)occ * sms);
+    const char* e = getenv("DWT_TILE_GRID");
+    const long long cap = e ? atoll(e) : 0;
+    if (cap > 0) g = std::min(g, cap);
+    return (int)g;
+}
+
+// The tiled form for 14 <= m <= 27 (one cooperative launch for the backward
+// sweep, one launch for the forward reading, one synchronisation).
+int tiles_build(dwt_plan_s* Pl, const Map4& I0, const std::vector<Map4>& Qmap, cudaStream_t st) {
+    const long long N = Pl->N;
+    const int m = Pl->m, s = Pl->s;
+    const long long tiles = N >> kTL;
+    uint8_t *T = nullptr, *rec0 = nullptr, *rec4 = nullptr, *rec8 = nullptr, *tmin = nullptr;
+    uint32_t* K = nullptr;
+    Map4* dmaps = nullptr;
+    unsigned* flags = nullptr;
+    auto cleanup = [&]() {
+        dfree(T, st); dfree(rec0, st); dfree(rec4, st); dfree(rec8, st); dfree(tmin, st);
+        dfree(K, st); dfree(dmaps, st); dfree(flags, st);
+    };
+    if (dmalloc((void**)&T, (size_t)N, st) || dmalloc((void**)&rec0, (size_t)N * 2, st) ||
+        dmalloc((void**)&rec4, (size_t)N / 8, st) || dmalloc((void**)&rec8, (size_t)N / 128, st) ||
+        dmalloc((void**)&tmin, (size_t)tiles, st) || dmalloc((void**)&K, (size_t)s * N * 4, st) ||
+        dmalloc((void**)&dmaps, sizeof(Map4) * s, st) || dmalloc((void**)&flags, 16, st) ||
+        dmalloc((void**)&Pl->d_W, (size_t)N * 4, st) || dmalloc((void**)&Pl->d_cls, (size_t)N * 2, st)) {
+        cleanup();
+        return DWT_ENOMEM;
+    }
+    // maps: I_0, then Q_0 .. Q_{s-2}
+    std::vector<Map4> hm(s);
+    hm[0] = I0;
+    for (int j = 0; j + 1 < s; ++j) hm[1 + j] = Qmap[j];
+    DWT_CK(cudaMemcpyAsync(dmaps, hm.data(), sizeof(Map4) * s, cudaMemcpyHostToDevice, st));
+    DWT_CK(cudaMemsetAsync(flags, 0, 16, st));
+    const size_t smem = 4096 + kRecBytes + 256 + 16 + 16 + (size_t)((2 * tiles + 15) & ~15ll);
+    int rc = smem_limit_max(k_tiles_bwd);
+    if (rc) { cleanup(); return rc; }
+    const int grid = tiles_grid(tiles, smem);
+    if (grid < 1) {
+        cleanup();
+        set_error("no resident grid for the tiled coset-table sweep (%zu bytes of shared memory)", smem);
+        return DWT_ECUDA;
+    }
+    TileArgs A;
+    A.Q = dmaps + 1;
+    A.T = T;
+    A.K = K;
+    A.rec0 = rec0;
+    A.rec4 = rec4;
+    A.rec8 = rec8;
+    A.tmin = tmin;
+    A.flags = flags;
+    A.N = N;
+    A.m = m;
+    A.s = s;
+    {
+        LaunchScope ls("tree_sweep", st);
+        void* args[] = {&A};
+        DWT_CK(cudaLaunchCooperativeKernel((const void*)k_tiles_bwd, dim3((unsigned)grid), dim3(kTT), args, smem, st));
+    }
+    {
+        const long long per_cta = 256ll * kFwdL;
+        const unsigned fg = (unsigned)((N + per_cta - 1) / per_cta);
+        LaunchScope ls("tree_read", st);
+        k_tiles_fwd<<<fg, 256, 0, st>>>(K, dmaps, dmaps + 1, flags, Pl->d_W, Pl->d_cls, N, s);
+    }
+    DWT_CK_LAUNCH("tiled coset tables");
+    unsigned hf[4] = {0, 0, 0, 0};
+    DWT_CK(cudaMemcpyAsync(hf, flags, 16, cudaMemcpyDeviceToHost, st));
+    DWT_CK(cudaStreamSynchronize(st));
+    cleanup();
+    if (hf[2]) {
+        set_error("tiled coset tables: a grid-wide wait gave up");
+        return DWT_ETIMEOUT;
+    }
+    if (hf[0] >= kInfB) {
+        set_error("a least nu over some coset reaches 255");
+        return DWT_EUNSUPPORTED;
+    }
+    if (hf[1]) {
+        set_error("a weight denominator prod (1+k_j)^2 exceeds 64 bits");
+        return DWT_EUNSUPPORTED;
+    }
+    return DWT_OK;
+}
+
 }  // namespace
 
 // Tables W, cls of a p = 2 plan by the tree form.  *used = false (nothing
 // allocated or launched, DWT_OK returned) when a coordinate's rows are
 // dependent or m > 27: the caller then runs the per-digit programme.
 int coset_tables_tree2(dwt_plan_s* Pl, cudaStream_t st, bool* used) {
-    const long long N = Pl->N;
     const int m = Pl->m, s = Pl->s;
     *used = false;
     if (Pl->p != 2 || m > 27 || m < 1) return DWT_OK;
@@ -471,11 +763,9 @@ int coset_tables_tree2(dwt_plan_s* Pl, cudaStream_t st, bool* used) {
     // maps: I_j (labels -> U_j) and Q_j (U_j -> U_{j+1})
     std::vector<Map4> Imap(s), Qmap(s);
     std::vector<uint32_t> inv(m);
-    std::vector<Map4> Fmap(s);
     for (int j = 0; j < s; ++j) {
         if (!gf2_inverse(&R[(size_t)j * m], m, inv.data())) return DWT_OK;
         make_map(inv.data(), m, Imap[j]);
-        make_map(&R[(size_t)j * m], m, Fmap[j]);
     }
     for (int j = 0; j + 1 < s; ++j) {
         std::vector<uint32_t> qc(m);
@@ -484,109 +774,7 @@ int coset_tables_tree2(dwt_plan_s* Pl, cudaStream_t st, bool* used) {
     }
     *used = true;
     if (m <= kLB) return tree_one(Pl, Imap, Qmap, st);
-    const int LB = std::min(m, kLB);
-    const long long nLB = N >> LB;
-    uint8_t *TU = nullptr, *DU = nullptr, *lev = nullptr;
-    uint16_t* Ac = nullptr;
-    Map4* dmaps = nullptr;
-    uint32_t* G = nullptr;
-    unsigned long long* Pden = nullptr;
-    unsigned* flags = nullptr;
-    auto cleanup = [&]() {
-        dfree(TU, st); dfree(DU, st); dfree(lev, st); dfree(Ac, st); dfree(dmaps, st);
-        dfree(G, st); dfree(Pden, st); dfree(flags, st);
-    };
-    if (dmalloc((void**)&TU, (size_t)s * N, st) || dmalloc((void**)&DU, (size_t)s * N, st) ||
-        dmalloc((void**)&lev, (size_t)2 * N, st) || dmalloc((void**)&Ac, (size_t)2 * nLB, st) ||
-        dmalloc((void**)&dmaps, sizeof(Map4) * 2 * s, st) || dmalloc((void**)&flags, 8, st)) {
-        cleanup();
-        return DWT_ENOMEM;
-    }
-    std::vector<Map4> hm(2 * s);
-    for (int j = 0; j < s; ++j) {
-        hm[j] = Imap[j];
-        hm[s + j] = Qmap[j];
-    }
-    DWT_CK(cudaMemcpyAsync(dmaps, hm.data(), sizeof(Map4) * 2 * s, cudaMemcpyHostToDevice, st));
-    DWT_CK(cudaMemsetAsync(flags, 0, 8, st));
-    const Map4* dI = dmaps;
-    const Map4* dQ = dmaps + s;
-    const size_t coarse_smem = (size_t)((2 * nLB + 15) & ~15ll) + (size_t)4 * nLB;
-    {
-        int rc = smem_limit_max(k_tree_coarse);
-        if (rc) { cleanup(); return rc; }
-    }
-    const unsigned tiles = (unsigned)nLB;
-    // backward sweep
-    for (int j = s - 1; j >= 0; --j) {
-        const uint8_t* Tn = j + 1 < s ? TU + (size_t)(j + 1) * N : nullptr;
-        {
-            LaunchScope ls("tree_up", st);
-            k_tree_up<<<tiles, kThreads, 0, st>>>(Tn, Tn ? dQ + j : nullptr, lev, N, LB);
-        }
-        {
-            LaunchScope ls("tree_coarse", st);
-            k_tree_coarse<<<1, 1024, coarse_smem, st>>>(lev, Ac, N, m, LB, 1);
-        }
-        {
-            LaunchScope ls("tree_down", st);
-            k_tree_down<<<tiles, kThreads, 0, st>>>(lev, Ac, TU + (size_t)j * N, DU + (size_t)j * N, N, LB);
-        }
-    }
-    DWT_CK_LAUNCH("coset tree backward sweep");
-    {
-        LaunchScope ls("tree_check", st);
-        k_tree_max<<<grid_n(N), 256, 0, st>>>(TU, N, flags);
-    }
-    unsigned mx = 0;
-    DWT_CK(cudaMemcpyAsync(&mx, flags, sizeof(unsigned), cudaMemcpyDeviceToHost, st));
-    DWT_CK(cudaStreamSynchronize(st));
-    if (mx >= kInfB) {
-        cleanup();
-        set_error("a least nu over some coset reaches 255");
-        return DWT_EUNSUPPORTED;
-    }
-    if (dmalloc((void**)&G, (size_t)N * 4, st) || dmalloc((void**)&Pden, (size_t)N * 8, st) ||
-        dmalloc((void**)&Pl->d_W, (size_t)N * 4, st) || dmalloc((void**)&Pl->d_cls, (size_t)N * 2, st)) {
-        cleanup();
-        return DWT_ENOMEM;
-    }
-    {
-        LaunchScope ls("tree_init", st);
-        k_tree_init<<<grid_n(N), 256, 0, st>>>(G, Pden, Pl->d_cls, N);
-    }
-    int* over = reinterpret_cast<int*>(flags + 1);
-    for (int j = 0; j < s; ++j) {
-        const uint8_t* Tn = j + 1 < s ? TU + (size_t)(j + 1) * N : nullptr;
-        {
-            LaunchScope ls("tree_up", st);
-            k_tree_up<<<tiles, kThreads, 0, st>>>(Tn, Tn ? dQ + j : nullptr, lev, N, LB);
-        }
-        if (m > LB) {
-            LaunchScope ls("tree_coarse", st);
-            k_tree_coarse<<<1, 1024, coarse_smem, st>>>(lev, Ac, N, m, LB, 0);
-        }
-        {
-            LaunchScope ls("tree_recon", st);
-            k_tree_recon<<<grid_n(N), kThreads, 0, st>>>(G, Pden, Pl->d_cls, over, TU + (size_t)j * N,
-                                                         DU + (size_t)j * N, lev, dI + j, Pl->d_R + (size_t)j * m, j,
-                                                         m, N);
-        }
-    }
-    {
-        LaunchScope ls("tree_weights", st);
-        k_tree_weights<<<grid_n(N), 256, 0, st>>>(Pden, Pl->d_W, N);
-    }
-    DWT_CK_LAUNCH("coset tree reconstruction");
-    int ov = 0;
-    DWT_CK(cudaMemcpyAsync(&ov, over, sizeof(int), cudaMemcpyDeviceToHost, st));
-    DWT_CK(cudaStreamSynchronize(st));
-    cleanup();
-    if (ov) {
-        set_error("a weight denominator prod (1+k_j)^2 exceeds 64 bits");
-        return DWT_EUNSUPPORTED;
-    }
-    return DWT_OK;
+    return tiles_build(Pl, Imap[0], Qmap, st);
 }
 
 }  // namespace dwt
