@@ -798,7 +798,13 @@ def serve_runs(dwt, reqs, slots, fracs):
                                 "plan_p50_ms": float(np.percentile(plan[sel], 50)),
                                 "service_p50_ms": float(np.percentile(svc[sel], 50)),
                                 "service_p99_ms": float(np.percentile(svc[sel], 99))})
+        pr = np.array([r["p"] for r in reqs])
+        by_p = [{"p": int(q), "requests": int((pr == q).sum()),
+                 "plan_p50_ms": float(np.percentile(plan[pr == q], 50)),
+                 "service_p50_ms": float(np.percentile(svc[pr == q], 50)),
+                 "service_p99_ms": float(np.percentile(svc[pr == q], 99))} for q in sorted(set(pr.tolist()))]
         return {"label": label, "rate_req_s": rate, "wall_s": wall, "req_per_s": len(reqs) / wall, "by_size": by_size,
+                "by_p": by_p,
                 "points_per_s": pts / wall, "p50_ms": float(np.percentile(lat, 50)),
                 "p99_ms": float(np.percentile(lat, 99)), "service_p50_ms": float(np.percentile(svc, 50)),
                 "service_p99_ms": float(np.percentile(svc, 99)), "plan_p50_ms": float(np.percentile(plan, 50)),

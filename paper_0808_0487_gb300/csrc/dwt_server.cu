@@ -190,11 +190,15 @@ int dwt_server_create(size_t hbm_budget_bytes, int slots, int max_queue, dwt_ser
         hbm_budget_bytes = fr / 2;
     }
     // keep freed blocks in the stream-ordered pool instead of returning them to
-    // the driver at every synchronisation (a setting of this process's pool only)
+    // the driver at every synchronisation, and never let one slot's allocation
+    // wait for another slot's stream to reach a free (settings of this
+    // process's pool only)
     cudaMemPool_t pool;
     if (cudaDeviceGetDefaultMemPool(&pool, S->device) == cudaSuccess) {
         unsigned long long thr = hbm_budget_bytes;
         cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
+        int no = 0;
+        cudaMemPoolSetAttribute(pool, cudaMemPoolReuseAllowInternalDependencies, &no);
     }
     S->budget = hbm_budget_bytes;
     S->slots = slots;

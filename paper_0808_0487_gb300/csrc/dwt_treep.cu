@@ -13,9 +13,12 @@
 // applied with tables over groups of base-p digits whose entries are vectors
 // of 4-bit digits in a 64-bit word; two such vectors add digit-wise mod p
 // without carries (each digit sum is at most 2p - 2 < 16), with the reduction
-// done on all digits at once.  Nets outside m <= 16 and the shared-memory
+// done on all digits at once.  A net of one tile runs in one CTA, larger
+// ones in the tiled form below.  Nets outside m <= 16 and the shared-memory
 // limits of the coarse tree (p = 3: m <= 16, p = 5: m <= 11, p = 7: m <= 8),
 // or with dependent rows, use the per-digit programme.
+#include <stdlib.h>
+
 #include <algorithm>
 #include <vector>
 
@@ -83,46 +86,10 @@ __device__ __forceinline__ unsigned sat_addP(unsigned v, unsigned d) {
     return c > kInfP ? kInfP : c;
 }
 
-template <int P>
-__global__ void __launch_bounds__(kThreadsP) k_treep_up(const uint8_t* __restrict__ Tprev, const MapP* __restrict__ Q,
-                                                        uint8_t* lev, long long N, int m, int ng) {
-    using SH = TreeShape<P>;
-    __shared__ unsigned long long q[kMaxGroups][256];
-    __shared__ uint8_t sl[2 * SH::TS];
-    const long long base = (long long)blockIdx.x * SH::TS;
-    if (Tprev) load_mapP<P>(q, Q, ng);
-    __syncthreads();
-    for (int e = threadIdx.x; e < SH::TS; e += blockDim.x) {
-        const uint32_t U = (uint32_t)(base + e);
-        const uint8_t v = Tprev ? Tprev[applyP<P>(q, U, ng, m)] : (U == 0 ? 0 : kInfP);
-        sl[e] = v;
-        lev[base + e] = v;
-    }
-    __syncthreads();
-    int n = SH::TS;
-    long long nN = N;
-    for (int i = 1; i <= SH::LB; ++i) {
-        const int np = n / P;
-        const long long nNp = nN / P;
-        const uint8_t* src = sl + loffP<P>(SH::TS, n);
-        uint8_t* dst = sl + loffP<P>(SH::TS, np);
-        for (int v = threadIdx.x; v < np; v += blockDim.x) {
-            unsigned x = src[P * v];
-#pragma unroll
-            for (int c = 1; c < P; ++c) x = min(x, (unsigned)src[P * v + c]);
-            dst[v] = (uint8_t)x;
-            lev[loffP<P>(N, nNp) + base / (N / nNp) + v] = (uint8_t)x;
-        }
-        __syncthreads();
-        n = np;
-        nN = nNp;
-    }
-}
-
 // the least of the p - 1 siblings of node v (children of v's parent other than v)
 template <int P>
-__device__ __forceinline__ unsigned sib_min(const uint8_t* S, long long v) {
-    const long long b = v - v % P;
+__device__ __forceinline__ unsigned sib_min(const uint8_t* S, uint32_t v) {
+    const uint32_t b = v - v % P;
     unsigned x = kInfP;
 #pragma unroll
     for (int c = 0; c < P; ++c)
@@ -130,152 +97,352 @@ __device__ __forceinline__ unsigned sib_min(const uint8_t* S, long long v) {
     return x;
 }
 
+// ---------------------------------------------------------------------------
+// The tiled form for nets of more than one tile.  Tiles of p^LB labels (one
+// CTA of kThreadsP threads each); the levels 0 .. LB of every tile in a global
+// array laid out level after level over all N labels; the levels above,
+// built from the tile minima (level LB) in every CTA's shared memory.
+//
+// Backward sweep, one cooperative launch with two grid-wide waits per
+// coordinate j = s-1 .. 0:
+//   up    leaves T'[U] = T_{j+1}[Q_j(U)] of every tile and the tile's levels;
+//   wait
+//   down  the coarse tree, A from the tile root to the leaves, T_j =
+//         min(T', A_0) and the digit vector k_j(U) of the representative
+//         (top digit a >= 1 at position d-1, then the lower digits, each the
+//         smallest a whose node keeps S_i + d = T_j), which depends on U
+//         alone; T_j replaces T_{j+1} in place, k_j goes to K[j][U];
+//   wait  (T_j complete before coordinate j-1 gathers from it).
+// Forward reading, one ordinary launch: every label H follows
+//   U_0 = I_0(H),  k_j = K[j][U_j],  U_{j+1} = Q_j(U_j - k_j digit-wise)
+// and multiplies its weight denominator by (1 + k_j)^2.
+constexpr int kFwdLP = 8;   // labels per thread of the forward reading
+constexpr unsigned long long kGridWaitNsP = 2000000000ull;
+
+struct ArgsP {
+    const MapP* Q;     // Q_j, j = 0 .. s-2
+    uint8_t* T;        // N bytes: T_{j+1} before coordinate j's down pass, T_j after
+    uint32_t* K;       // s x N: k_j(U)
+    uint8_t* lev;      // levels 0 .. LB over all N labels
+    unsigned* flags;   // [0] max T_0, [1] weight overflow, [2] a wait gave up, [3] arrivals
+    long long N;
+    int m, s, ng;
+};
+
+// per-level constants of the tiled sweep (shared memory, set once per launch):
+// pw[i] = p^i; for i <= LB the offset of level i in a tile's levels (toff) and
+// in the global levels (goff), and the nodes of level i per tile (per); for
+// i >= LB the offset of level i in the coarse tree (coff)
+struct LevelsP {
+    uint32_t pw[33], toff[17], goff[17], per[17], coff[33];
+};
+
+// dynamic shared memory of the backward sweep: map | tile levels | A, A' | ok | coarse levels
 template <int P>
-__global__ void __launch_bounds__(1024) k_treep_coarse(uint8_t* lev, uint16_t* Aout, long long N, int m, int want_a) {
-    using SH = TreeShape<P>;
-    extern __shared__ __align__(16) unsigned char sm[];
-    const int nLB = (int)(N / SH::TS);
-    uint8_t* sl = sm;
-    uint16_t* A0 = reinterpret_cast<uint16_t*>(sm + ((2 * nLB + 15) & ~15));
-    uint16_t* A1 = A0 + nLB;
-    const int top = m - SH::LB;
-    const long long offLB = loffP<P>(N, nLB);
-    for (int v = threadIdx.x; v < nLB; v += blockDim.x) sl[v] = lev[offLB + v];
+struct SmemP {
+    static constexpr int TS = TreeShape<P>::TS;
+    static constexpr size_t kMap = sizeof(MapP);
+    static constexpr size_t kLev = ((size_t)2 * TS + 15) & ~(size_t)15;
+    static constexpr size_t kA = ((size_t)2 * TS * 2 + 15) & ~(size_t)15;
+    static constexpr size_t kFixed = kMap + kLev + kA + 16 + ((sizeof(LevelsP) + 15) & ~(size_t)15);
+    static size_t bytes(long long nLB) { return kFixed + (((size_t)2 * nLB + 15) & ~(size_t)15); }
+};
+
+__device__ __forceinline__ unsigned ld_acquire_gpu(const unsigned* p) {
+    unsigned v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ unsigned long long global_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Every CTA of the cooperative grid arrives at flags[3]; false, with flags[2]
+// set, when the wait gives up after kGridWaitNsP or another CTA gave up.
+__device__ bool grid_wait_p(unsigned* flags, unsigned& target, int* ok) {
     __syncthreads();
-    int n = nLB;
-    for (int i = 1; i <= top; ++i) {
-        const int np = n / P;
-        const uint8_t* src = sl + loffP<P>(nLB, n);
-        uint8_t* dst = sl + loffP<P>(nLB, np);
+    if (threadIdx.x == 0) {
+        target += gridDim.x;
+        __threadfence();
+        asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(flags + 3), "r"(1u) : "memory");
+        int good = 1;
+        const unsigned long long t0 = global_ns();
+        while ((int)(ld_acquire_gpu(flags + 3) - target) < 0) {
+            if (*(volatile unsigned*)(flags + 2)) {
+                good = 0;
+                break;
+            }
+            if (global_ns() - t0 > kGridWaitNsP) {
+                atomicExch(flags + 2, 1u);
+                good = 0;
+                break;
+            }
+            __nanosleep(32);
+        }
+        __threadfence();
+        *ok = good;
+    }
+    __syncthreads();
+    return *ok != 0;
+}
+
+template <int P>
+__device__ void levels_init(LevelsP* L, long long N, int m) {
+    using SH = TreeShape<P>;
+    if (threadIdx.x == 0) {
+        const long long nLB = N / SH::TS;
+        long long w = 1;
+        for (int i = 0; i <= m; ++i) {
+            L->pw[i] = (uint32_t)w;
+            if (i <= SH::LB) {
+                long long per = 1;
+                for (int l = i; l < SH::LB; ++l) per *= P;
+                L->per[i] = (uint32_t)per;
+                L->toff[i] = (uint32_t)loffP<P>(SH::TS, per);
+                L->goff[i] = (uint32_t)loffP<P>(N, N / w);
+            }
+            if (i >= SH::LB) L->coff[i] = (uint32_t)loffP<P>(nLB, N / w);
+            w *= P;
+        }
+    }
+}
+
+template <int P>
+__device__ __forceinline__ void tileP_up(const ArgsP& a, uint32_t tile, bool first, const unsigned long long (*q)[256],
+                                         uint8_t* sl, const LevelsP* L) {
+    using SH = TreeShape<P>;
+    const uint32_t base = tile * (uint32_t)SH::TS;
+    for (int e = threadIdx.x; e < SH::TS; e += blockDim.x) {
+        const uint32_t U = base + (uint32_t)e;
+        const uint8_t v = first ? (U == 0 ? 0 : kInfP) : a.T[applyP<P>(q, U, a.ng, a.m)];
+        sl[e] = v;
+        a.lev[U] = v;
+    }
+    __syncthreads();
+    for (int i = 1; i <= SH::LB; ++i) {
+        const int np = (int)L->per[i];   // nodes of level i in the tile
+        const uint8_t* src = sl + L->toff[i - 1];
+        uint8_t* dst = sl + L->toff[i];
+        uint8_t* gdst = a.lev + L->goff[i] + (size_t)tile * (uint32_t)np;
         for (int v = threadIdx.x; v < np; v += blockDim.x) {
             unsigned x = src[P * v];
 #pragma unroll
             for (int c = 1; c < P; ++c) x = min(x, (unsigned)src[P * v + c]);
             dst[v] = (uint8_t)x;
-            lev[loffP<P>(N, np) + v] = (uint8_t)x;
+            gdst[v] = (uint8_t)x;
         }
         __syncthreads();
-        n = np;
     }
-    if (!want_a) return;
-    uint16_t* cur = A0;
-    uint16_t* nxt = A1;
-    if (threadIdx.x == 0) cur[0] = kInfP;
-    __syncthreads();
-    n = 1;   // nodes at level i + 1
-    for (int i = m - 1; i >= SH::LB; --i) {
-        const int ni = n * P;
-        const uint8_t* S = sl + loffP<P>(nLB, ni);
-        for (int v = threadIdx.x; v < ni; v += blockDim.x) {
-            const uint16_t par = cur[v / P];
-            const unsigned c = sat_addP(sib_min<P>(S, v), (unsigned)(i + 1));
-            nxt[v] = c <= (unsigned)(par & 255) ? (uint16_t)(c | ((unsigned)(i + 1) << 8)) : par;
-        }
-        __syncthreads();
-        uint16_t* tmp = cur;
-        cur = nxt;
-        nxt = tmp;
-        n = ni;
-    }
-    for (int v = threadIdx.x; v < nLB; v += blockDim.x) Aout[v] = cur[v];
 }
 
 template <int P>
-__global__ void __launch_bounds__(kThreadsP) k_treep_down(const uint8_t* __restrict__ lev,
-                                                          const uint16_t* __restrict__ Acoarse, uint8_t* TU, uint8_t* DU,
-                                                          long long N) {
+__device__ __forceinline__ void tileP_down(const ArgsP& a, uint32_t tile, int j, const uint8_t* cl, uint8_t* sl,
+                                           uint16_t* a0, uint16_t* a1, const LevelsP* L, unsigned& mx) {
     using SH = TreeShape<P>;
-    __shared__ uint8_t sl[2 * SH::TS];
-    __shared__ uint16_t a0[SH::TS], a1[SH::TS];
-    const long long base = (long long)blockIdx.x * SH::TS;
-    {
-        int n = SH::TS;
-        long long nN = N;
-        for (int i = 0; i < SH::LB; ++i) {
-            for (int v = threadIdx.x; v < n; v += blockDim.x)
-                sl[loffP<P>(SH::TS, n) + v] = lev[loffP<P>(N, nN) + base / (N / nN) + v];
-            n /= P;
-            nN /= P;
-        }
+    const long long N = a.N;
+    const int m = a.m;
+    const uint32_t base = tile * (uint32_t)SH::TS;
+    for (int i = 0; i < SH::LB; ++i) {
+        const int n = (int)L->per[i];
+        const uint8_t* g = a.lev + L->goff[i] + (size_t)tile * (uint32_t)n;
+        uint8_t* d = sl + L->toff[i];
+        for (int v = threadIdx.x; v < n; v += blockDim.x) d[v] = g[v];
     }
-    if (threadIdx.x == 0) a0[0] = Acoarse[blockIdx.x];
+    if (threadIdx.x == 0) {
+        // A at the tile root, down the coarse tree: node tile / p^(i - LB) of level i
+        unsigned av = kInfP, ad = 0;
+        for (int i = m - 1; i >= SH::LB; --i) {
+            const uint32_t node = tile / L->pw[i - SH::LB];
+            const unsigned c = sat_addP(sib_min<P>(cl + L->coff[i], node), (unsigned)(i + 1));
+            if (c <= av) {
+                av = c;
+                ad = (unsigned)(i + 1);
+            }
+        }
+        a0[0] = (uint16_t)(av | (ad << 8));
+    }
     __syncthreads();
     uint16_t* cur = a0;
     uint16_t* nxt = a1;
-    int n = 1;
     for (int i = SH::LB - 1; i >= 0; --i) {
-        const int ni = n * P;
-        const uint8_t* S = sl + loffP<P>(SH::TS, ni);
+        const int ni = (int)L->per[i];
+        const uint8_t* S = sl + L->toff[i];
         for (int v = threadIdx.x; v < ni; v += blockDim.x) {
             const uint16_t par = cur[v / P];
-            const unsigned c = sat_addP(sib_min<P>(S, v), (unsigned)(i + 1));
+            const unsigned c = sat_addP(sib_min<P>(S, (uint32_t)v), (unsigned)(i + 1));
             nxt[v] = c <= (unsigned)(par & 255) ? (uint16_t)(c | ((unsigned)(i + 1) << 8)) : par;
         }
         __syncthreads();
         uint16_t* tmp = cur;
         cur = nxt;
         nxt = tmp;
-        n = ni;
     }
     for (int e = threadIdx.x; e < SH::TS; e += blockDim.x) {
-        const unsigned t = sl[e], a = cur[e];
-        const bool keep = t <= (a & 255);
-        TU[base + e] = keep ? (uint8_t)t : (uint8_t)(a & 255);
-        DU[base + e] = keep ? 0 : (uint8_t)(a >> 8);
+        const unsigned t = sl[e], A = cur[e];
+        const bool keep = t <= (A & 255);
+        const int tau = (int)(keep ? t : (A & 255));
+        const int d = keep ? 0 : (int)(A >> 8);
+        const uint32_t U = base + (uint32_t)e;
+        uint32_t k = 0;
+        if (d) {
+            // digits 0 .. d-1 of U (4 bits each); the reading changes digit i at level i only
+            unsigned long long dg = 0;
+            uint32_t x = U;
+            for (int c = 0; c < d; ++c) {
+                dg |= (unsigned long long)(x % P) << (4 * c);
+                x /= P;
+            }
+            uint32_t node = x;                 // node of level d above U
+            bool own = d - 1 < SH::LB;         // below level LB the nodes lie in this tile
+            for (int i = d - 1; i >= 0; --i) {
+                if (i == SH::LB - 1 && !own) own = node == tile;
+                const uint32_t u = (uint32_t)(dg >> (4 * i)) & 15u;
+                int av = i == d - 1 ? 1 : 0;
+                uint32_t un = u;
+                for (; av < P; ++av) {
+                    un = u >= (uint32_t)av ? u - (uint32_t)av : u + P - (uint32_t)av;
+                    const uint32_t cand = node * P + un;
+                    unsigned v;
+                    if (i >= SH::LB) v = cl[L->coff[i] + cand];
+                    else if (own) v = sl[L->toff[i] + (cand - tile * L->per[i])];
+                    else v = a.lev[L->goff[i] + cand];
+                    if ((int)v + d == tau) break;
+                }
+                if (av == P) av = P - 1;   // unreachable for a consistent table
+                node = node * P + un;
+                k += (uint32_t)av * L->pw[i];
+            }
+        }
+        a.T[U] = (uint8_t)tau;
+        a.K[(size_t)j * N + U] = k;
+        if (j == 0) mx = max(mx, (unsigned)tau);
     }
 }
 
 template <int P>
-__global__ void __launch_bounds__(kThreadsP) k_treep_recon(uint32_t* G, unsigned long long* Pden, uint8_t* cls,
-                                                           int* overflow, const uint8_t* __restrict__ TU,
-                                                           const uint8_t* __restrict__ DU,
-                                                           const uint8_t* __restrict__ lev,
-                                                           const MapP* __restrict__ Ij, const MapP* __restrict__ Fj,
-                                                           int j, int m, int ng, long long N) {
-    __shared__ unsigned long long inv[kMaxGroups][256];
-    __shared__ unsigned long long fwd[kMaxGroups][256];
-    __shared__ long long off[32];
-    __shared__ uint32_t pw[32];
-    load_mapP<P>(inv, Ij, ng);
-    load_mapP<P>(fwd, Fj, ng);
-    if (threadIdx.x == 0) {
-        long long n = N;
-        uint32_t w = 1;
-        for (int i = 0; i <= m; ++i) {
-            off[i] = loffP<P>(N, n);
-            pw[i] = w;
-            n /= P;
-            w *= P;
+__global__ void __launch_bounds__(kThreadsP) k_treep_bwd(ArgsP a) {
+    using SH = TreeShape<P>;
+    using L = SmemP<P>;
+    extern __shared__ __align__(16) unsigned char sm[];
+    unsigned long long (*q)[256] = reinterpret_cast<unsigned long long (*)[256]>(sm);
+    uint8_t* sl = sm + L::kMap;
+    uint16_t* a0 = reinterpret_cast<uint16_t*>(sm + L::kMap + L::kLev);
+    uint16_t* a1 = a0 + SH::TS;
+    int* ok = reinterpret_cast<int*>(sm + L::kMap + L::kLev + L::kA);
+    LevelsP* lv = reinterpret_cast<LevelsP*>(sm + L::kMap + L::kLev + L::kA + 16);
+    uint8_t* cl = sm + L::kFixed;
+    const long long N = a.N;
+    const long long nLB = N / SH::TS;
+    const int top = a.m - SH::LB;
+    unsigned target = 0, mx = 0;
+    levels_init<P>(lv, N, a.m);
+    for (int j = a.s - 1; j >= 0; --j) {
+        const bool first = j == a.s - 1;
+        if (!first) load_mapP<P>(q, a.Q + j, a.ng);
+        __syncthreads();
+        for (long long tl = blockIdx.x; tl < nLB; tl += gridDim.x) {
+            tileP_up<P>(a, (uint32_t)tl, first, q, sl, lv);
+            __syncthreads();
         }
-    }
-    __syncthreads();
-    for (long long H = blockIdx.x * (long long)blockDim.x + threadIdx.x; H < N; H += (long long)gridDim.x * blockDim.x) {
-        const uint32_t g = G[H];
-        uint32_t U = applyP<P>(inv, g, ng, m);
-        const int tau = TU[U], d = DU[U];
-        if (!d) continue;
-        uint32_t k = 0;
-        for (int i = d - 1; i >= 0; --i) {
-            const uint32_t u = (U / pw[i]) % P;
-            int a = i == d - 1 ? 1 : 0;
-            uint32_t Un = U;
-            for (; a < P; ++a) {
-                const uint32_t un = (u + P - (uint32_t)a) % P;
-                Un = U - u * pw[i] + un * pw[i];
-                if ((int)lev[off[i] + Un / pw[i]] + d == tau) break;
+        if (!grid_wait_p(a.flags, target, ok)) return;
+        // the coarse tree: level LB (tile minima) .. m
+        for (long long v = threadIdx.x; v < nLB; v += blockDim.x) cl[v] = a.lev[lv->goff[SH::LB] + v];
+        __syncthreads();
+        long long n = nLB;
+        for (int i = 1; i <= top; ++i) {
+            const long long np = n / P;
+            const uint8_t* src = cl + loffP<P>(nLB, n);
+            uint8_t* dst = cl + loffP<P>(nLB, np);
+            for (long long v = threadIdx.x; v < np; v += blockDim.x) {
+                unsigned x = src[P * v];
+#pragma unroll
+                for (int c = 1; c < P; ++c) x = min(x, (unsigned)src[P * v + c]);
+                dst[v] = (uint8_t)x;
             }
-            if (a == P) a = P - 1;   // unreachable for a consistent table
-            U = Un;
-            k += (uint32_t)a * pw[i];
+            __syncthreads();
+            n = np;
         }
-        G[H] = applyP<P>(fwd, U, ng, m);
-        const unsigned long long q = (unsigned long long)k + 1ull, q2 = q * q;
-        const unsigned long long pd = Pden[H];
-        if (__umul64hi(pd, q2) != 0ull) *overflow = 1;
-        Pden[H] = pd * q2;
-        cls[2 * H] = (uint8_t)(j + 1);
-        cls[2 * H + 1] = (uint8_t)(cls[2 * H + 1] + 1);
+        for (long long tl = blockIdx.x; tl < nLB; tl += gridDim.x) {
+            tileP_down<P>(a, (uint32_t)tl, j, cl, sl, a0, a1, lv, mx);
+            __syncthreads();
+        }
+        if (j > 0 && !grid_wait_p(a.flags, target, ok)) return;
     }
+    for (int o = 16; o > 0; o >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    if ((threadIdx.x & 31) == 0) atomicMax(a.flags, mx);
+}
+
+// a linear map applied from global memory (tables read through the read-only cache)
+template <int P>
+__device__ __forceinline__ uint32_t applyP_ldg(const MapP* M, uint32_t x, int ng, int m) {
+    unsigned long long v = 0;
+    for (int g = 0; g < ng; ++g) {
+        const uint32_t q = x / TreeShape<P>::PG;
+        v = padd<P>(v, __ldg(&M->t[g][x - q * TreeShape<P>::PG]));
+        x = q;
+    }
+    return unpack<P>(v, m);
+}
+
+// U minus k, digit by digit mod p
+template <int P>
+__device__ __forceinline__ uint32_t sub_digits(uint32_t U, uint32_t k) {
+    uint32_t r = 0, pw = 1;
+    while (k) {
+        const uint32_t ud = U % P, kd = k % P;
+        U /= P;
+        k /= P;
+        r += ((ud + P - kd) % P) * pw;
+        pw *= P;
+    }
+    return r + U * pw;
+}
+
+template <int P>
+__global__ void __launch_bounds__(256) k_treep_read(const uint32_t* __restrict__ K, const MapP* __restrict__ I0,
+                                                    const MapP* __restrict__ Q, unsigned* flags, float* W,
+                                                    uint8_t* cls, long long N, int m, int s, int ng) {
+    if (flags[0] >= kInfP || flags[2]) return;   // the backward sweep did not finish: nothing to read
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    const long long h0 = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    uint32_t U[kFwdLP];
+    unsigned long long pd[kFwdLP];
+    uint32_t c[kFwdLP];   // last coordinate with k_j != 0 | count << 8
+#pragma unroll
+    for (int l = 0; l < kFwdLP; ++l) {
+        const long long H = h0 + l * stride;
+        U[l] = H < N ? applyP_ldg<P>(I0, (uint32_t)H, ng, m) : 0u;
+        pd[l] = 1ull;
+        c[l] = 0u;
+    }
+    bool over = false;
+    for (int j = 0; j < s; ++j) {
+        const uint32_t* Kj = K + (size_t)j * N;
+#pragma unroll
+        for (int l = 0; l < kFwdLP; ++l) {
+            if (h0 + l * stride >= N) continue;
+            const uint32_t k = __ldg(Kj + U[l]);
+            if (k) {
+                const unsigned long long qq = (unsigned long long)k + 1ull, q2 = qq * qq;
+                if (__umul64hi(pd[l], q2) != 0ull) over = true;
+                pd[l] *= q2;
+                c[l] = (uint32_t)(j + 1) | (((c[l] >> 8) + 1u) << 8);
+            }
+            if (j + 1 < s) U[l] = applyP_ldg<P>(Q + j, sub_digits<P>(U[l], k), ng, m);
+        }
+    }
+#pragma unroll
+    for (int l = 0; l < kFwdLP; ++l) {
+        const long long H = h0 + l * stride;
+        if (H >= N) continue;
+        W[H] = __fdiv_rn(1.0f, __ull2float_rn(pd[l]));
+        cls[2 * H] = (uint8_t)(c[l] & 255u);
+        cls[2 * H + 1] = (uint8_t)(c[l] >> 8);
+    }
+    if (over) atomicExch(flags + 1, 1u);
 }
 
 // The whole construction for a net of N = p^m <= one tile in one CTA (see the
@@ -430,28 +597,6 @@ __global__ void __launch_bounds__(1024, 1) k_treep_one(const MapP* __restrict__ 
     if (over) atomicExch(flags + 1, 1u);
 }
 
-__global__ void k_treep_max(const uint8_t* __restrict__ a, long long N, unsigned* out) {
-    unsigned mx = 0;
-    for (long long h = blockIdx.x * (long long)blockDim.x + threadIdx.x; h < N; h += (long long)gridDim.x * blockDim.x)
-        mx = max(mx, (unsigned)a[h]);
-    for (int o = 16; o > 0; o >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-    if ((threadIdx.x & 31) == 0) atomicMax(out, mx);
-}
-
-__global__ void k_treep_init(uint32_t* G, unsigned long long* Pden, uint8_t* cls, long long N) {
-    for (long long H = blockIdx.x * (long long)blockDim.x + threadIdx.x; H < N; H += (long long)gridDim.x * blockDim.x) {
-        G[H] = (uint32_t)H;
-        Pden[H] = 1ull;
-        cls[2 * H] = 0;
-        cls[2 * H + 1] = 0;
-    }
-}
-
-__global__ void k_treep_weights(const unsigned long long* __restrict__ Pden, float* W, long long N) {
-    for (long long H = blockIdx.x * (long long)blockDim.x + threadIdx.x; H < N; H += (long long)gridDim.x * blockDim.x)
-        W[H] = __fdiv_rn(1.0f, __ull2float_rn(Pden[H]));
-}
-
 int inv_mod_p(int a, int p) {
     for (int x = 1; x < p; ++x)
         if (a * x % p == 1) return x;
@@ -512,19 +657,25 @@ void make_mapP(const std::vector<std::vector<int>>& cols, int m, MapP& M) {
         const unsigned long long c = pack(cols[i]);
         for (int a = 1; a < P; ++a) mult[(size_t)i * P + a] = padd<P>(mult[(size_t)i * P + a - 1], c);
     }
-    for (int g = 0; g < kMaxGroups; ++g)
-        for (int x = 0; x < 256; ++x) {
-            unsigned long long v = 0;
-            if (g < ng && x < SH::PG) {
-                int y = x;
-                for (int l = 0; l < SH::G; ++l) {
-                    const int dgt = y % P, i = g * SH::G + l;
-                    y /= P;
-                    if (dgt && i < m) v = padd<P>(v, mult[(size_t)i * P + dgt]);
-                }
+    // entry x of group g: the entry with x's lowest nonzero digit (position l,
+    // value a) cleared, plus a * column gG + l -- one digit-wise addition each
+    for (int g = 0; g < kMaxGroups; ++g) {
+        M.t[g][0] = 0ull;
+        for (int x = 1; x < 256; ++x) {
+            if (g >= ng || x >= SH::PG) {
+                M.t[g][x] = 0ull;
+                continue;
             }
-            M.t[g][x] = v;
+            int y = x, l = 0, w = 1;
+            while (y % P == 0) {
+                y /= P;
+                ++l;
+                w *= P;
+            }
+            const int a = y % P, i = g * SH::G + l;
+            M.t[g][x] = i < m ? padd<P>(M.t[g][x - a * w], mult[(size_t)i * P + a]) : M.t[g][x - a * w];
         }
+    }
 }
 
 template <int P>
@@ -536,8 +687,6 @@ unsigned long long host_applyP(const MapP& M, uint32_t x, int ng) {
     }
     return v;
 }
-
-unsigned grid_np(long long n) { return (unsigned)std::max(1ll, std::min((n + 255) / 256, 8ll * 152)); }
 
 template <int P>
 int treep_one(dwt_plan_s* Pl, const std::vector<MapP>& Imap, const std::vector<MapP>& Fmap,
@@ -588,6 +737,102 @@ int treep_one(dwt_plan_s* Pl, const std::vector<MapP>& Imap, const std::vector<M
     return DWT_OK;
 }
 
+// Largest cooperative grid of the backward sweep (see the p = 2 form);
+// DWT_TILE_GRID, if set to a positive number, caps it.
+template <int P>
+int treep_grid(long long tiles, size_t smem) {
+    int dev = 0, sms = 0, occ = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_treep_bwd<P>, kThreadsP, smem) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    long long g = std::min(tiles, (long long)occ * sms);
+    const char* e = getenv("DWT_TILE_GRID");
+    const long long cap = e ? atoll(e) : 0;
+    if (cap > 0) g = std::min(g, cap);
+    return (int)g;
+}
+
+// The tiled form: one cooperative launch for the backward sweep, one launch
+// for the forward reading, one synchronisation.
+template <int P>
+int treep_tiles(dwt_plan_s* Pl, const MapP& I0, const std::vector<MapP>& Qmap, int ng, cudaStream_t st) {
+    using SH = TreeShape<P>;
+    const long long N = Pl->N;
+    const int m = Pl->m, s = Pl->s;
+    const long long tiles = N / SH::TS;
+    uint8_t *T = nullptr, *lev = nullptr;
+    uint32_t* K = nullptr;
+    MapP* dmaps = nullptr;
+    unsigned* flags = nullptr;
+    auto cleanup = [&]() {
+        dfree(T, st); dfree(lev, st); dfree(K, st); dfree(dmaps, st); dfree(flags, st);
+    };
+    if (dmalloc((void**)&T, (size_t)N, st) || dmalloc((void**)&lev, (size_t)2 * N, st) ||
+        dmalloc((void**)&K, (size_t)s * N * 4, st) || dmalloc((void**)&dmaps, sizeof(MapP) * s, st) ||
+        dmalloc((void**)&flags, 16, st) || dmalloc((void**)&Pl->d_W, (size_t)N * 4, st) ||
+        dmalloc((void**)&Pl->d_cls, (size_t)N * 2, st)) {
+        cleanup();
+        return DWT_ENOMEM;
+    }
+    std::vector<MapP> hm(s);
+    hm[0] = I0;
+    for (int j = 0; j + 1 < s; ++j) hm[1 + j] = Qmap[j];
+    DWT_CK(cudaMemcpyAsync(dmaps, hm.data(), sizeof(MapP) * s, cudaMemcpyHostToDevice, st));
+    DWT_CK(cudaMemsetAsync(flags, 0, 16, st));
+    const size_t smem = SmemP<P>::bytes(tiles);
+    int rc = smem_limit_max(k_treep_bwd<P>);
+    if (rc) { cleanup(); return rc; }
+    const int grid = treep_grid<P>(tiles, smem);
+    if (grid < 1) {
+        cleanup();
+        set_error("no resident grid for the tiled coset-table sweep (%zu bytes of shared memory)", smem);
+        return DWT_ECUDA;
+    }
+    ArgsP A;
+    A.Q = dmaps + 1;
+    A.T = T;
+    A.K = K;
+    A.lev = lev;
+    A.flags = flags;
+    A.N = N;
+    A.m = m;
+    A.s = s;
+    A.ng = ng;
+    {
+        LaunchScope ls("tree_sweep", st);
+        void* args[] = {&A};
+        DWT_CK(cudaLaunchCooperativeKernel((const void*)k_treep_bwd<P>, dim3((unsigned)grid), dim3(kThreadsP), args,
+                                           smem, st));
+    }
+    {
+        const long long per_cta = 256ll * kFwdLP;
+        const unsigned fg = (unsigned)((N + per_cta - 1) / per_cta);
+        LaunchScope ls("tree_read", st);
+        k_treep_read<P><<<fg, 256, 0, st>>>(K, dmaps, dmaps + 1, flags, Pl->d_W, Pl->d_cls, N, m, s, ng);
+    }
+    DWT_CK_LAUNCH("tiled coset tables");
+    unsigned hf[4] = {0, 0, 0, 0};
+    DWT_CK(cudaMemcpyAsync(hf, flags, 16, cudaMemcpyDeviceToHost, st));
+    DWT_CK(cudaStreamSynchronize(st));
+    cleanup();
+    if (hf[2]) {
+        set_error("tiled coset tables: a grid-wide wait gave up");
+        return DWT_ETIMEOUT;
+    }
+    if (hf[0] >= kInfP) {
+        set_error("a least nu over some coset reaches 255");
+        return DWT_EUNSUPPORTED;
+    }
+    if (hf[1]) {
+        set_error("a weight denominator prod (1+k_j)^2 exceeds 64 bits");
+        return DWT_EUNSUPPORTED;
+    }
+    return DWT_OK;
+}
+
 template <int P>
 int treep(dwt_plan_s* Pl, cudaStream_t st, bool* used) {
     using SH = TreeShape<P>;
@@ -620,107 +865,7 @@ int treep(dwt_plan_s* Pl, cudaStream_t st, bool* used) {
     }
     *used = true;
     if (m <= SH::LB) return treep_one<P>(Pl, Imap, Fmap, Qmap, ng, st);
-    uint8_t *TU = nullptr, *DU = nullptr, *lev = nullptr;
-    uint16_t* Ac = nullptr;
-    MapP* dmaps = nullptr;
-    uint32_t* G = nullptr;
-    unsigned long long* Pden = nullptr;
-    unsigned* flags = nullptr;
-    auto cleanup = [&]() {
-        dfree(TU, st); dfree(DU, st); dfree(lev, st); dfree(Ac, st); dfree(dmaps, st);
-        dfree(G, st); dfree(Pden, st); dfree(flags, st);
-    };
-    if (dmalloc((void**)&TU, (size_t)s * N, st) || dmalloc((void**)&DU, (size_t)s * N, st) ||
-        dmalloc((void**)&lev, (size_t)2 * N, st) || dmalloc((void**)&Ac, (size_t)2 * nLB, st) ||
-        dmalloc((void**)&dmaps, sizeof(MapP) * 3 * s, st) || dmalloc((void**)&flags, 8, st)) {
-        cleanup();
-        return DWT_ENOMEM;
-    }
-    std::vector<MapP> hm(3 * s);
-    for (int j = 0; j < s; ++j) {
-        hm[j] = Imap[j];
-        hm[s + j] = Fmap[j];
-        hm[2 * s + j] = Qmap[j];
-    }
-    DWT_CK(cudaMemcpyAsync(dmaps, hm.data(), sizeof(MapP) * 3 * s, cudaMemcpyHostToDevice, st));
-    DWT_CK(cudaMemsetAsync(flags, 0, 8, st));
-    const MapP* dI = dmaps;
-    const MapP* dF = dmaps + s;
-    const MapP* dQ = dmaps + 2 * s;
-    const size_t coarse_smem = (size_t)((2 * nLB + 15) & ~15ll) + (size_t)4 * nLB;
-    {
-        int rc = smem_limit_max(k_treep_coarse<P>);
-        if (rc) { cleanup(); return rc; }
-    }
-    const unsigned tiles = (unsigned)nLB;
-    for (int j = s - 1; j >= 0; --j) {
-        const uint8_t* Tn = j + 1 < s ? TU + (size_t)(j + 1) * N : nullptr;
-        {
-            LaunchScope ls("tree_up", st);
-            k_treep_up<P><<<tiles, kThreadsP, 0, st>>>(Tn, Tn ? dQ + j : nullptr, lev, N, m, ng);
-        }
-        {
-            LaunchScope ls("tree_coarse", st);
-            k_treep_coarse<P><<<1, 1024, coarse_smem, st>>>(lev, Ac, N, m, 1);
-        }
-        {
-            LaunchScope ls("tree_down", st);
-            k_treep_down<P><<<tiles, kThreadsP, 0, st>>>(lev, Ac, TU + (size_t)j * N, DU + (size_t)j * N, N);
-        }
-    }
-    DWT_CK_LAUNCH("coset tree backward sweep");
-    {
-        LaunchScope ls("tree_check", st);
-        k_treep_max<<<grid_np(N), 256, 0, st>>>(TU, N, flags);
-    }
-    unsigned mx = 0;
-    DWT_CK(cudaMemcpyAsync(&mx, flags, sizeof(unsigned), cudaMemcpyDeviceToHost, st));
-    DWT_CK(cudaStreamSynchronize(st));
-    if (mx >= kInfP) {
-        cleanup();
-        set_error("a least nu over some coset reaches 255");
-        return DWT_EUNSUPPORTED;
-    }
-    if (dmalloc((void**)&G, (size_t)N * 4, st) || dmalloc((void**)&Pden, (size_t)N * 8, st) ||
-        dmalloc((void**)&Pl->d_W, (size_t)N * 4, st) || dmalloc((void**)&Pl->d_cls, (size_t)N * 2, st)) {
-        cleanup();
-        return DWT_ENOMEM;
-    }
-    {
-        LaunchScope ls("tree_init", st);
-        k_treep_init<<<grid_np(N), 256, 0, st>>>(G, Pden, Pl->d_cls, N);
-    }
-    int* over = reinterpret_cast<int*>(flags + 1);
-    for (int j = 0; j < s; ++j) {
-        const uint8_t* Tn = j + 1 < s ? TU + (size_t)(j + 1) * N : nullptr;
-        {
-            LaunchScope ls("tree_up", st);
-            k_treep_up<P><<<tiles, kThreadsP, 0, st>>>(Tn, Tn ? dQ + j : nullptr, lev, N, m, ng);
-        }
-        if (m > SH::LB) {
-            LaunchScope ls("tree_coarse", st);
-            k_treep_coarse<P><<<1, 1024, coarse_smem, st>>>(lev, Ac, N, m, 0);
-        }
-        {
-            LaunchScope ls("tree_recon", st);
-            k_treep_recon<P><<<grid_np(N), kThreadsP, 0, st>>>(G, Pden, Pl->d_cls, over, TU + (size_t)j * N,
-                                                               DU + (size_t)j * N, lev, dI + j, dF + j, j, m, ng, N);
-        }
-    }
-    {
-        LaunchScope ls("tree_weights", st);
-        k_treep_weights<<<grid_np(N), 256, 0, st>>>(Pden, Pl->d_W, N);
-    }
-    DWT_CK_LAUNCH("coset tree reconstruction");
-    int ov = 0;
-    DWT_CK(cudaMemcpyAsync(&ov, over, sizeof(int), cudaMemcpyDeviceToHost, st));
-    DWT_CK(cudaStreamSynchronize(st));
-    cleanup();
-    if (ov) {
-        set_error("a weight denominator prod (1+k_j)^2 exceeds 64 bits");
-        return DWT_EUNSUPPORTED;
-    }
-    return DWT_OK;
+    return treep_tiles<P>(Pl, Imap[0], Qmap, ng, st);
 }
 
 }  // namespace

@@ -143,14 +143,15 @@ def test_tables_small_large_boundary(dwt, dev, orc, p, m, s):
 
 # Plans without DWT_PLAN_KEEP_INDEX_MAP build K(C) with the min-tree form when
 # every C_j is nonsingular; the tables must equal the oracle's bit for bit, on
-# one tile, several tiles, and with a coarse tree of several levels.  For
-# p = 2: one CTA up to 2^13 labels, else tiles of 2^12 labels in one
-# cooperative launch (both sweeps' trees, the representatives k_j(U)) and one
-# launch of the per-label reading.  For p = 3, 5, 7: tiles of 3^8, 5^5, 7^4
-# labels with one up-sweep launch per coordinate and sweep, or one CTA.
+# one tile, several tiles, and with a coarse tree of several levels.  A net of
+# one tile (2^13, 3^8, 5^5, 7^4 labels) runs in one CTA; larger ones in tiles
+# (2^12, 3^8, 5^5, 7^4 labels) with one cooperative launch (the trees of the
+# backward sweep and the representatives k_j(U)) and one launch of the
+# per-label reading.
 @pytest.mark.parametrize("p,m,s", [(2, 1, 3), (2, 9, 4), (2, 13, 9), (2, 14, 3), (2, 17, 20), (3, 2, 4), (3, 8, 5),
                                    (3, 11, 9), (3, 13, 3), (5, 5, 7), (5, 9, 3), (7, 4, 6), (7, 6, 10), (2, 12, 64),
-                                   (2, 14, 64), (2, 15, 33), (2, 16, 2), (2, 18, 7), (2, 20, 3)])
+                                   (2, 14, 64), (2, 15, 33), (2, 16, 2), (2, 18, 7), (2, 20, 3), (3, 12, 40),
+                                   (5, 8, 33), (7, 7, 12), (3, 14, 3)])
 def test_tables_tree_form(dwt, dev, orc, p, m, s):
     C = S.small_net(p, m, s, index=100 + m + s)
     N = p ** m
@@ -164,10 +165,8 @@ def test_tables_tree_form(dwt, dev, orc, p, m, s):
     # which form ran
     if N <= {2: 8192, 3: 6561, 5: 3125, 7: 2401}[p]:
         assert n == {"tree_up": 0, "tree_one": 1, "tree_sweep": 0, "tree_read": 0}
-    elif p == 2:
-        assert n == {"tree_up": 0, "tree_one": 0, "tree_sweep": 1, "tree_read": 1}
     else:
-        assert (n["tree_one"], n["tree_up"]) == (0, 2 * s)
+        assert n == {"tree_up": 0, "tree_one": 0, "tree_sweep": 1, "tree_read": 1}
     W, cls = _read_tables(dwt, plan, N)
     ref = orc.coset_leaders_dp(p, m, C, want_W64=False)
     assert ref["status"] == 0
@@ -190,17 +189,17 @@ def test_tables_tree_form_dense_fallback(dwt, dev, orc):
     assert np.array_equal(cls, ref["cls"])
 
 
-@pytest.mark.parametrize("grid", [1, 3, 5])
-def test_tables_tiled_form_any_grid(dwt, dev, orc, monkeypatch, grid):
+@pytest.mark.parametrize("p,m,s,grid", [(2, 17, 12, 1), (2, 17, 12, 3), (2, 17, 12, 5), (3, 11, 7, 2),
+                                        (5, 8, 6, 7), (7, 6, 5, 3)])
+def test_tables_tiled_form_any_grid(dwt, dev, orc, monkeypatch, p, m, s, grid):
     """The tiled form with fewer CTAs than tiles (each CTA loops over tiles,
     representatives read across tiles it did not build): same tables."""
-    p, m, s = 2, 17, 12
     C = S.small_net(p, m, s, index=77)
     monkeypatch.setenv("DWT_TILE_GRID", str(grid))
     plan = dwt.dwt_plan_create(p, m, s, C)
     monkeypatch.delenv("DWT_TILE_GRID")
     assert plan.status == 0
-    W, cls = _read_tables(dwt, plan, 2 ** m)
+    W, cls = _read_tables(dwt, plan, p ** m)
     ref = orc.coset_leaders_dp(p, m, C, want_W64=False)
     assert np.array_equal(W.view(np.uint32), ref["W32"].view(np.uint32))
     assert np.array_equal(cls, ref["cls"])
