@@ -60,22 +60,23 @@ __device__ __forceinline__ void load_map(uint32_t (*sm)[256], const Map4* g) {
 }
 
 // ---------------------------------------------------------------------------
-// The tiled form, 14 <= m <= 27.  Tiles of 2^12 labels, one CTA of 256
-// threads per tile, thread t owning the 16 labels 16 t .. 16 t + 15 of its
-// tile ("group" t).
+// The tiled form, 14 <= m <= 27.  Tiles of 2^12 labels in groups of 16 (one
+// thread each); a tile's work in a pass may be split over `parts` CTAs of 256
+// threads, so that small nets still keep many SMs busy.
 //
 // Tree storage.  Levels are kept as 32-byte records.  A record of base level L
 // holds the 16 nodes of level L under one node of level L + 4 (bytes 0..15),
 // the 8, 4 and 2 nodes of levels L+1 .. L+3 between (bytes 16..23, 24..27,
-// 28..29) and that node (byte 30).  Records of base level 0 (one per group),
-// 4 (one per 256 labels) and 8 (one per tile) hold the tile's levels 0 .. 12;
-// the tile minima (level 12) also go to a plain array, from which every CTA
-// builds levels 12 .. m in its shared memory.  Reading a representative
-// downwards from level 11 touches at most one record of each base level.
+// 28..29) and that node (byte 30).  Records of base level 0 (one per group)
+// and 4 (one per block of 256 labels) are stored; the record of base level 8
+// (one per tile) is its 16 block minima, stored as such, the rest derived
+// where needed.  Every CTA builds levels 12 .. m (from the tile minima) in its
+// shared memory.  Reading a representative downwards from level 11 touches at
+// most one record of each base level.
 //
 // Backward sweep, one cooperative launch with two grid-wide waits per
-// coordinate j = s-1 .. 0:
-//   up    leaves T'[U] = T_{j+1}[Q_j(U)] of every tile and their records;
+// coordinate j = s-2 .. 0 (T_{s-1} and k_{s-1} have a closed form):
+//   up    leaves T'[U] = T_{j+1}[Q_j(U)] of every group and their records;
 //   wait
 //   down  the coarse tree, A down to the leaves, T_j = min(T', A_0) and the
 //         digit vector k_j(U) of the representative: top digit d-1, then the
@@ -100,8 +101,7 @@ struct TileArgs {
     uint32_t* K;       // s x N: k_j(U)
     uint8_t* rec0;     // N / 16 records
     uint8_t* rec4;     // N / 256 records
-    uint8_t* rec8;     // N / 4096 records
-    uint8_t* tmin;     // N / 4096 tile minima
+    uint8_t* bmin;     // N / 256 block minima: 16 per tile, the base nodes of the tile's record
     unsigned* flags;   // [0] max T_0, [1] weight overflow, [2] a wait gave up, [3] arrivals
     long long N;
     int m, s;
@@ -167,19 +167,18 @@ __device__ bool grid_wait(unsigned* flags, unsigned& target, int* ok) {
     return *ok != 0;
 }
 
-// up: the leaves of tile `tile` and its records (st4: 256 bytes, st8: 16 bytes
-// of shared staging, both 16-byte aligned)
-__device__ __forceinline__ void tile_up(const TileArgs& a, uint32_t tile, bool first, const uint32_t (*q)[256],
-                                        uint8_t* st4, uint8_t* st8) {
+// up, for part `part` of `parts` of tile `tile`: the groups part * G ..
+// part * G + G - 1 (G = 256 / parts), one per thread: leaves, group records,
+// and per 16 groups the block record and the block minimum (st4: 256 bytes of
+// shared staging, 16-byte aligned)
+__device__ __forceinline__ void tile_up(const TileArgs& a, uint32_t tile, int part, int parts, const uint32_t (*q)[256],
+                                        uint8_t* st4) {
     const int t = threadIdx.x;
-    const uint32_t g = (tile << 8) | (uint32_t)t;
-    const uint32_t U0 = g << 4;
-    uint32_t w[4];
-    if (first) {
-        // T_{s} in any basis: 0 at label 0, infinite elsewhere
-        w[0] = U0 == 0 ? 0xffffff00u : 0xffffffffu;
-        w[1] = w[2] = w[3] = 0xffffffffu;
-    } else {
+    const int G = kTT / parts;
+    const uint32_t g = (tile << 8) | (uint32_t)(part * G + t);   // group, over all labels
+    if (t < G) {
+        const uint32_t U0 = g << 4;
+        uint32_t w[4];
         const uint32_t base = apply4(q, U0);   // Q(U0 ^ e) = Q(U0) ^ Q(e), e < 16
 #pragma unroll
         for (int i = 0; i < 4; ++i) {
@@ -188,30 +187,21 @@ __device__ __forceinline__ void tile_up(const TileArgs& a, uint32_t tile, bool f
             for (int b = 0; b < 4; ++b) x |= (uint32_t)a.T[base ^ q[0][4 * i + b]] << (8 * b);
             w[i] = x;
         }
+        const uint4 lo = make_uint4(w[0], w[1], w[2], w[3]);
+        const uint4 hi = rec_upper(lo);
+        uint4* r0 = reinterpret_cast<uint4*>(a.rec0 + ((size_t)g << 5));
+        r0[0] = lo;
+        r0[1] = hi;
+        st4[t] = (uint8_t)(hi.w >> 16);
     }
-    const uint4 lo = make_uint4(w[0], w[1], w[2], w[3]);
-    const uint4 hi = rec_upper(lo);
-    uint4* r0 = reinterpret_cast<uint4*>(a.rec0 + ((size_t)g << 5));
-    r0[0] = lo;
-    r0[1] = hi;
-    st4[t] = (uint8_t)(hi.w >> 16);
     __syncwarp();
-    if ((t & 15) == 0) {
+    if (t < G && (t & 15) == 0) {
         const uint4 l4 = *reinterpret_cast<const uint4*>(st4 + t);
         const uint4 h4 = rec_upper(l4);
         uint4* r4 = reinterpret_cast<uint4*>(a.rec4 + ((size_t)(g >> 4) << 5));
         r4[0] = l4;
         r4[1] = h4;
-        st8[t >> 4] = (uint8_t)(h4.w >> 16);
-    }
-    __syncthreads();
-    if (t == 0) {
-        const uint4 l8 = *reinterpret_cast<const uint4*>(st8);
-        const uint4 h8 = rec_upper(l8);
-        uint4* r8 = reinterpret_cast<uint4*>(a.rec8 + ((size_t)tile << 5));
-        r8[0] = l8;
-        r8[1] = h8;
-        a.tmin[tile] = (uint8_t)(h8.w >> 16);
+        a.bmin[g >> 4] = (uint8_t)(h4.w >> 16);
     }
 }
 
@@ -226,10 +216,87 @@ __device__ __forceinline__ void a_step(unsigned sv, int i, unsigned& av, unsigne
     }
 }
 
-// down: T_j and k_j of tile `tile`; cl = levels 12 .. m (level 12 + i at
-// loff(nLB, i)); sr = shared staging of kRecBytes bytes
-__device__ __forceinline__ void tile_down(const TileArgs& a, uint32_t tile, int j, const uint8_t* cl, long long nLB,
-                                          uint8_t* sr, unsigned& mx) {
+// 16-bit mask of the bytes 0..15 of a record equal to v
+__device__ __forceinline__ uint32_t eq_mask16(const uint4& r, uint32_t v) {
+    const uint32_t v4 = v * 0x01010101u;
+    auto z = [v4](uint32_t w) {
+        const uint32_t x = w ^ v4;
+        uint32_t y = ~(((x & 0x7f7f7f7fu) + 0x7f7f7f7fu) | x | 0x7f7f7f7fu);   // 0x80 in each zero byte
+        y >>= 7;
+        return (y | (y >> 7) | (y >> 14) | (y >> 21)) & 15u;
+    };
+    return z(r.x) | (z(r.y) << 4) | (z(r.z) << 8) | (z(r.w) << 12);
+}
+
+// the x in the 16-bit set M minimising x ^ u (fallback when M is empty)
+__device__ __forceinline__ uint32_t closest16(uint32_t M, uint32_t u, uint32_t fallback) {
+    uint32_t P = M;
+    P = (u & 1u) ? (((P & 0x5555u) << 1) | ((P >> 1) & 0x5555u)) : P;
+    P = (u & 2u) ? (((P & 0x3333u) << 2) | ((P >> 2) & 0x3333u)) : P;
+    P = (u & 4u) ? (((P & 0x0f0fu) << 4) | ((P >> 4) & 0x0f0fu)) : P;
+    P = (u & 8u) ? (((P & 0x00ffu) << 8) | ((P >> 8) & 0x00ffu)) : P;
+    return P ? ((uint32_t)(__ffs(P) - 1) ^ u) : fallback;
+}
+
+// One step of a reading inside a record of base level L: from `node` of level
+// l (L <= l <= L + 4) down to level L, keeping at each level the child on U's
+// side when its subtree holds the target value, else the other child -- that
+// is, the node x of level L under `node` with value tgt that minimises x ^ U.
+__device__ __forceinline__ uint32_t record_step(const uint8_t* R, int L, int l, uint32_t node, uint32_t U,
+                                                uint32_t tgt) {
+    const int h = l - L;
+    const uint32_t first = (node << h) & 15u;
+    const uint32_t span = (h == 4 ? 0xffffu : ((1u << (1u << h)) - 1u)) << first;
+    const uint4 r = *reinterpret_cast<const uint4*>(R);
+    const uint32_t x = closest16(eq_mask16(r, tgt) & span, (U >> L) & 15u, first);
+    return ((node >> (4 - h)) << 4) | x;   // record index (node of level L + 4) and x
+}
+
+// The representative k_j(U) of a label with d > 0: the top digit d-1 selects
+// the sibling of U's node of level d-1, then the lower digits read the tree
+// downwards, smallest-first, keeping subtrees with value tau - d (levels above
+// 12 from the coarse tree in shared memory, below through one tile, one block
+// and one group record: this tile's from shared memory, others' from global
+// memory).  k_j = U ^ (the leaf reached).
+__device__ __forceinline__ uint32_t representative(const TileArgs& a, uint32_t U, int d, int tau, uint32_t tile,
+                                                   const uint8_t* cl, long long nLB, const uint8_t* R0,
+                                                   const uint8_t* R4, const uint8_t* R8) {
+    const uint32_t tgt = (uint32_t)(tau - d) & 255u;
+    int l = d - 1;
+    uint32_t node = (U >> l) ^ 1u;
+    for (; l > kTL; --l) {
+        uint32_t c = (node << 1) | ((U >> (l - 1)) & 1u);
+        if ((uint32_t)cl[loff(nLB, l - 1 - kTL) + c] != tgt) c ^= 1u;
+        node = c;
+    }
+    if (l >= 8) {
+        const uint32_t tl = node >> (kTL - l);
+        const uint8_t* R = tl == tile ? R8 : a.bmin + ((size_t)tl << 4);
+        node = record_step(R, 8, l, node, U, tgt);
+        l = 8;
+    }
+    if (l >= 4) {
+        const uint32_t bl = node >> (8 - l);
+        const uint8_t* R = (bl >> 4) == tile ? R4 + ((bl & 15u) << 5) : a.rec4 + ((size_t)bl << 5);
+        node = record_step(R, 4, l, node, U, tgt);
+        l = 4;
+    }
+    {
+        const uint32_t gr = node >> (4 - l);
+        const uint8_t* R = (gr >> 8) == tile ? R0 + ((gr & 255u) << 5) : a.rec0 + ((size_t)gr << 5);
+        node = record_step(R, 0, l, node, U, tgt);
+    }
+    return U ^ node;
+}
+
+// down, for part `part` of `parts` (a power of two <= 16) of tile `tile`: the
+// groups g = part * G .. part * G + G - 1, G = 256 / parts, each by one thread
+// (A down the tile to its 16 leaves, T_j), then the readings of their 16 G
+// leaves by all kTT threads, 16 / parts each.  cl = levels 12 .. m (level
+// 12 + i at loff(nLB, i)); sr = shared staging of kRecBytes bytes of records
+// and 2 x 4096 bytes of T_j, d per leaf.
+__device__ __forceinline__ void tile_down(const TileArgs& a, uint32_t tile, int part, int parts, int j,
+                                          const uint8_t* cl, long long nLB, uint8_t* sr, unsigned& mx) {
     const int t = threadIdx.x;
     const int m = a.m;
     const long long N = a.N;
@@ -238,131 +305,138 @@ __device__ __forceinline__ void tile_down(const TileArgs& a, uint32_t tile, int 
         uint4* d = reinterpret_cast<uint4*>(sr);
         d[t] = s0[t];
         d[t + kTT] = s0[t + kTT];
-        if (t < 32) d[512 + t] = reinterpret_cast<const uint4*>(a.rec4 + ((size_t)tile << 9))[t];
-        else if (t < 34) d[544 + t - 32] = reinterpret_cast<const uint4*>(a.rec8 + ((size_t)tile << 5))[t - 32];
+        if (t < 32) {
+            d[512 + t] = reinterpret_cast<const uint4*>(a.rec4 + ((size_t)tile << 9))[t];
+        } else if (t == 32) {
+            const uint4 l8 = *reinterpret_cast<const uint4*>(a.bmin + ((size_t)tile << 4));
+            d[544] = l8;
+            d[545] = rec_upper(l8);
+        }
     }
     __syncthreads();
     const uint8_t* R0 = sr;          // 256 group records
     const uint8_t* R4 = sr + 8192;   // 16 block records
     const uint8_t* R8 = sr + 8704;   // the tile record
-    // A at the tile root, down the coarse tree
-    unsigned av = kInfB, ad = 0;
-    for (int i = m - 1; i >= kTL; --i) a_step(cl[loff(nLB, i - kTL) + ((tile >> (i - kTL)) ^ 1u)], i, av, ad);
-    // levels 11 .. 4: this thread's ancestors, node t >> (i - 4) of level i in the tile
+    uint8_t* stau = sr + kRecBytes;  // T_j of the part's leaves
+    uint8_t* sd = stau + 4096;       // d of the part's leaves
+    const int G = kTT / parts;
+    if (t < G) {
+        const int g = part * G + t;   // group within the tile
+        // A at the tile root, down the coarse tree
+        unsigned av = kInfB, ad = 0;
+        for (int i = m - 1; i >= kTL; --i) a_step(cl[loff(nLB, i - kTL) + ((tile >> (i - kTL)) ^ 1u)], i, av, ad);
+        // levels 11 .. 4: the group's ancestors, node g >> (i - 4) of level i in the tile
 #pragma unroll
-    for (int i = 11; i >= 8; --i) a_step(R8[rec_off(i - 8, ((uint32_t)t >> (i - 4)) ^ 1u)], i, av, ad);
+        for (int i = 11; i >= 8; --i) a_step(R8[rec_off(i - 8, ((uint32_t)g >> (i - 4)) ^ 1u)], i, av, ad);
 #pragma unroll
-    for (int i = 7; i >= 4; --i) a_step(R4[((t >> 4) << 5) + rec_off(i - 4, ((uint32_t)t >> (i - 4)) ^ 1u)], i, av, ad);
-    // levels 3 .. 0 inside the group record
-    const uint4 glo = *reinterpret_cast<const uint4*>(R0 + (t << 5));
-    const uint4 ghi = *reinterpret_cast<const uint4*>(R0 + (t << 5) + 16);
-    const uint32_t gw[8] = {glo.x, glo.y, glo.z, glo.w, ghi.x, ghi.y, ghi.z, ghi.w};
-    unsigned v3[2], d3[2], v2[4], d2[4], v1[8], d1[8];
+        for (int i = 7; i >= 4; --i)
+            a_step(R4[((g >> 4) << 5) + rec_off(i - 4, ((uint32_t)g >> (i - 4)) ^ 1u)], i, av, ad);
+        // levels 3 .. 0 inside the group record
+        const uint4 glo = *reinterpret_cast<const uint4*>(R0 + (g << 5));
+        const uint4 ghi = *reinterpret_cast<const uint4*>(R0 + (g << 5) + 16);
+        const uint32_t gw[8] = {glo.x, glo.y, glo.z, glo.w, ghi.x, ghi.y, ghi.z, ghi.w};
+        unsigned v3[2], d3[2], v2[4], d2[4], v1[8], d1[8];
 #pragma unroll
-    for (int x = 0; x < 2; ++x) {
-        const int b = 28 + (x ^ 1);
-        v3[x] = av;
-        d3[x] = ad;
-        a_step(byte_of(gw[b >> 2], b & 3), 3, v3[x], d3[x]);
-    }
-#pragma unroll
-    for (int x = 0; x < 4; ++x) {
-        const int b = 24 + (x ^ 1);
-        v2[x] = v3[x >> 1];
-        d2[x] = d3[x >> 1];
-        a_step(byte_of(gw[b >> 2], b & 3), 2, v2[x], d2[x]);
-    }
-#pragma unroll
-    for (int x = 0; x < 8; ++x) {
-        const int b = 16 + (x ^ 1);
-        v1[x] = v2[x >> 1];
-        d1[x] = d2[x >> 1];
-        a_step(byte_of(gw[b >> 2], b & 3), 1, v1[x], d1[x]);
-    }
-    const uint32_t U0 = (tile << kTL) | ((uint32_t)t << 4);
-    uint32_t tw[4] = {0u, 0u, 0u, 0u};
-    uint32_t kv[16];
-#pragma unroll
-    for (int e = 0; e < 16; ++e) {
-        unsigned v0 = v1[e >> 1], d0 = d1[e >> 1];
-        a_step(byte_of(gw[(e ^ 1) >> 2], (e ^ 1) & 3), 0, v0, d0);
-        const unsigned leaf = byte_of(gw[e >> 2], e & 3);
-        const bool keep = leaf <= v0;
-        const int tau = (int)(keep ? leaf : v0);
-        const int d = keep ? 0 : (int)d0;
-        tw[e >> 2] |= (uint32_t)tau << (8 * (e & 3));
-        uint32_t k = 0;
-        if (d) {
-            uint32_t U = (U0 + (uint32_t)e) ^ (1u << (d - 1));
-            k = 1u << (d - 1);
-            int i = d - 2;
-            for (; i >= kTL; --i)
-                if ((int)cl[loff(nLB, i - kTL) + (U >> i)] + d != tau) {
-                    U ^= 1u << i;
-                    k |= 1u << i;
-                }
-            if (i >= 8) {
-                const uint32_t tl = U >> kTL;
-                const uint8_t* R = tl == tile ? R8 : a.rec8 + ((size_t)tl << 5);
-                for (; i >= 8; --i)
-                    if ((int)R[rec_off(i - 8, U >> i)] + d != tau) {
-                        U ^= 1u << i;
-                        k |= 1u << i;
-                    }
-            }
-            if (i >= 4) {
-                const uint32_t bl = U >> 8;
-                const uint8_t* R = (bl >> 4) == tile ? R4 + ((bl & 15u) << 5) : a.rec4 + ((size_t)bl << 5);
-                for (; i >= 4; --i)
-                    if ((int)R[rec_off(i - 4, U >> i)] + d != tau) {
-                        U ^= 1u << i;
-                        k |= 1u << i;
-                    }
-            }
-            if (i >= 0) {
-                const uint32_t gr = U >> 4;
-                const uint8_t* R = (gr >> 8) == tile ? R0 + ((gr & 255u) << 5) : a.rec0 + ((size_t)gr << 5);
-                for (; i >= 0; --i)
-                    if ((int)R[rec_off(i, U >> i)] + d != tau) {
-                        U ^= 1u << i;
-                        k |= 1u << i;
-                    }
-            }
+        for (int x = 0; x < 2; ++x) {
+            const int b = 28 + (x ^ 1);
+            v3[x] = av;
+            d3[x] = ad;
+            a_step(byte_of(gw[b >> 2], b & 3), 3, v3[x], d3[x]);
         }
-        kv[e] = k;
-        if (j == 0) mx = max(mx, (unsigned)tau);
-    }
-    *reinterpret_cast<uint4*>(a.T + U0) = make_uint4(tw[0], tw[1], tw[2], tw[3]);
-    uint4* kd = reinterpret_cast<uint4*>(a.K + (size_t)j * N + U0);
 #pragma unroll
-    for (int i = 0; i < 4; ++i) kd[i] = make_uint4(kv[4 * i], kv[4 * i + 1], kv[4 * i + 2], kv[4 * i + 3]);
+        for (int x = 0; x < 4; ++x) {
+            const int b = 24 + (x ^ 1);
+            v2[x] = v3[x >> 1];
+            d2[x] = d3[x >> 1];
+            a_step(byte_of(gw[b >> 2], b & 3), 2, v2[x], d2[x]);
+        }
+#pragma unroll
+        for (int x = 0; x < 8; ++x) {
+            const int b = 16 + (x ^ 1);
+            v1[x] = v2[x >> 1];
+            d1[x] = d2[x >> 1];
+            a_step(byte_of(gw[b >> 2], b & 3), 1, v1[x], d1[x]);
+        }
+        uint32_t tw[4] = {0u, 0u, 0u, 0u}, dw[4] = {0u, 0u, 0u, 0u};
+#pragma unroll
+        for (int e = 0; e < 16; ++e) {
+            unsigned v0 = v1[e >> 1], d0 = d1[e >> 1];
+            a_step(byte_of(gw[(e ^ 1) >> 2], (e ^ 1) & 3), 0, v0, d0);
+            const unsigned leaf = byte_of(gw[e >> 2], e & 3);
+            const bool keep = leaf <= v0;
+            const unsigned tau = keep ? leaf : v0;
+            tw[e >> 2] |= tau << (8 * (e & 3));
+            dw[e >> 2] |= (keep ? 0u : d0) << (8 * (e & 3));
+            if (j == 0) mx = max(mx, tau);
+        }
+        const uint4 tv = make_uint4(tw[0], tw[1], tw[2], tw[3]);
+        *reinterpret_cast<uint4*>(a.T + (((size_t)tile << kTL) | ((size_t)g << 4))) = tv;
+        *reinterpret_cast<uint4*>(stau + (t << 4)) = tv;
+        *reinterpret_cast<uint4*>(sd + (t << 4)) = make_uint4(dw[0], dw[1], dw[2], dw[3]);
+    }
+    __syncthreads();
+    // the readings: leaf x = t + kTT i of the part (consecutive threads, consecutive leaves)
+    const uint32_t L0 = (tile << kTL) | ((uint32_t)part << (kTL - __ffs(parts) + 1));
+    uint32_t* Kj = a.K + (size_t)j * N;
+    for (int x = t; x < 16 * G; x += kTT) {
+        const int d = sd[x];
+        Kj[L0 + x] = d ? representative(a, L0 + (uint32_t)x, d, stau[x], tile, cl, nLB, R0, R4, R8) : 0u;
+    }
 }
 
-// The backward sweep (cooperative launch; grid <= tiles, every CTA resident).
-// Dynamic shared memory: map 4096 | records kRecBytes | st4 256 | st8 16 |
-// ok 16 | coarse levels 2 nLB.
-__global__ void __launch_bounds__(kTT) k_tiles_bwd(TileArgs a) {
+// The backward sweep (cooperative launch, every CTA resident).  The up pass
+// runs one CTA per tile, the down pass one CTA per part of a tile (`parts`
+// per tile).  Dynamic shared memory: map 4096 | records kRecBytes | T_j, d
+// 2 x 4096 | st4 256 | ok 16 | coarse levels 2 nLB.
+__global__ void __launch_bounds__(kTT) k_tiles_bwd(TileArgs a, int parts) {
     extern __shared__ __align__(16) unsigned char sm[];
     uint32_t (*q)[256] = reinterpret_cast<uint32_t (*)[256]>(sm);
     uint8_t* sr = sm + 4096;
-    uint8_t* st4 = sr + kRecBytes;
-    uint8_t* st8 = st4 + 256;
-    int* ok = reinterpret_cast<int*>(st8 + 16);
-    uint8_t* cl = st8 + 32;
+    uint8_t* st4 = sr + kRecBytes + 8192;
+    int* ok = reinterpret_cast<int*>(st4 + 256);
+    uint8_t* cl = st4 + 256 + 16;
     const long long nLB = a.N >> kTL;
     const int top = a.m - kTL;
     unsigned target = 0, mx = 0;
     for (int j = a.s - 1; j >= 0; --j) {
-        const bool first = j == a.s - 1;
-        if (!first) load_map(q, a.Q + j);
+        if (j == a.s - 1) {
+            // T_s is 0 at label 0 only, so T_{s-1}(U) = (highest set bit of U) + 1
+            // with the reading running down to label 0: k_{s-1}(U) = U
+            for (long long tl = blockIdx.x; tl < nLB; tl += gridDim.x) {
+                const uint32_t U0 = ((uint32_t)tl << kTL) | ((uint32_t)threadIdx.x << 4);
+                uint32_t tw[4];
+#pragma unroll
+                for (int w = 0; w < 4; ++w) {
+                    uint32_t x = 0;
+#pragma unroll
+                    for (int b = 0; b < 4; ++b) {
+                        const uint32_t U = U0 + (uint32_t)(4 * w + b);
+                        x |= (U ? (uint32_t)(32 - __clz(U)) : 0u) << (8 * b);
+                    }
+                    tw[w] = x;
+                    if (j == 0) mx = max(mx, (unsigned)(32 - __clz(U0 + 4 * w + 3)));
+                }
+                *reinterpret_cast<uint4*>(a.T + U0) = make_uint4(tw[0], tw[1], tw[2], tw[3]);
+                uint4* kd = reinterpret_cast<uint4*>(a.K + (size_t)j * a.N + U0);
+#pragma unroll
+                for (int w = 0; w < 4; ++w) kd[w] = make_uint4(U0 + 4 * w, U0 + 4 * w + 1, U0 + 4 * w + 2, U0 + 4 * w + 3);
+            }
+            if (j > 0 && !grid_wait(a.flags, target, ok)) return;
+            continue;
+        }
+        load_map(q, a.Q + j);
         __syncthreads();
-        for (long long tl = blockIdx.x; tl < nLB; tl += gridDim.x) {
-            tile_up(a, (uint32_t)tl, first, q, st4, st8);
+        for (long long u = blockIdx.x; u < nLB * parts; u += gridDim.x) {
+            tile_up(a, (uint32_t)(u / parts), (int)(u % parts), parts, q, st4);
             __syncthreads();
         }
         if (!grid_wait(a.flags, target, ok)) return;
         // levels 12 .. m of the tree, in every CTA
-        for (long long v = threadIdx.x; v < nLB; v += kTT) cl[v] = a.tmin[v];
+        for (long long v = threadIdx.x; v < nLB; v += kTT) {
+            const uint4 b = *reinterpret_cast<const uint4*>(a.bmin + (v << 4));
+            const uint32_t x = __vminu4(__vminu4(b.x, b.y), __vminu4(b.z, b.w));
+            cl[v] = (uint8_t)min(min(x & 255u, (x >> 8) & 255u), min((x >> 16) & 255u, x >> 24));
+        }
         __syncthreads();
         for (int i = 1; i <= top; ++i) {
             const long long n = nLB >> i;
@@ -371,8 +445,8 @@ __global__ void __launch_bounds__(kTT) k_tiles_bwd(TileArgs a) {
             for (long long v = threadIdx.x; v < n; v += kTT) dst[v] = min(src[2 * v], src[2 * v + 1]);
             __syncthreads();
         }
-        for (long long tl = blockIdx.x; tl < nLB; tl += gridDim.x) {
-            tile_down(a, (uint32_t)tl, j, cl, nLB, sr, mx);
+        for (long long u = blockIdx.x; u < nLB * parts; u += gridDim.x) {
+            tile_down(a, (uint32_t)(u / parts), (int)(u % parts), parts, j, cl, nLB, sr, mx);
             __syncthreads();
         }
         if (j > 0 && !grid_wait(a.flags, target, ok)) return;
@@ -651,11 +725,8 @@ int tree_one(dwt_plan_s* Pl, const std::vector<Map4>& Imap, const std::vector<Ma
     return DWT_OK;
 }
 
-// Largest cooperative grid of the backward sweep: every tile's CTA when the
-// GPU holds them all at once, else as many as it holds (the CTAs then loop
-// over tiles).  DWT_TILE_GRID, if set to a positive number, caps it further
-// (a tuning and testing knob: results do not depend on the grid).
-static int tiles_grid(long long tiles, size_t smem) {
+// Resident CTAs of the backward sweep on this GPU (0 if unknown).
+static long long tiles_resident(size_t smem) {
     int dev = 0, sms = 0, occ = 0;
     if (cudaGetDevice(&dev) != cudaSuccess ||
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
@@ -663,11 +734,7 @@ static int tiles_grid(long long tiles, size_t smem) {
         cudaGetLastError();
         return 0;
     }
-    long long g = std::min(tiles, (long long)occ * sms);
-    const char* e = getenv("DWT_TILE_GRID");
-    const long long cap = e ? atoll(e) : 0;
-    if (cap > 0) g = std::min(g, cap);
-    return (int)g;
+    return (long long)occ * sms;
 }
 
 // The tiled form for 14 <= m <= 27 (one cooperative launch for the backward
@@ -676,17 +743,17 @@ int tiles_build(dwt_plan_s* Pl, const Map4& I0, const std::vector<Map4>& Qmap, c
     const long long N = Pl->N;
     const int m = Pl->m, s = Pl->s;
     const long long tiles = N >> kTL;
-    uint8_t *T = nullptr, *rec0 = nullptr, *rec4 = nullptr, *rec8 = nullptr, *tmin = nullptr;
+    uint8_t *T = nullptr, *rec0 = nullptr, *rec4 = nullptr, *bmin = nullptr;
     uint32_t* K = nullptr;
     Map4* dmaps = nullptr;
     unsigned* flags = nullptr;
     auto cleanup = [&]() {
-        dfree(T, st); dfree(rec0, st); dfree(rec4, st); dfree(rec8, st); dfree(tmin, st);
+        dfree(T, st); dfree(rec0, st); dfree(rec4, st); dfree(bmin, st);
         dfree(K, st); dfree(dmaps, st); dfree(flags, st);
     };
     if (dmalloc((void**)&T, (size_t)N, st) || dmalloc((void**)&rec0, (size_t)N * 2, st) ||
-        dmalloc((void**)&rec4, (size_t)N / 8, st) || dmalloc((void**)&rec8, (size_t)N / 128, st) ||
-        dmalloc((void**)&tmin, (size_t)tiles, st) || dmalloc((void**)&K, (size_t)s * N * 4, st) ||
+        dmalloc((void**)&rec4, (size_t)N / 8, st) || dmalloc((void**)&bmin, (size_t)N / 256, st) ||
+        dmalloc((void**)&K, (size_t)s * N * 4, st) ||
         dmalloc((void**)&dmaps, sizeof(Map4) * s, st) || dmalloc((void**)&flags, 16, st) ||
         dmalloc((void**)&Pl->d_W, (size_t)N * 4, st) || dmalloc((void**)&Pl->d_cls, (size_t)N * 2, st)) {
         cleanup();
@@ -698,10 +765,27 @@ int tiles_build(dwt_plan_s* Pl, const Map4& I0, const std::vector<Map4>& Qmap, c
     for (int j = 0; j + 1 < s; ++j) hm[1 + j] = Qmap[j];
     DWT_CK(cudaMemcpyAsync(dmaps, hm.data(), sizeof(Map4) * s, cudaMemcpyHostToDevice, st));
     DWT_CK(cudaMemsetAsync(flags, 0, 16, st));
-    const size_t smem = 4096 + kRecBytes + 256 + 16 + 16 + (size_t)((2 * tiles + 15) & ~15ll);
+    const size_t smem = 4096 + kRecBytes + 8192 + 256 + 16 + (size_t)((2 * tiles + 15) & ~15ll);
     int rc = smem_limit_max(k_tiles_bwd);
     if (rc) { cleanup(); return rc; }
-    const int grid = tiles_grid(tiles, smem);
+    // every resident CTA busy in the down pass: parts per tile (a power of two
+    // <= 16); the grid is capped by DWT_TILE_GRID if set (a tuning and testing
+    // knob: the tables do not depend on the grid or the parts)
+    const long long resident = tiles_resident(smem);
+    int parts = 1;
+    while (parts < 16 && tiles * parts * 2 <= resident) parts *= 2;
+    long long g = std::min(tiles * parts, resident);
+    {
+        const char* e = getenv("DWT_TILE_GRID");
+        const long long cap = e ? atoll(e) : 0;
+        if (cap > 0) g = std::min(g, cap);
+    }
+    if (g > 0) {
+        // as few CTAs as give the same number of rounds over the parts
+        const long long rounds = (tiles * parts + g - 1) / g;
+        g = (tiles * parts + rounds - 1) / rounds;
+    }
+    const int grid = (int)g;
     if (grid < 1) {
         cleanup();
         set_error("no resident grid for the tiled coset-table sweep (%zu bytes of shared memory)", smem);
@@ -713,15 +797,14 @@ int tiles_build(dwt_plan_s* Pl, const Map4& I0, const std::vector<Map4>& Qmap, c
     A.K = K;
     A.rec0 = rec0;
     A.rec4 = rec4;
-    A.rec8 = rec8;
-    A.tmin = tmin;
+    A.bmin = bmin;
     A.flags = flags;
     A.N = N;
     A.m = m;
     A.s = s;
     {
         LaunchScope ls("tree_sweep", st);
-        void* args[] = {&A};
+        void* args[] = {&A, &parts};
         DWT_CK(cudaLaunchCooperativeKernel((const void*)k_tiles_bwd, dim3((unsigned)grid), dim3(kTT), args, smem, st));
     }
     {
