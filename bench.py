@@ -386,8 +386,9 @@ def memory_floor(f, c, B, N, stream, peak):
 
 def run_other_configs(dwt, dev, stream, timed, steps):
     """Throughput of the transforms at the other workload shapes: p = 2, m = 20,
-    s = 16 with 32 FP32 and 32 int32 functions (forward, inverse, round trip) and
-    p = 3, m = 13, s = 8 (real FP32 in, complex FP32 out; forward and inverse)."""
+    s = 16 with 32 FP32 and 32 int32 functions (forward, inverse, round trip),
+    mixed-size batches through the grouped call, and p = 3, m = 13, s = 8 (real
+    FP32 in, complex FP32 out; forward and inverse)."""
     import numpy as np
     import torch
 
@@ -417,6 +418,33 @@ def run_other_configs(dwt, dev, stream, timed, steps):
             r[k + "_points_per_s"] = B * N * steps / (ms / 1e3)
         out["p2_m20_s16_b32_" + name] = r
         del x, y
+    # a mixed-size batch: several plans of different N in one grouped call
+    # against one dwt_forward call per plan (same results, bit for bit)
+    for gname, gp, gms, gin, gout in (("grouped_p2_m8_15_f32", 2, range(8, 16), dwt.DWT_F32, dwt.DWT_F32),
+                                      ("grouped_p3_m5_9_c64", 3, range(5, 10), dwt.DWT_F32, dwt.DWT_C64)):
+        gjobs, gpts = [], 0
+        for i, gm in enumerate(gms):
+            gN = gp ** gm
+            gpl = dwt.dwt_plan_create(gp, gm, 1, S.small_net(gp, gm, 1, index=i), dwt.DWT_PLAN_TRANSFORM_ONLY)
+            gx = torch.ones((4, gN), dtype=torch.float32, device=dev)
+            gy = torch.empty((4, gN), dtype=torch.float32 if gp == 2 else torch.complex64, device=dev)
+            gjobs.append((gpl, gx, gy, 4, gN, gN))
+            gpts += 4 * gN
+
+        def per_plan():
+            for j in gjobs:
+                dwt.dwt_forward(j[0], j[1], j[2], j[3], j[4], j[5], gin, gout, stream=stream)
+
+        def grouped():
+            dwt.dwt_forward_grouped(gjobs, gin, gout, stream=stream)
+
+        ms_pp, l_pp = timed(per_plan, steps)
+        ms_g, l_g = timed(grouped, steps)
+        out[gname] = {"jobs": [[gp, gm, 4] for gm in gms], "points_per_step": gpts,
+                      "per_plan_points_per_s": gpts * steps / (ms_pp / 1e3),
+                      "grouped_points_per_s": gpts * steps / (ms_g / 1e3),
+                      "per_plan_launches_per_step": l_pp / steps, "grouped_launches_per_step": l_g / steps}
+        del gjobs
     # the kernel spline of Sec. 3.1 with its ANOVA variances (FP64) on the same
     # net: forward, weight 1 / (p^m K~), inverse and the 2s variance sums
     w2 = S.workload_p2_m20()

@@ -173,6 +173,33 @@ int dwt_inverse(dwt_plan_t plan, const void *in, void *out, int batch, long long
                 dwt_dtype in_t, dwt_dtype out_t, dwt_algo algo, void *stream);
 
 /*
+ * Grouped transforms: the dwt_forward (dwt_inverse) calls of njobs jobs, with
+ * nets of different sizes, in few launches.  Job i is the call
+ *   dwt_forward(jobs[i].plan, jobs[i].in, jobs[i].out, jobs[i].batch,
+ *               jobs[i].ld_in, jobs[i].ld_out, in_t, out_t, DWT_ALGO_AUTO, stream)
+ * (Algorithm 1 / Algorithm 2 per job, same layout, types and in-place rules),
+ * and every output element is bit-identical to that call's.  All plans share
+ * p; in_t / out_t apply to every job.  The jobs' passes run as one launch per
+ * pass index (the generic passes of every prime), and p = 2 F32 / I32 jobs of
+ * 2^12 .. 2^14 points as one launch per size; p = 2 F32 / I32 jobs of
+ * 2^16 .. 2^24 points, which fill the GPU alone, run their own launches.
+ * Jobs with batch 0 are skipped.  The host array is read before return.
+ * Errors: DWT_EINVAL (NULL or empty list, a bad job, mixed p, more than
+ * 2^31 - 1 blocks in one pass), DWT_EUNSUPPORTED (types), DWT_ENOMEM.
+ */
+typedef struct dwt_job {
+    dwt_plan_t plan;
+    const void *in;
+    void *out;
+    int batch;
+    long long ld_in;
+    long long ld_out;
+} dwt_job;
+
+int dwt_forward_grouped(const dwt_job *jobs, int njobs, dwt_dtype in_t, dwt_dtype out_t, void *stream);
+int dwt_inverse_grouped(const dwt_job *jobs, int njobs, dwt_dtype in_t, dwt_dtype out_t, void *stream);
+
+/*
  * dwt_forward_digits / dwt_inverse_digits: the stages of Algorithm 1
  * (Algorithm 2) for the index digits d0 .. d0+nd-1 only, 0 <= d0,
  * d0 + nd <= m.  The transform is the Kronecker product of one p-point DFT per

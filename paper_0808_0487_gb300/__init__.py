@@ -77,6 +77,8 @@ _SIGS = {
     "dwt_index_to_wavenumber": (_I, [_VP, _VP, _VP, _LL, _VP]),
     "dwt_forward": (_I, [_VP, _VP, _VP, _I, _LL, _LL, _I, _I, _I, _VP]),
     "dwt_inverse": (_I, [_VP, _VP, _VP, _I, _LL, _LL, _I, _I, _I, _VP]),
+    "dwt_forward_grouped": (_I, [_VP, _I, _I, _I, _VP]),
+    "dwt_inverse_grouped": (_I, [_VP, _I, _I, _I, _VP]),
     "dwt_forward_digits": (_I, [_VP, _VP, _VP, _I, _LL, _LL, _I, _I, _I, _I, _VP]),
     "dwt_inverse_digits": (_I, [_VP, _VP, _VP, _I, _LL, _LL, _I, _I, _I, _I, _VP]),
     "dwt_interpolate": (_I, [_VP, _VP, _VP, _VP, _I, _LL, _I, _I, _I, _VP, _VP, ctypes.c_double, _VP]),
@@ -272,6 +274,29 @@ def dwt_forward(plan, inp, out, batch, ld_in, ld_out, in_t, out_t, algo=DWT_ALGO
 def dwt_inverse(plan, inp, out, batch, ld_in, ld_out, in_t, out_t, algo=DWT_ALGO_AUTO, stream=None):
     return _check(lib().dwt_inverse(plan.handle, _ptr(inp), _ptr(out), batch, ld_in, ld_out, in_t, out_t, algo,
                                     _stream(stream)))
+
+
+class _Job(ctypes.Structure):
+    """struct dwt_job of include/dwt.h."""
+    _fields_ = [("plan", _VP), ("in_", _VP), ("out", _VP), ("batch", _I), ("ld_in", _LL), ("ld_out", _LL)]
+
+
+def _jobs(jobs):
+    arr = (_Job * len(jobs))()
+    for i, (plan, inp, out, batch, ld_in, ld_out) in enumerate(jobs):
+        arr[i] = _Job(plan.handle, _ptr(inp), _ptr(out), batch, ld_in, ld_out)
+    return arr
+
+
+def dwt_forward_grouped(jobs, in_t, out_t, stream=None):
+    """jobs: list of (plan, in, out, batch, ld_in, ld_out); see dwt_forward_grouped in include/dwt.h."""
+    arr = _jobs(jobs)
+    return _check(lib().dwt_forward_grouped(ctypes.cast(arr, _VP), len(jobs), in_t, out_t, _stream(stream)))
+
+
+def dwt_inverse_grouped(jobs, in_t, out_t, stream=None):
+    arr = _jobs(jobs)
+    return _check(lib().dwt_inverse_grouped(ctypes.cast(arr, _VP), len(jobs), in_t, out_t, _stream(stream)))
 
 
 def dwt_forward_digits(plan, inp, out, batch, ld_in, ld_out, in_t, out_t, d0, nd, stream=None):

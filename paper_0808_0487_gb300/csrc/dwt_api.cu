@@ -639,6 +639,39 @@ int dwt_inverse(dwt_plan_t P, const void* in, void* out, int batch, long long ld
     return transform_common(P, in, out, batch, ld_in, ld_out, in_t, out_t, algo, stream, +1);
 }
 
+static int grouped_common(const dwt_job* jobs, int njobs, dwt_dtype in_t, dwt_dtype out_t, void* stream, int sgn) {
+    if (!jobs || njobs < 1) {
+        set_error("grouped transform: no jobs");
+        return DWT_EINVAL;
+    }
+    std::vector<GroupJob> js;
+    js.reserve((size_t)njobs);
+    for (int i = 0; i < njobs; ++i) {
+        const dwt_job& j = jobs[i];
+        dwt_plan_s* P = j.plan;
+        if (!P || j.batch < 0 || (j.batch > 0 && (!j.in || !j.out)) || j.ld_in < P->N || j.ld_out < P->N) {
+            set_error("grouped transform: bad job %d", i);
+            return DWT_EINVAL;
+        }
+        if (P->p != jobs[0].plan->p) {
+            set_error("grouped transform: job %d has p = %d, job 0 p = %d", i, P->p, jobs[0].plan->p);
+            return DWT_EINVAL;
+        }
+        const int rc = check_transform_types(P, in_t, out_t, sgn);
+        if (rc) return rc;
+        js.push_back(GroupJob{P, j.in, j.out, j.batch, j.ld_in, j.ld_out});
+    }
+    return run_transform_grouped(js, in_t, out_t, sgn, (cudaStream_t)stream);
+}
+
+int dwt_forward_grouped(const dwt_job* jobs, int njobs, dwt_dtype in_t, dwt_dtype out_t, void* stream) {
+    return grouped_common(jobs, njobs, in_t, out_t, stream, -1);
+}
+
+int dwt_inverse_grouped(const dwt_job* jobs, int njobs, dwt_dtype in_t, dwt_dtype out_t, void* stream) {
+    return grouped_common(jobs, njobs, in_t, out_t, stream, +1);
+}
+
 static int digits_common(dwt_plan_t P, const void* in, void* out, int batch, long long ld_in, long long ld_out,
                          dwt_dtype in_t, dwt_dtype out_t, int d0, int nd, void* stream, int sgn) {
     if (!P || batch < 0 || (batch > 0 && (!in || !out)) || ld_in < P->N || ld_out < P->N || d0 < 0 || nd < 1 ||

@@ -118,6 +118,17 @@ const PassPlan& pass_plan(dwt_plan_s* P, int elem_bytes);
 void pass_geometry(int p, int m, int elem, const int* b, int q, long long min_tiles, int wc_div, PassPlan& pp);
 void pass_splits(int p, int m, int elem, std::vector<std::vector<int>>& out);
 void pass_plan_range(int p, int m, int elem, int d0, int nd, long long min_tiles, PassPlan& pp);
+// one job of a grouped transform (the arguments of one dwt_forward call)
+struct GroupJob {
+    dwt_plan_s* plan;
+    const void* in;
+    void* out;
+    int batch;
+    long long ld_in, ld_out;
+};
+int run_transform_grouped(const std::vector<GroupJob>& jobs, dwt_dtype in_t, dwt_dtype out_t, int sgn,
+                          cudaStream_t st);
+int p2_lo_grouped(int L, const std::vector<GroupJob>& jobs, dwt_dtype t, int sgn, cudaStream_t st);
 int tune_passes(dwt_plan_s* P, long long min_tiles, cudaStream_t st);
 bool p2_fast_ok(int m);
 bool p2i_ok(int m, int s);

@@ -43,23 +43,14 @@ template <typename T> struct LoJob {
 // Tiles [0, tiles0) belong to job 0, the rest to job 1: two independent low
 // passes share one launch (e.g. the inverse of one function and the forward of
 // the next), which keeps the memory system busy while either one computes.
+// the low pass of one tile of 2^L elements, src -> dst
 template <typename T, int L>
-__global__ void __launch_bounds__(1 << (L - 6), (L == 14 ? 3 : 4))
-    k2_lo(LoJob<T> j0, LoJob<T> j1, unsigned tiles0) {
-    static_assert(L >= 12 && L <= 14, "low-pass tile 2^12 .. 2^14");
+__device__ __forceinline__ void lo_body(const T* src, T* dst, float scale, int do_scale, bool stream_out) {
     using V = typename P2<T>::t;
     constexpr int NT = 1 << (L - 6);
     extern __shared__ __align__(16) unsigned char smraw[];
     T* sm = reinterpret_cast<T*>(smraw);
     const int t = threadIdx.x;
-    const bool second = blockIdx.x >= tiles0;
-    if ((int)blockIdx.y >= (second ? j1.nf : j0.nf)) return;
-    const long long tile = second ? blockIdx.x - tiles0 : blockIdx.x;
-    const T* src = (second ? j1.in : j0.in) + blockIdx.y * (second ? j1.ld_in : j0.ld_in) + (tile << L);
-    T* dst = (second ? j1.out : j0.out) + blockIdx.y * (second ? j1.ld_out : j0.ld_out) + (tile << L);
-    const float scale = second ? j1.scale : j0.scale;
-    const int do_scale = second ? j1.do_scale : j0.do_scale;
-    const bool stream_out = (second ? j1.stream_out : j0.stream_out) != 0;
     V v[32];
 #pragma unroll
     for (int q = 0; q < 16; ++q) ld16_cs(src + 4 * (t + NT * q), v + 2 * q);
@@ -70,6 +61,42 @@ __global__ void __launch_bounds__(1 << (L - 6), (L == 14 ? 3 : 4))
         for (int k = 0; k < 32; ++k) v[k] = pmul(v[k], scale);
     }
     lo_tile_store<T, L>(dst, v, t, stream_out);
+}
+
+template <typename T, int L>
+__global__ void __launch_bounds__(1 << (L - 6), (L == 14 ? 3 : 4))
+    k2_lo(LoJob<T> j0, LoJob<T> j1, unsigned tiles0) {
+    static_assert(L >= 12 && L <= 14, "low-pass tile 2^12 .. 2^14");
+    const bool second = blockIdx.x >= tiles0;
+    if ((int)blockIdx.y >= (second ? j1.nf : j0.nf)) return;
+    const long long tile = second ? blockIdx.x - tiles0 : blockIdx.x;
+    const T* src = (second ? j1.in : j0.in) + blockIdx.y * (second ? j1.ld_in : j0.ld_in) + (tile << L);
+    T* dst = (second ? j1.out : j0.out) + blockIdx.y * (second ? j1.ld_out : j0.ld_out) + (tile << L);
+    lo_body<T, L>(src, dst, second ? j1.scale : j0.scale, second ? j1.do_scale : j0.do_scale,
+                  (second ? j1.stream_out : j0.stream_out) != 0);
+}
+
+// Whole transforms of 2^L points (one tile per function) of several plans in
+// one launch: job i owns the blocks [first, first + nf), one function each,
+// each run by the tile body of k2_lo.
+template <typename T> struct LoGroup {
+    LoJob<T> j;
+    long long first;
+};
+
+template <typename T, int L>
+__global__ void __launch_bounds__(1 << (L - 6), (L == 14 ? 3 : 4))
+    k2_lo_grouped(const LoGroup<T>* __restrict__ jobs, int njobs) {
+    const long long b = blockIdx.x;
+    int lo = 0, hi = njobs - 1;   // the last job starting at or before b
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (jobs[mid].first <= b) lo = mid;
+        else hi = mid - 1;
+    }
+    const LoJob<T>& j = jobs[lo].j;
+    const long long fn = b - jobs[lo].first;
+    lo_body<T, L>(j.in + fn * j.ld_in, j.out + fn * j.ld_out, j.scale, j.do_scale, j.stream_out != 0);
 }
 
 // ---------------------------------------------------------------------------
@@ -309,6 +336,55 @@ static int launch_lo2(int L, const LoJob<T>& a, const LoJob<T>* b, long long N, 
 #undef DWT_LO
     DWT_CK_LAUNCH("k2_lo");
     return DWT_OK;
+}
+
+template <typename T>
+static int lo_grouped_t(int L, const std::vector<GroupJob>& jobs, int sgn, cudaStream_t st) {
+    const bool scale = sgn < 0 && std::is_same<T, float>::value;
+    std::vector<LoGroup<T>> h;
+    long long blocks = 0;
+    for (const GroupJob& g : jobs) {
+        const long long N = g.plan->N;
+        LoGroup<T> x;
+        x.j = LoJob<T>{(const T*)g.in, (T*)g.out, g.ld_in, g.ld_out, g.batch, (float)(1.0 / (double)N), scale ? 1 : 0, 0};
+        x.first = blocks;
+        blocks += g.batch;
+        h.push_back(x);
+    }
+    if (blocks > 0x7fffffffll) {
+        set_error("grouped low pass: %lld blocks exceed one launch", blocks);
+        return DWT_EINVAL;
+    }
+    LoGroup<T>* d = nullptr;
+    if (dmalloc((void**)&d, sizeof(LoGroup<T>) * h.size(), st)) return DWT_ENOMEM;
+    DWT_CK(cudaMemcpyAsync(d, h.data(), sizeof(LoGroup<T>) * h.size(), cudaMemcpyHostToDevice, st));
+    const size_t smem = (((size_t)1 << L) + ((size_t)1 << (L - 4))) * sizeof(T);
+    int rc = DWT_OK;
+#define DWT_LOG(LL)                                                                       \
+    case LL: {                                                                            \
+        auto k = k2_lo_grouped<T, LL>;                                                    \
+        if ((rc = attr_smem(k, smem))) break;                                             \
+        LaunchScope ls("grouped_lo", st);                                                 \
+        k<<<(unsigned)blocks, 1 << (LL - 6), smem, st>>>(d, (int)h.size());               \
+        break;                                                                            \
+    }
+    switch (L) {
+        DWT_LOG(12)
+        DWT_LOG(13)
+        DWT_LOG(14)
+        default: set_error("low-pass tile"); rc = DWT_EUNSUPPORTED;
+    }
+#undef DWT_LOG
+    dfree(d, st);
+    if (rc) return rc;
+    DWT_CK_LAUNCH("k2_lo_grouped");
+    return DWT_OK;
+}
+
+// whole transforms of 2^L points, L = 12 .. 14, of several plans in one launch
+int p2_lo_grouped(int L, const std::vector<GroupJob>& jobs, dwt_dtype t, int sgn, cudaStream_t st) {
+    if (jobs.empty()) return DWT_OK;
+    return t == DWT_F32 ? lo_grouped_t<float>(L, jobs, sgn, st) : lo_grouped_t<int>(L, jobs, sgn, st);
 }
 
 template <typename T>

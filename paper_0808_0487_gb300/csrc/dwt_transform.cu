@@ -288,11 +288,9 @@ template <int P> constexpr int pass_maxnreg() { return P > 13 ? 160 : 96; }
 template <int P> constexpr long long pass_max_threads() { return P > 13 ? 384 : 512; }
 
 template <int P, typename T, typename TI, int SGN, int KM>
-__global__ void __maxnreg__(pass_maxnreg<P>()) k_pass(PassArgs a) {
+__device__ __forceinline__ void pass_body(const PassArgs& a, long long tile, long long fn) {
     extern __shared__ __align__(16) unsigned char smraw[];
     T* sm = reinterpret_cast<T*>(smraw);
-    const long long fn = blockIdx.y;
-    const long long tile = blockIdx.x;
     const long long lo0 = (tile % a.nlo) << a.wlog;
     const long long base = lo0 + (tile / a.nlo) * a.SR;
     const int ncols = (int)min((long long)a.Wc, a.S - lo0);
@@ -331,6 +329,33 @@ __global__ void __maxnreg__(pass_maxnreg<P>()) k_pass(PassArgs a) {
             }
         }
     }
+}
+
+template <int P, typename T, typename TI, int SGN, int KM>
+__global__ void __maxnreg__(pass_maxnreg<P>()) k_pass(PassArgs a) {
+    pass_body<P, T, TI, SGN, KM>(a, blockIdx.x, blockIdx.y);
+}
+
+// One pass of several plans' transforms in one launch: job i owns the blocks
+// [first, first + ntile * nf) (tile fastest).  Each block runs exactly the tile
+// body of k_pass, so every element is computed as by the plan's own launch.
+struct GroupPass {
+    PassArgs a;
+    long long ntile, first;
+};
+
+template <int P, typename T, typename TI, int SGN, int KM>
+__global__ void __maxnreg__(pass_maxnreg<P>()) k_pass_grouped(const GroupPass* __restrict__ jobs, int njobs) {
+    const long long b = blockIdx.x;
+    int lo = 0, hi = njobs - 1;   // the last job starting at or before b
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (jobs[mid].first <= b) lo = mid;
+        else hi = mid - 1;
+    }
+    const GroupPass& g = jobs[lo];
+    const long long local = b - g.first;
+    pass_body<P, T, TI, SGN, KM>(g.a, local % g.ntile, local / g.ntile);
 }
 
 // ---------------------------------------------------------------------------
@@ -740,6 +765,152 @@ int run_transform_digits(dwt_plan_s* Pl, const void* in, void* out, int batch, l
         case 23: return digits_p<23>(Pl, in, out, batch, ld_in, ld_out, in_t, out_t, d0, nd, sgn, st);
         case 29: return digits_p<29>(Pl, in, out, batch, ld_in, ld_out, in_t, out_t, d0, nd, sgn, st);
         case 31: return digits_p<31>(Pl, in, out, batch, ld_in, ld_out, in_t, out_t, d0, nd, sgn, st);
+        default: set_error("unsupported p"); return DWT_EUNSUPPORTED;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// grouped transforms: pass t of every job in one launch of k_pass_grouped
+
+template <int P, typename T, typename TI, int SGN>
+static int launch_grouped(const std::vector<GroupPass>& h, long long blocks, int threads, size_t smem, const char* fam,
+                          cudaStream_t st) {
+    if (h.empty()) return DWT_OK;
+    if (blocks > 0x7fffffffll) {
+        set_error("grouped pass: %lld blocks exceed one launch", blocks);
+        return DWT_EINVAL;
+    }
+    constexpr int KM = KMax<P, T>::v;
+    auto kern = k_pass_grouped<P, T, TI, SGN, KM>;
+    int rc = set_smem(kern, smem);
+    if (rc) return rc;
+    GroupPass* d = nullptr;
+    if (dmalloc((void**)&d, sizeof(GroupPass) * h.size(), st)) return DWT_ENOMEM;
+    DWT_CK(cudaMemcpyAsync(d, h.data(), sizeof(GroupPass) * h.size(), cudaMemcpyHostToDevice, st));
+    {
+        LaunchScope ls(fam, st);
+        kern<<<(unsigned)blocks, threads, smem, st>>>(d, (int)h.size());
+    }
+    dfree(d, st);
+    DWT_CK_LAUNCH("k_pass_grouped");
+    return DWT_OK;
+}
+
+// The jobs' transforms by their plans' pass plans, pass t of all jobs in one
+// launch; the same tile body, geometry and scaling as transform_pp, so every
+// element equals the one of the job's own call.
+template <int P, typename T, typename TI, int SGN>
+static int grouped_t(const std::vector<GroupJob>& js, cudaStream_t st) {
+    const Tw tw = make_tw(P);
+    const bool scale = SGN < 0 && !std::is_same<T, int>::value;
+    constexpr int KM = KMax<P, T>::v;
+    std::vector<const PassPlan*> pps;
+    int qmax = 0;
+    for (const GroupJob& j : js) {
+        pps.push_back(&pass_plan(j.plan, sizeof(T)));
+        qmax = std::max(qmax, pps.back()->q);
+    }
+    for (int t = 0; t < qmax; ++t) {
+        std::vector<GroupPass> h;
+        long long blocks = 0;
+        int threads = 32;
+        size_t smem = 0;
+        for (size_t i = 0; i < js.size(); ++i) {
+            const PassPlan& pp = *pps[i];
+            const GroupJob& j = js[i];
+            if (t >= pp.q || j.batch <= 0) continue;
+            const PassGeom& g = pp.g[t];
+            GroupPass gp;
+            if (t == 0) {
+                gp.a = pass_args(g, j.in, j.out, j.ld_in, j.ld_out, tw);
+                if (scale && pp.q == 1) {
+                    gp.a.do_scale = 1;
+                    gp.a.scale = 1.0 / (double)j.plan->N;
+                }
+            } else {
+                gp.a = pass_args(g, j.out, j.out, j.ld_out, j.ld_out, tw);
+                if (scale && t == pp.q - 1) {
+                    gp.a.do_scale = 1;
+                    gp.a.scale = 1.0 / (double)j.plan->N;
+                }
+            }
+            gp.ntile = g.ntile;
+            gp.first = blocks;
+            blocks += g.ntile * (long long)j.batch;
+            h.push_back(gp);
+            threads = std::max(threads, pass_threads<P, KM>(g));
+            smem = std::max(smem, spad_bytes<T>(g.R << g.wlog));
+        }
+        const int rc = t == 0 ? launch_grouped<P, T, TI, SGN>(h, blocks, threads, smem, "grouped_pass", st)
+                              : launch_grouped<P, T, T, SGN>(h, blocks, threads, smem, "grouped_pass", st);
+        if (rc) return rc;
+    }
+    return DWT_OK;
+}
+
+template <int P>
+static int grouped_p(const std::vector<GroupJob>& js, dwt_dtype in_t, dwt_dtype out_t, int sgn, cudaStream_t st) {
+    if constexpr (P == 2) {
+        if (in_t == DWT_F32)
+            return sgn < 0 ? grouped_t<2, float, float, -1>(js, st) : grouped_t<2, float, float, +1>(js, st);
+        if (in_t == DWT_F64)
+            return sgn < 0 ? grouped_t<2, double, double, -1>(js, st) : grouped_t<2, double, double, +1>(js, st);
+        return sgn < 0 ? grouped_t<2, int, int, -1>(js, st) : grouped_t<2, int, int, +1>(js, st);
+    } else {
+        if (out_t == DWT_C64) {
+            if (sgn < 0)
+                return in_t == DWT_F32 ? grouped_t<P, float2, float, -1>(js, st)
+                                       : grouped_t<P, float2, float2, -1>(js, st);
+            return grouped_t<P, float2, float2, +1>(js, st);
+        }
+        if (sgn < 0)
+            return in_t == DWT_F64 ? grouped_t<P, double2, double, -1>(js, st)
+                                   : grouped_t<P, double2, double2, -1>(js, st);
+        return grouped_t<P, double2, double2, +1>(js, st);
+    }
+}
+
+// Grouped transforms of jobs that share p and the element types (checked by
+// the caller).  p = 2 jobs that their own call sends to the register-tile
+// kernels go there too: m = 12 .. 14 as one grouped low pass per tile size,
+// larger ones one call each; all other jobs run the generic passes grouped.
+int run_transform_grouped(const std::vector<GroupJob>& jobs, dwt_dtype in_t, dwt_dtype out_t, int sgn,
+                          cudaStream_t st) {
+    if (jobs.empty()) return DWT_OK;
+    const int p = jobs[0].plan->p;
+    std::vector<GroupJob> generic, lo[3];
+    for (const GroupJob& j : jobs) {
+        if (j.batch <= 0) continue;
+        if (p == 2 && (in_t == DWT_F32 || in_t == DWT_I32) && p2_fast_ok(j.plan->m) && aligned16(j.in, j.ld_in, 4) &&
+            aligned16(j.out, j.ld_out, 4)) {
+            if (j.plan->m <= 14) {
+                lo[j.plan->m - 12].push_back(j);
+            } else {
+                const int rc = p2_transform(j.plan, j.in, j.out, j.batch, j.ld_in, j.ld_out, in_t, sgn, st);
+                if (rc) return rc;
+            }
+            continue;
+        }
+        generic.push_back(j);
+    }
+    for (int L = 12; L <= 14; ++L)
+        if (!lo[L - 12].empty()) {
+            const int rc = p2_lo_grouped(L, lo[L - 12], in_t, sgn, st);
+            if (rc) return rc;
+        }
+    if (generic.empty()) return DWT_OK;
+    switch (p) {
+        case 2: return grouped_p<2>(generic, in_t, out_t, sgn, st);
+        case 3: return grouped_p<3>(generic, in_t, out_t, sgn, st);
+        case 5: return grouped_p<5>(generic, in_t, out_t, sgn, st);
+        case 7: return grouped_p<7>(generic, in_t, out_t, sgn, st);
+        case 11: return grouped_p<11>(generic, in_t, out_t, sgn, st);
+        case 13: return grouped_p<13>(generic, in_t, out_t, sgn, st);
+        case 17: return grouped_p<17>(generic, in_t, out_t, sgn, st);
+        case 19: return grouped_p<19>(generic, in_t, out_t, sgn, st);
+        case 23: return grouped_p<23>(generic, in_t, out_t, sgn, st);
+        case 29: return grouped_p<29>(generic, in_t, out_t, sgn, st);
+        case 31: return grouped_p<31>(generic, in_t, out_t, sgn, st);
         default: set_error("unsupported p"); return DWT_EUNSUPPORTED;
     }
 }
