@@ -61,7 +61,7 @@ typedef enum { DWT_WEIGHT_NONE = 0, DWT_WEIGHT_INV_SQ_WAVENUMBER = 1 } dwt_weigh
 /* plan flags */
 #define DWT_PLAN_TRANSFORM_ONLY 1u  /* build no K(C) tables: forward/inverse/points/k->H only */
 #define DWT_PLAN_KEEP_INDEX_MAP 2u  /* keep the coset tables needed by dwt_index_to_wavenumber */
-#define DWT_PLAN_TUNE 4u            /* time the candidate pass splits of the generic transform, keep the fastest */
+#define DWT_PLAN_TUNE 4u            /* measure the plan's launch choices (see dwt_plan), keep the fastest */
 
 typedef struct dwt_plan_s *dwt_plan_t;
 
@@ -80,14 +80,21 @@ typedef struct dwt_plan_s *dwt_plan_t;
  * rows of C do not span F_p^m, DWT_EUNSUPPORTED (plan still created) when a
  * least nu reaches 255 or a weight denominator exceeds 64 bits.  On any other
  * failure *plan is NULL.  Synchronises "stream".
- * DWT_PLAN_TUNE: the digits of the generic transform passes (used for p > 2,
- * and for p = 2 outside 12 <= m <= 14, 16 <= m <= 24) may be grouped in any
- * way (Sec. 2.2); with this flag the plan times the candidate groupings of the
- * FP32 form (real in, complex out for p > 2) on a scratch function of N
- * points and keeps the fastest, for N (4 + element size) <= 1 GiB.  Results
- * are kept per process and per device, and appended to the file named by the
- * environment variable DWT_TUNE_CACHE when it is set (one JSON object per
- * line), from which later processes read them instead of measuring again.
+ * DWT_PLAN_TUNE: the digits of the transform may be grouped into passes in
+ * any way (Sec. 2.2); with this flag the plan times, on scratch functions of N
+ * points in the FP32 form (real in, complex out for p > 2), for
+ * N (4 + element size) <= 1 GiB, and keeps the fastest of:
+ *   - the grouping of the generic passes (used for p > 2, and for p = 2
+ *     outside 12 <= m <= 14, 16 <= m <= 24) and the functions per
+ *     L2-resident group of those passes;
+ *   - p = 2, 16 <= m <= 19: the digits of the register-tile low pass;
+ *   - p = 2, m = 14 or 18 <= m <= 24: whether DWT_ALGO_AUTO runs the
+ *     split-BF16 tensor-core form (results then differ from the butterflies'
+ *     by rounding, within the same tolerance).
+ * dwt_plan_tuned reports the choices.  Results are kept per process and per
+ * device, and appended to the file named by the environment variable
+ * DWT_TUNE_CACHE when it is set (one JSON object per line), from which later
+ * processes read them instead of measuring again.
  */
 int dwt_plan(int p, int m, int s, const uint8_t *C, unsigned flags, void *stream, dwt_plan_t *plan);
 /* The same call under its earlier name (identical arguments and behaviour). */
@@ -113,6 +120,12 @@ int dwt_plan_info(dwt_plan_t plan, int *p, int *m, int *s, long long *N, int *ta
  * digits and wc[t] columns (consecutive low indices per row) in pass t, from
  * the lowest digits up.  digits and wc: host int [32]. */
 int dwt_plan_passes(dwt_plan_t plan, int elem_bytes, int *q, int *digits, int *wc);
+
+/* The measured choices of a DWT_PLAN_TUNE plan (0 where the heuristic stays):
+ * *lo_digits = digits of the p = 2 register-tile low pass, *tc = 1 when
+ * DWT_ALGO_AUTO runs the tensor-core form, *group_bytes = bytes of functions
+ * per L2-resident group of the generic passes.  Any pointer may be NULL. */
+int dwt_plan_tuned(dwt_plan_t plan, int *lo_digits, int *tc, long long *group_bytes);
 
 /* The heuristic split that dwt_plan_create gives a plan (before any tuning),
  * computed on the host without a device: fewest passes within the 64 KB tile

@@ -77,6 +77,7 @@ _SIGS = {
     "dwt_index_to_wavenumber": (_I, [_VP, _VP, _VP, _LL, _VP]),
     "dwt_forward": (_I, [_VP, _VP, _VP, _I, _LL, _LL, _I, _I, _I, _VP]),
     "dwt_inverse": (_I, [_VP, _VP, _VP, _I, _LL, _LL, _I, _I, _I, _VP]),
+    "dwt_plan_tuned": (_I, [_VP, _VP, _VP, _VP]),
     "dwt_forward_grouped": (_I, [_VP, _I, _I, _I, _VP]),
     "dwt_inverse_grouped": (_I, [_VP, _I, _I, _I, _VP]),
     "dwt_forward_digits": (_I, [_VP, _VP, _VP, _I, _LL, _LL, _I, _I, _I, _I, _VP]),
@@ -236,6 +237,15 @@ def dwt_plan_passes(plan, elem_bytes):
     w = (_I * 32)()
     _check(lib().dwt_plan_passes(plan.handle, elem_bytes, ctypes.byref(q), d, w))
     return [(d[t], w[t]) for t in range(q.value)]
+
+
+def dwt_plan_tuned(plan):
+    """The measured choices of a DWT_PLAN_TUNE plan: dict(lo_digits, tc, group_bytes); 0 = heuristic."""
+    lo = _I()
+    tc = _I()
+    gb = _LL()
+    _check(lib().dwt_plan_tuned(plan.handle, ctypes.byref(lo), ctypes.byref(tc), ctypes.byref(gb)))
+    return {"lo_digits": lo.value, "tc": tc.value, "group_bytes": gb.value}
 
 
 def dwt_pass_plan_for(p, m, elem_bytes, min_tiles=304):

@@ -486,6 +486,17 @@ int dwt_plan_passes(dwt_plan_t P, int elem_bytes, int* q, int* digits, int* wc) 
     return DWT_OK;
 }
 
+int dwt_plan_tuned(dwt_plan_t P, int* lo_digits, int* tc, long long* group_bytes) {
+    if (!P) {
+        set_error("dwt_plan_tuned: NULL plan");
+        return DWT_EINVAL;
+    }
+    if (lo_digits) *lo_digits = P->tuned_lo;
+    if (tc) *tc = P->tuned_tc;
+    if (group_bytes) *group_bytes = P->tuned_group_bytes;
+    return DWT_OK;
+}
+
 int dwt_plan_destroy(dwt_plan_t P) {
     if (!P) return DWT_OK;
     cudaDeviceSynchronize();
@@ -626,6 +637,9 @@ static int transform_common(dwt_plan_t P, const void* in, void* out, int batch, 
         set_error("unknown algo %d", (int)algo);
         return DWT_EINVAL;
     }
+    // a tuned plan's measured choice for DWT_ALGO_AUTO
+    if (algo == DWT_ALGO_AUTO && P->tuned_tc && P->p == 2 && in_t == DWT_F32 && tc_ok(P->m))
+        return run_tc_transform(P, (const float*)in, (float*)out, batch, ld_in, ld_out, sgn, (cudaStream_t)stream);
     return run_transform(P, in, out, batch, ld_in, ld_out, in_t, out_t, sgn, (cudaStream_t)stream);
 }
 

@@ -97,6 +97,10 @@ struct dwt_plan_s {
     // pass decompositions by element size (4, 8, 16 bytes)
     dwt::PassPlan passes[3];
     long long min_tiles = 1;        // tiles per function the high passes aim for (two per SM)
+    // measured choices of DWT_PLAN_TUNE (0: the heuristic)
+    int tuned_lo = 0;               // p = 2 transforms: digits of the register-tile low pass
+    int tuned_tc = 0;               // p = 2 FP32 DWT_ALGO_AUTO: 1 = the split-BF16 tensor-core form
+    long long tuned_group_bytes = 0;   // generic passes: bytes of functions per L2-resident group
     // device slots, streams and events of dwt_interpolate_host (first use)
     dwt::HostStage* host = nullptr;
     // kernel spline tables (dwt_spline_prepare): W_K [N], then R~_d - [H=0] and E~_j, [2s][N], FP64

@@ -309,6 +309,14 @@ static int attr_smem(F* k, size_t bytes) {
 // otherwise a low pass of L = min(14, m - 4) digits and a high pass of B = m - L
 // digits, 4 <= B <= 10 (16 <= m <= 24)
 static int p2_low_digits(int m) { return m <= 14 ? m : std::min(14, m - 4); }
+
+// the low-pass digits of a plan's transform: a measured choice (DWT_PLAN_TUNE)
+// when one lies in the kernels' range 12 <= L <= 14, 4 <= m - L <= 10
+static int p2_lo_digits_of(const dwt_plan_s* Pl) {
+    const int m = Pl->m, L = Pl->tuned_lo;
+    if (m >= 16 && L >= 12 && L <= 14 && m - L >= 4 && m - L <= 10) return L;
+    return p2_low_digits(m);
+}
 bool p2_fast_ok(int m) { return (m >= 12 && m <= 14) || (m >= 16 && m <= 24); }
 
 template <typename T>
@@ -449,7 +457,7 @@ static int p2_transform_t(dwt_plan_s* Pl, const T* in, T* out, int batch, long l
             if (rc) return rc;
             continue;
         }
-        const int L = p2_low_digits(m);
+        const int L = p2_lo_digits_of(Pl);
         int rc = launch_lo<T>(L, src, dst, ld_in, ld_out, nf, N, 1.f, 0, sgn < 0 ? "p2_lo_fwd" : "p2_lo_inv", st);
         if (rc) return rc;
         HiArgs a{};

@@ -672,7 +672,7 @@ static int transform_pp(dwt_plan_s* Pl, const PassPlan& pp, double scale_by_n, c
                         long long ld_in, long long ld_out, cudaStream_t st) {
     const Tw tw = make_tw(P);
     const long long fbytes = Pl->N * (long long)sizeof(T);
-    int G = (int)std::max(1ll, kL2Group / fbytes);
+    int G = (int)std::max(1ll, (Pl->tuned_group_bytes > 0 ? Pl->tuned_group_bytes : kL2Group) / fbytes);
     G = std::min(G, 65535);
     const bool scale = SGN < 0 && !std::is_same<T, int>::value;
     for (int f0 = 0; f0 < batch; f0 += G) {

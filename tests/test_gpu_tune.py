@@ -68,3 +68,38 @@ def test_tune_cache_file_across_processes(tmp_path):
     mine = [x for x in lines if x["p"] == 3 and x["m"] == 11 and x["elem"] == 8]
     assert len(mine) == 1                        # measured once
     assert mine[0]["digits"] == [d for d, _ in first] and mine[0]["wc"] == [w for _, w in first]
+
+
+@pytest.mark.parametrize("p,m", [(2, 17), (2, 18), (3, 9)])
+def test_tuned_choices_keep_results(dwt, dev, orc, p, m, tmp_path, monkeypatch):
+    """The measured launch choices (p = 2 low-pass digits, tensor-core form for
+    DWT_ALGO_AUTO, functions per L2 group) leave the transform within the same
+    tolerance of the oracle, and are reported in the kernels' ranges."""
+    monkeypatch.setenv("DWT_TUNE_CACHE", str(tmp_path / "tune.jsonl"))
+    N = p ** m
+    C = S.small_net(p, m, 2, index=60 + m)
+    plan = dwt.dwt_plan_create(p, m, 2, C, dwt.DWT_PLAN_TRANSFORM_ONLY | dwt.DWT_PLAN_TUNE)
+    ch = dwt.dwt_plan_tuned(plan)
+    if p == 2 and m <= 19:
+        assert max(12, m - 10) <= ch["lo_digits"] <= min(14, m - 4)
+    else:
+        assert ch["lo_digits"] == 0
+    assert ch["tc"] in (0, 1) and (ch["tc"] == 0 or (p == 2 and (m == 14 or 18 <= m <= 24)))
+    assert ch["group_bytes"] in (0, 16 << 20, 128 << 20)
+    line = [json.loads(x) for x in (tmp_path / "tune.jsonl").read_text().splitlines() if x.strip()][-1]
+    assert line["lo"] == ch["lo_digits"] and line["tc"] == ch["tc"] and line["group_mb"] << 20 == ch["group_bytes"]
+    f = orc.eval_exp(p, m, orc.net_points(p, m, C))
+    fin = torch.tensor(np.tile(f.astype(np.float32), (3, 1)), device=dev)
+    if p == 2:
+        out = torch.empty((3, N), device=dev)
+        dwt.dwt_forward(plan, fin, out, 3, N, N, dwt.DWT_F32, dwt.DWT_F32)
+        ref = orc.fwt(p, m, f).real
+        for b in range(3):
+            assert rel_l2(out[b].cpu().numpy(), ref) < 1e-5
+        back = torch.empty_like(out)
+        dwt.dwt_inverse(plan, out, back, 3, N, N, dwt.DWT_F32, dwt.DWT_F32)
+        assert rel_l2(back[0].cpu().numpy(), f) < 1e-5
+    else:
+        out = torch.empty((3, 2 * N), device=dev)
+        dwt.dwt_forward(plan, fin, out, 3, N, N, dwt.DWT_F32, dwt.DWT_C64)
+        assert rel_l2(_cplx(out[2].cpu().numpy()), orc.fwt(p, m, f)) < 1e-5
