@@ -537,6 +537,19 @@ def run_other_configs(dwt, dev, stream, timed, steps):
         ms, _ = timed(fn, steps)
         r[k + "_direct_calls_points_per_s"] = N * steps / (ms / 1e3)
     r["passes"] = dwt.dwt_plan_passes(plan, 8)
+    r["tuned"] = dwt.dwt_plan_tuned(plan)
+    # 32 such functions per call through the same tuned plan: one transform
+    # fills less than one wave of the GPU, a batch fills several
+    del x, y, z
+    xb = torch.ones((32, ld), dtype=torch.float32, device=dev)
+    yb = torch.empty((32, ld), dtype=torch.complex64, device=dev)
+
+    def fwb():
+        dwt.dwt_forward(plan, xb, yb, 32, ld, ld, dwt.DWT_F32, dwt.DWT_C64, stream=stream)
+
+    ms, _ = timed(fwb, steps)
+    r["forward_batch32_points_per_s"] = 32 * N * steps / (ms / 1e3)
+    del xb, yb
     out["p3_m13_s8"] = r
     return out
 

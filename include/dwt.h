@@ -85,8 +85,9 @@ typedef struct dwt_plan_s *dwt_plan_t;
  * points in the FP32 form (real in, complex out for p > 2), for
  * N (4 + element size) <= 1 GiB, and keeps the fastest of:
  *   - the grouping of the generic passes (used for p > 2, and for p = 2
- *     outside 12 <= m <= 14, 16 <= m <= 24) and the functions per
- *     L2-resident group of those passes;
+ *     outside 12 <= m <= 14, 16 <= m <= 24) and the functions per group of
+ *     those passes (16, 48 or 128 MB of functions kept in L2 between the
+ *     passes of a group, or 1 GB: each pass over the whole batch at once);
  *   - p = 2, 16 <= m <= 19: the digits of the register-tile low pass;
  *   - p = 2, m = 14 or 18 <= m <= 24: whether DWT_ALGO_AUTO runs the
  *     split-BF16 tensor-core form (results then differ from the butterflies'

@@ -6,8 +6,9 @@
 // FP32 form (real to complex for p > 2):
 //  - the digit split of the generic passes: every candidate split, each with
 //    the heuristic row width and with half of it;
-//  - the functions per L2-resident group of the generic passes (16, 48 or
-//    128 MB of functions between the passes of a group);
+//  - the functions per group of the generic passes (16, 48, 128 MB of
+//    functions between the passes of a group, L2-resident, or 1 GB: every
+//    pass over the whole batch in one launch);
 //  - p = 2, 16 <= m <= 19: the digits of the register-tile low pass (the high
 //    pass takes the rest);
 //  - p = 2 where the split-BF16 tensor-core form exists: whether
@@ -263,7 +264,7 @@ int tune_passes(dwt_plan_s* P, long long min_tiles, cudaStream_t st) {
             long long best_g = 0;
             float gbest = -1.f;
             int last_G = -1;
-            for (long long mb : {48ll, 16ll, 128ll}) {
+            for (long long mb : {48ll, 16ll, 128ll, 1024ll}) {
                 const long long bytes = mb << 20;
                 const int G = (int)std::max(1ll, bytes / fbytes);
                 if (G == last_G || (G >= nbatch && last_G >= nbatch)) continue;

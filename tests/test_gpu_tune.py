@@ -85,7 +85,7 @@ def test_tuned_choices_keep_results(dwt, dev, orc, p, m, tmp_path, monkeypatch):
     else:
         assert ch["lo_digits"] == 0
     assert ch["tc"] in (0, 1) and (ch["tc"] == 0 or (p == 2 and (m == 14 or 18 <= m <= 24)))
-    assert ch["group_bytes"] in (0, 16 << 20, 128 << 20)
+    assert ch["group_bytes"] in (0, 16 << 20, 128 << 20, 1024 << 20)
     line = [json.loads(x) for x in (tmp_path / "tune.jsonl").read_text().splitlines() if x.strip()][-1]
     assert line["lo"] == ch["lo_digits"] and line["tc"] == ch["tc"] and line["group_mb"] << 20 == ch["group_bytes"]
     f = orc.eval_exp(p, m, orc.net_points(p, m, C))
