@@ -13,8 +13,8 @@
 // applied with tables over groups of base-p digits whose entries are vectors
 // of 4-bit digits in a 64-bit word; two such vectors add digit-wise mod p
 // without carries (each digit sum is at most 2p - 2 < 16), with the reduction
-// done on all digits at once.  A net of one tile runs in one CTA, larger
-// ones in the tiled form below.  Nets outside m <= 16 and the shared-memory
+// done on all digits at once.  A net of at most one small tile runs in one
+// CTA, larger ones in the tiled form below.  Nets outside m <= 16 and the shared-memory
 // limits of the coarse tree (p = 3: m <= 16, p = 5: m <= 11, p = 7: m <= 8),
 // or with dependent rows, use the per-digit programme.
 #include <stdlib.h>
@@ -37,6 +37,15 @@ template <int P> struct TreeShape;
 template <> struct TreeShape<3> { static constexpr int LB = 8, TS = 6561, G = 5, PG = 243; };
 template <> struct TreeShape<5> { static constexpr int LB = 5, TS = 3125, G = 3, PG = 125; };
 template <> struct TreeShape<7> { static constexpr int LB = 4, TS = 2401, G = 2, PG = 49; };
+
+constexpr int cpow_i(int b, int e) { return e == 0 ? 1 : b * cpow_i(b, e - 1); }
+
+// the smaller tiles of the tiled form for nets of fewer than 64 full tiles:
+// 3^5, 5^3, 7^2 labels, one CTA of NT threads each
+template <int P> struct SmallTile;
+template <> struct SmallTile<3> { static constexpr int LB = 5, NT = 256; };
+template <> struct SmallTile<5> { static constexpr int LB = 3, NT = 128; };
+template <> struct SmallTile<7> { static constexpr int LB = 2, NT = 64; };
 
 // a linear map: table[g][x] = image of the digit group g with value x, as packed digits
 struct MapP {
@@ -98,13 +107,15 @@ __device__ __forceinline__ unsigned sib_min(const uint8_t* S, uint32_t v) {
 }
 
 // ---------------------------------------------------------------------------
-// The tiled form for nets of more than one tile.  Tiles of p^LB labels (one
-// CTA of kThreadsP threads each); the levels 0 .. LB of every tile in a global
-// array laid out level after level over all N labels; the levels above,
-// built from the tile minima (level LB) in every CTA's shared memory.
+// The tiled form for nets of more than one tile.  Tiles of p^LB labels, one
+// CTA each: 3^8, 5^5, 7^4 labels (512 threads), or for nets of fewer than 64
+// such tiles the smaller 3^5, 5^3, 7^2 (SmallTile), so that more CTAs share a
+// coordinate; the levels 0 .. LB of every tile in a global array laid out
+// level after level over all N labels; the levels above, built from the tile
+// minima (level LB) in every CTA's shared memory.
 //
 // Backward sweep, one cooperative launch with two grid-wide waits per
-// coordinate j = s-1 .. 0:
+// coordinate j = s-2 .. 0 (T_{s-1} and k_{s-1} have a closed form):
 //   up    leaves T'[U] = T_{j+1}[Q_j(U)] of every tile and the tile's levels;
 //   wait
 //   down  the coarse tree, A from the tile root to the leaves, T_j =
@@ -137,10 +148,17 @@ struct LevelsP {
     uint32_t pw[33], toff[17], goff[17], per[17], coff[33];
 };
 
+// a tile of the tiled form: P^LB labels
+template <int P, int LB_>
+struct TileP {
+    static constexpr int LB = LB_;
+    static constexpr int TS = cpow_i(P, LB_);
+};
+
 // dynamic shared memory of the backward sweep: map | tile levels | A, A' | ok | coarse levels
-template <int P>
+template <int P, int LB>
 struct SmemP {
-    static constexpr int TS = TreeShape<P>::TS;
+    static constexpr int TS = TileP<P, LB>::TS;
     static constexpr size_t kMap = sizeof(MapP);
     static constexpr size_t kLev = ((size_t)2 * TS + 15) & ~(size_t)15;
     static constexpr size_t kA = ((size_t)2 * TS * 2 + 15) & ~(size_t)15;
@@ -189,9 +207,9 @@ __device__ bool grid_wait_p(unsigned* flags, unsigned& target, int* ok) {
     return *ok != 0;
 }
 
-template <int P>
+template <int P, int LB>
 __device__ void levels_init(LevelsP* L, long long N, int m) {
-    using SH = TreeShape<P>;
+    using SH = TileP<P, LB>;
     if (threadIdx.x == 0) {
         const long long nLB = N / SH::TS;
         long long w = 1;
@@ -210,14 +228,14 @@ __device__ void levels_init(LevelsP* L, long long N, int m) {
     }
 }
 
-template <int P>
-__device__ __forceinline__ void tileP_up(const ArgsP& a, uint32_t tile, bool first, const unsigned long long (*q)[256],
+template <int P, int LB>
+__device__ __forceinline__ void tileP_up(const ArgsP& a, uint32_t tile, const unsigned long long (*q)[256],
                                          uint8_t* sl, const LevelsP* L) {
-    using SH = TreeShape<P>;
+    using SH = TileP<P, LB>;
     const uint32_t base = tile * (uint32_t)SH::TS;
     for (int e = threadIdx.x; e < SH::TS; e += blockDim.x) {
         const uint32_t U = base + (uint32_t)e;
-        const uint8_t v = first ? (U == 0 ? 0 : kInfP) : a.T[applyP<P>(q, U, a.ng, a.m)];
+        const uint8_t v = a.T[applyP<P>(q, U, a.ng, a.m)];
         sl[e] = v;
         a.lev[U] = v;
     }
@@ -238,10 +256,10 @@ __device__ __forceinline__ void tileP_up(const ArgsP& a, uint32_t tile, bool fir
     }
 }
 
-template <int P>
+template <int P, int LB>
 __device__ __forceinline__ void tileP_down(const ArgsP& a, uint32_t tile, int j, const uint8_t* cl, uint8_t* sl,
                                            uint16_t* a0, uint16_t* a1, const LevelsP* L, unsigned& mx) {
-    using SH = TreeShape<P>;
+    using SH = TileP<P, LB>;
     const long long N = a.N;
     const int m = a.m;
     const uint32_t base = tile * (uint32_t)SH::TS;
@@ -322,10 +340,10 @@ __device__ __forceinline__ void tileP_down(const ArgsP& a, uint32_t tile, int j,
     }
 }
 
-template <int P>
-__global__ void __launch_bounds__(kThreadsP) k_treep_bwd(ArgsP a) {
-    using SH = TreeShape<P>;
-    using L = SmemP<P>;
+template <int P, int LB, int NT>
+__global__ void __launch_bounds__(NT) k_treep_bwd(ArgsP a) {
+    using SH = TileP<P, LB>;
+    using L = SmemP<P, LB>;
     extern __shared__ __align__(16) unsigned char sm[];
     unsigned long long (*q)[256] = reinterpret_cast<unsigned long long (*)[256]>(sm);
     uint8_t* sl = sm + L::kMap;
@@ -338,13 +356,29 @@ __global__ void __launch_bounds__(kThreadsP) k_treep_bwd(ArgsP a) {
     const long long nLB = N / SH::TS;
     const int top = a.m - SH::LB;
     unsigned target = 0, mx = 0;
-    levels_init<P>(lv, N, a.m);
+    levels_init<P, LB>(lv, N, a.m);
+    __syncthreads();   // per-level constants
     for (int j = a.s - 1; j >= 0; --j) {
-        const bool first = j == a.s - 1;
-        if (!first) load_mapP<P>(q, a.Q + j, a.ng);
+        if (j == a.s - 1) {
+            // T_s is 0 at label 0 only, so T_{s-1}(U) = (position of the highest
+            // nonzero digit of U) + 1 with the reading running down to label 0:
+            // k_{s-1}(U) = U
+            for (long long v = (long long)blockIdx.x * blockDim.x + threadIdx.x; v < N;
+                 v += (long long)gridDim.x * blockDim.x) {
+                const uint32_t U = (uint32_t)v;
+                int n = 0;
+                while (n < a.m && U >= lv->pw[n]) ++n;
+                a.T[U] = (uint8_t)n;
+                a.K[(size_t)j * N + U] = U;
+                if (j == 0) mx = max(mx, (unsigned)n);
+            }
+            if (j > 0 && !grid_wait_p(a.flags, target, ok)) return;
+            continue;
+        }
+        load_mapP<P>(q, a.Q + j, a.ng);
         __syncthreads();
         for (long long tl = blockIdx.x; tl < nLB; tl += gridDim.x) {
-            tileP_up<P>(a, (uint32_t)tl, first, q, sl, lv);
+            tileP_up<P, LB>(a, (uint32_t)tl, q, sl, lv);
             __syncthreads();
         }
         if (!grid_wait_p(a.flags, target, ok)) return;
@@ -366,7 +400,7 @@ __global__ void __launch_bounds__(kThreadsP) k_treep_bwd(ArgsP a) {
             n = np;
         }
         for (long long tl = blockIdx.x; tl < nLB; tl += gridDim.x) {
-            tileP_down<P>(a, (uint32_t)tl, j, cl, sl, a0, a1, lv, mx);
+            tileP_down<P, LB>(a, (uint32_t)tl, j, cl, sl, a0, a1, lv, mx);
             __syncthreads();
         }
         if (j > 0 && !grid_wait_p(a.flags, target, ok)) return;
@@ -739,12 +773,12 @@ int treep_one(dwt_plan_s* Pl, const std::vector<MapP>& Imap, const std::vector<M
 
 // Largest cooperative grid of the backward sweep (see the p = 2 form);
 // DWT_TILE_GRID, if set to a positive number, caps it.
-template <int P>
+template <int P, int LB, int NT>
 int treep_grid(long long tiles, size_t smem) {
     int dev = 0, sms = 0, occ = 0;
     if (cudaGetDevice(&dev) != cudaSuccess ||
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_treep_bwd<P>, kThreadsP, smem) != cudaSuccess) {
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_treep_bwd<P, LB, NT>, NT, smem) != cudaSuccess) {
         cudaGetLastError();
         return 0;
     }
@@ -757,9 +791,9 @@ int treep_grid(long long tiles, size_t smem) {
 
 // The tiled form: one cooperative launch for the backward sweep, one launch
 // for the forward reading, one synchronisation.
-template <int P>
+template <int P, int LB, int NT>
 int treep_tiles(dwt_plan_s* Pl, const MapP& I0, const std::vector<MapP>& Qmap, int ng, cudaStream_t st) {
-    using SH = TreeShape<P>;
+    using SH = TileP<P, LB>;
     const long long N = Pl->N;
     const int m = Pl->m, s = Pl->s;
     const long long tiles = N / SH::TS;
@@ -782,10 +816,10 @@ int treep_tiles(dwt_plan_s* Pl, const MapP& I0, const std::vector<MapP>& Qmap, i
     for (int j = 0; j + 1 < s; ++j) hm[1 + j] = Qmap[j];
     DWT_CK(cudaMemcpyAsync(dmaps, hm.data(), sizeof(MapP) * s, cudaMemcpyHostToDevice, st));
     DWT_CK(cudaMemsetAsync(flags, 0, 16, st));
-    const size_t smem = SmemP<P>::bytes(tiles);
-    int rc = smem_limit_max(k_treep_bwd<P>);
+    const size_t smem = SmemP<P, LB>::bytes(tiles);
+    int rc = smem_limit_max(k_treep_bwd<P, LB, NT>);
     if (rc) { cleanup(); return rc; }
-    const int grid = treep_grid<P>(tiles, smem);
+    const int grid = treep_grid<P, LB, NT>(tiles, smem);
     if (grid < 1) {
         cleanup();
         set_error("no resident grid for the tiled coset-table sweep (%zu bytes of shared memory)", smem);
@@ -804,7 +838,7 @@ int treep_tiles(dwt_plan_s* Pl, const MapP& I0, const std::vector<MapP>& Qmap, i
     {
         LaunchScope ls("tree_sweep", st);
         void* args[] = {&A};
-        DWT_CK(cudaLaunchCooperativeKernel((const void*)k_treep_bwd<P>, dim3((unsigned)grid), dim3(kThreadsP), args,
+        DWT_CK(cudaLaunchCooperativeKernel((const void*)k_treep_bwd<P, LB, NT>, dim3((unsigned)grid), dim3(NT), args,
                                            smem, st));
     }
     {
@@ -864,8 +898,12 @@ int treep(dwt_plan_s* Pl, cudaStream_t st, bool* used) {
         make_mapP<P>(qc, m, Qmap[j]);
     }
     *used = true;
-    if (m <= SH::LB) return treep_one<P>(Pl, Imap, Fmap, Qmap, ng, st);
-    return treep_tiles<P>(Pl, Imap[0], Qmap, ng, st);
+    // nets of few full tiles run on smaller tiles (more CTAs per coordinate);
+    // a net of at most one small tile in one CTA
+    constexpr int LBs = SmallTile<P>::LB;
+    if (m <= LBs) return treep_one<P>(Pl, Imap, Fmap, Qmap, ng, st);
+    if (N / SH::TS < 64) return treep_tiles<P, LBs, SmallTile<P>::NT>(Pl, Imap[0], Qmap, ng, st);
+    return treep_tiles<P, SH::LB, kThreadsP>(Pl, Imap[0], Qmap, ng, st);
 }
 
 }  // namespace

@@ -144,14 +144,16 @@ def test_tables_small_large_boundary(dwt, dev, orc, p, m, s):
 # Plans without DWT_PLAN_KEEP_INDEX_MAP build K(C) with the min-tree form when
 # every C_j is nonsingular; the tables must equal the oracle's bit for bit, on
 # one tile, several tiles, and with a coarse tree of several levels.  A net of
-# one tile (2^13, 3^8, 5^5, 7^4 labels) runs in one CTA; larger ones in tiles
-# (2^12, 3^8, 5^5, 7^4 labels) with one cooperative launch (the trees of the
-# backward sweep and the representatives k_j(U)) and one launch of the
+# one tile (2^13 labels for p = 2; 3^5, 5^3, 7^2 for p = 3, 5, 7) runs in one
+# CTA; larger ones in tiles (2^12; 3^8, 5^5, 7^4, or 3^5, 5^3, 7^2 when the net
+# has fewer than 64 of the larger) with one cooperative launch (the trees of
+# the backward sweep and the representatives k_j(U)) and one launch of the
 # per-label reading.
 @pytest.mark.parametrize("p,m,s", [(2, 1, 3), (2, 9, 4), (2, 13, 9), (2, 14, 3), (2, 17, 20), (3, 2, 4), (3, 8, 5),
                                    (3, 11, 9), (3, 13, 3), (5, 5, 7), (5, 9, 3), (7, 4, 6), (7, 6, 10), (2, 12, 64),
                                    (2, 14, 64), (2, 15, 33), (2, 16, 2), (2, 18, 7), (2, 20, 3), (3, 12, 40),
-                                   (5, 8, 33), (7, 7, 12), (3, 14, 3)])
+                                   (5, 8, 33), (7, 7, 12), (3, 14, 3), (3, 6, 20), (5, 4, 9), (7, 3, 5), (3, 9, 64),
+                                   (5, 7, 33)])
 def test_tables_tree_form(dwt, dev, orc, p, m, s):
     C = S.small_net(p, m, s, index=100 + m + s)
     N = p ** m
@@ -163,7 +165,7 @@ def test_tables_tree_form(dwt, dev, orc, p, m, s):
     dwt.dwt_profile_reset()
     assert plan.status == 0
     # which form ran
-    if N <= {2: 8192, 3: 6561, 5: 3125, 7: 2401}[p]:
+    if N <= {2: 8192, 3: 243, 5: 125, 7: 49}[p]:
         assert n == {"tree_up": 0, "tree_one": 1, "tree_sweep": 0, "tree_read": 0}
     else:
         assert n == {"tree_up": 0, "tree_one": 0, "tree_sweep": 1, "tree_read": 1}
