@@ -21,7 +21,7 @@
 // Tables are kept in the coordinates of their own coordinate's basis (T^U_j);
 // consecutive coordinates are linked by the F_2-linear map U_j -> U_{j+1}.
 // Linear maps are applied as four 256-entry XOR tables (one per byte).  Nets
-// of up to 2^13 labels run in one CTA; larger ones in tiles of 2^12 labels
+// of up to 2^11 labels run in one CTA; larger ones in tiles of 2^12 labels
 // (the tiled form below).  Nets whose row sets are dependent, and m > 27, use
 // the per-digit programme.
 #include <stdlib.h>
@@ -60,7 +60,7 @@ __device__ __forceinline__ void load_map(uint32_t (*sm)[256], const Map4* g) {
 }
 
 // ---------------------------------------------------------------------------
-// The tiled form, 14 <= m <= 27.  Tiles of 2^12 labels in groups of 16 (one
+// The tiled form, 12 <= m <= 27.  Tiles of 2^12 labels in groups of 16 (one
 // thread each); a tile's work in a pass may be split over `parts` CTAs of 256
 // threads, so that small nets still keep many SMs busy.
 //
@@ -737,7 +737,7 @@ static long long tiles_resident(size_t smem) {
     return (long long)occ * sms;
 }
 
-// The tiled form for 14 <= m <= 27 (one cooperative launch for the backward
+// The tiled form for 12 <= m <= 27 (one cooperative launch for the backward
 // sweep, one launch for the forward reading, one synchronisation).
 int tiles_build(dwt_plan_s* Pl, const Map4& I0, const std::vector<Map4>& Qmap, cudaStream_t st) {
     const long long N = Pl->N;
@@ -856,7 +856,7 @@ int coset_tables_tree2(dwt_plan_s* Pl, cudaStream_t st, bool* used) {
         make_map(qc.data(), m, Qmap[j]);
     }
     *used = true;
-    if (m <= kLB) return tree_one(Pl, Imap, Qmap, st);
+    if (m < kTL) return tree_one(Pl, Imap, Qmap, st);
     return tiles_build(Pl, Imap[0], Qmap, st);
 }
 

@@ -144,8 +144,8 @@ def test_tables_small_large_boundary(dwt, dev, orc, p, m, s):
 # Plans without DWT_PLAN_KEEP_INDEX_MAP build K(C) with the min-tree form when
 # every C_j is nonsingular; the tables must equal the oracle's bit for bit, on
 # one tile, several tiles, and with a coarse tree of several levels.  A net of
-# one tile (2^13 labels for p = 2; 3^5, 5^3, 7^2 for p = 3, 5, 7) runs in one
-# CTA; larger ones in tiles (2^12; 3^8, 5^5, 7^4, or 3^5, 5^3, 7^2 when the net
+# less than one tile (2^11 labels for p = 2; 3^5, 5^3, 7^2 for p = 3, 5, 7)
+# runs in one CTA; larger ones in tiles (2^12; 3^8, 5^5, 7^4, or 3^5, 5^3, 7^2 when the net
 # has fewer than 64 of the larger) with one cooperative launch (the trees of
 # the backward sweep and the representatives k_j(U)) and one launch of the
 # per-label reading.
@@ -165,7 +165,7 @@ def test_tables_tree_form(dwt, dev, orc, p, m, s):
     dwt.dwt_profile_reset()
     assert plan.status == 0
     # which form ran
-    if N <= {2: 8192, 3: 243, 5: 125, 7: 49}[p]:
+    if N <= {2: 2048, 3: 243, 5: 125, 7: 49}[p]:
         assert n == {"tree_up": 0, "tree_one": 1, "tree_sweep": 0, "tree_read": 0}
     else:
         assert n == {"tree_up": 0, "tree_one": 0, "tree_sweep": 1, "tree_read": 1}
