@@ -16,6 +16,7 @@
 // polled; timestamps give queueing and service latency.
 #include <stdio.h>
 
+#include <algorithm>
 #include <chrono>
 #include <condition_variable>
 #include <deque>
@@ -65,9 +66,11 @@ namespace dwt {
 // device bytes one request holds at its peak (plan build + buffers)
 static size_t request_footprint(int p, int m, int s) {
     const size_t N = (size_t)ipow_ll(p, m);
-    // plan build per label: p = 2 tiled tree form (k_j per coordinate, records,
-    // T, W, cls), else the DP / tree tables, state, W and cls
-    const size_t plan_build = (p == 2 && m >= 14) ? (size_t)(4 * s + 10) : (size_t)(2 * s + 1 + m + 2) + 12;
+    // plan build per label: the tiled tree forms (k_j per coordinate, records
+    // or levels, T, W, cls) or the per-digit programme's tables, state, W and
+    // cls, whichever is larger
+    const size_t plan_build = p == 2 ? std::max<size_t>((size_t)(4 * s + 10), (size_t)(2 * s + 1 + m + 2) + 12)
+                                     : std::max<size_t>((size_t)(4 * s + 10), (size_t)(2 * s + 1 + m + 2) + 12);
     const size_t tiled = (p == 2 && m >= 16) ? 6 : 0;
     const size_t data = 4 + (p == 2 ? 4 : 8);                    // f (real) and c
     return N * (plan_build + tiled + data) + ((size_t)1 << 20);
