@@ -97,6 +97,36 @@ int smem_limit_max_ptr(const void* kern) {
 // ---- workspace ----------------------------------------------------------------
 void count_host_alloc() { g_allocs.fetch_add(1, std::memory_order_relaxed); }
 
+// A page-locked staging buffer of the calling host thread, grown on demand and
+// kept for the thread's life (uploads of plan-build inputs).  The caller
+// synchronises the stream of its copy before the thread uses the buffer again.
+namespace {
+struct HostStaging {
+    unsigned char* p = nullptr;
+    size_t n = 0;
+    ~HostStaging() {
+        if (p) cudaFreeHost(p);
+    }
+};
+thread_local HostStaging g_staging;
+}  // namespace
+
+unsigned char* host_staging(size_t bytes) {
+    if (g_staging.n >= bytes) return g_staging.p;
+    if (g_staging.p) cudaFreeHost(g_staging.p);
+    g_staging.p = nullptr;
+    g_staging.n = 0;
+    const size_t want = std::max(bytes, (size_t)1 << 20);
+    count_host_alloc();
+    if (cudaMallocHost((void**)&g_staging.p, want) != cudaSuccess) {
+        cudaGetLastError();
+        g_staging.p = nullptr;
+        return nullptr;
+    }
+    g_staging.n = want;
+    return g_staging.p;
+}
+
 int dmalloc(void** p, size_t bytes, cudaStream_t st) {
     *p = nullptr;
     if (bytes == 0) bytes = 16;
@@ -416,13 +446,18 @@ int dwt_plan_create(int p, int m, int s, const uint8_t* C, unsigned flags, void*
         dwt_plan_destroy(P);
         return code;
     };
-    if (dmalloc((void**)&P->d_R, R.size() * 4, st) || dmalloc((void**)&P->d_col, col.size() * 4, st) ||
-        dmalloc((void**)&P->d_C, P->C.size(), st)) {
+    // R, col and C in one device block, uploaded by one copy (d_R owns it)
+    const size_t nR = R.size() * 4, nC = P->C.size();
+    std::vector<unsigned char> blob(2 * nR + nC);
+    memcpy(blob.data(), R.data(), nR);
+    memcpy(blob.data() + nR, col.data(), nR);
+    memcpy(blob.data() + 2 * nR, P->C.data(), nC);
+    if (dmalloc((void**)&P->d_R, blob.size(), st)) {
         return fail(DWT_ENOMEM);
     }
-    if (cudaMemcpyAsync(P->d_R, R.data(), R.size() * 4, cudaMemcpyHostToDevice, st) != cudaSuccess ||
-        cudaMemcpyAsync(P->d_col, col.data(), col.size() * 4, cudaMemcpyHostToDevice, st) != cudaSuccess ||
-        cudaMemcpyAsync(P->d_C, P->C.data(), P->C.size(), cudaMemcpyHostToDevice, st) != cudaSuccess) {
+    P->d_col = P->d_R + R.size();
+    P->d_C = reinterpret_cast<uint8_t*>(P->d_R) + 2 * nR;
+    if (cudaMemcpyAsync(P->d_R, blob.data(), blob.size(), cudaMemcpyHostToDevice, st) != cudaSuccess) {
         set_error("plan upload failed: %s", cudaGetErrorString(cudaGetLastError()));
         return fail(DWT_ECUDA);
     }
@@ -502,9 +537,7 @@ int dwt_plan_destroy(dwt_plan_t P) {
     cudaDeviceSynchronize();
     host_stage_free(P, nullptr, true);
     spline_free(P, nullptr, true);
-    cudaFree(P->d_R);
-    cudaFree(P->d_col);
-    cudaFree(P->d_C);
+    cudaFree(P->d_R);   // also holds d_col and d_C
     cudaFree(P->d_W);
     cudaFree(P->d_cls);
     cudaFree(P->d_Wt);
@@ -525,9 +558,7 @@ int dwt_plan_destroy_async(dwt_plan_t P, void* stream) {
     cudaStream_t st = (cudaStream_t)stream;
     host_stage_free(P, st, false);
     spline_free(P, st, false);
-    dfree(P->d_R, st);
-    dfree(P->d_col, st);
-    dfree(P->d_C, st);
+    dfree(P->d_R, st);   // also holds d_col and d_C
     dfree(P->d_W, st);
     dfree(P->d_cls, st);
     dfree(P->d_Wt, st);

@@ -603,13 +603,15 @@ int build_coset_tables(dwt_plan_s* Pl, cudaStream_t st) {
     // the min-tree form (O(s N)) when every coordinate's rows are a basis; the
     // per-digit programme otherwise, and when the index maps are kept
     if (!(Pl->flags & DWT_PLAN_KEEP_INDEX_MAP)) {
+        // the tree form runs only when every C_j is nonsingular, so its rows
+        // already span F_p^m and the rank test below is not needed for it
+        bool used = false;
+        const int rc = Pl->p == 2 ? coset_tables_tree2(Pl, st, &used) : coset_tables_treep(Pl, st, &used);
+        if (used || rc) return rc;
         if (host_rank(Pl) < Pl->m) {
             set_error("rows of C_1..C_s span a space of dimension < m");
             return DWT_ESPAN;
         }
-        bool used = false;
-        const int rc = Pl->p == 2 ? coset_tables_tree2(Pl, st, &used) : coset_tables_treep(Pl, st, &used);
-        if (used || rc) return rc;
     }
     const bool small = Pl->N <= kSmallDpMax;
     switch (Pl->p) {

@@ -75,7 +75,7 @@ struct dwt_plan_s {
     // device copies of the generating data
     uint32_t* d_R = nullptr;      // [s][m]: coset label of row i of C_j, sum_c C[j][i][c] p^c
     uint32_t* d_col = nullptr;    // [s][m]: point contribution of index digit c = 1, sum_i C[j][i][c] p^{m-1-i}
-    uint8_t* d_C = nullptr;       // [s][m][m]
+    uint8_t* d_C = nullptr;       // [s][m][m]   (d_col and d_C lie in d_R's allocation)
     // coset tables
     float* d_W = nullptr;         // [N]
     uint8_t* d_cls = nullptr;     // [N][2]
@@ -130,6 +130,7 @@ struct GroupJob {
     int batch;
     long long ld_in, ld_out;
 };
+unsigned char* host_staging(size_t bytes);   // page-locked, per host thread (NULL if unavailable)
 int run_transform_grouped(const std::vector<GroupJob>& jobs, dwt_dtype in_t, dwt_dtype out_t, int sgn,
                           cudaStream_t st);
 int p2_lo_grouped(int L, const std::vector<GroupJob>& jobs, dwt_dtype t, int sgn, cudaStream_t st);

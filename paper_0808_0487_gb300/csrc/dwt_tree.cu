@@ -25,6 +25,7 @@
 // (the tiled form below).  Nets whose row sets are dependent, and m > 27, use
 // the per-digit programme.
 #include <stdlib.h>
+#include <string.h>
 
 #include <algorithm>
 #include <vector>
@@ -743,28 +744,39 @@ int tiles_build(dwt_plan_s* Pl, const Map4& I0, const std::vector<Map4>& Qmap, c
     const long long N = Pl->N;
     const int m = Pl->m, s = Pl->s;
     const long long tiles = N >> kTL;
-    uint8_t *T = nullptr, *rec0 = nullptr, *rec4 = nullptr, *bmin = nullptr;
-    uint32_t* K = nullptr;
-    Map4* dmaps = nullptr;
-    unsigned* flags = nullptr;
-    auto cleanup = [&]() {
-        dfree(T, st); dfree(rec0, st); dfree(rec4, st); dfree(bmin, st);
-        dfree(K, st); dfree(dmaps, st); dfree(flags, st);
-    };
-    if (dmalloc((void**)&T, (size_t)N, st) || dmalloc((void**)&rec0, (size_t)N * 2, st) ||
-        dmalloc((void**)&rec4, (size_t)N / 8, st) || dmalloc((void**)&bmin, (size_t)N / 256, st) ||
-        dmalloc((void**)&K, (size_t)s * N * 4, st) ||
-        dmalloc((void**)&dmaps, sizeof(Map4) * s, st) || dmalloc((void**)&flags, 16, st) ||
-        dmalloc((void**)&Pl->d_W, (size_t)N * 4, st) || dmalloc((void**)&Pl->d_cls, (size_t)N * 2, st)) {
+    // one scratch block: flags (16 B, padded), the maps I_0, Q_0 .. Q_{s-2},
+    // then T, the records, the block minima and K (256-byte aligned pieces)
+    auto al = [](size_t x) { return (x + 255) & ~(size_t)255; };
+    const size_t o_maps = 256, o_T = al(o_maps + sizeof(Map4) * s), o_rec0 = al(o_T + (size_t)N),
+                 o_rec4 = al(o_rec0 + (size_t)N * 2), o_bmin = al(o_rec4 + (size_t)N / 8),
+                 o_K = al(o_bmin + (size_t)N / 256), total = al(o_K + (size_t)s * N * 4);
+    unsigned char* ws = nullptr;
+    auto cleanup = [&]() { dfree(ws, st); };
+    if (dmalloc((void**)&ws, total, st) || dmalloc((void**)&Pl->d_W, (size_t)N * 4, st) ||
+        dmalloc((void**)&Pl->d_cls, (size_t)N * 2, st)) {
         cleanup();
         return DWT_ENOMEM;
     }
-    // maps: I_0, then Q_0 .. Q_{s-2}
-    std::vector<Map4> hm(s);
-    hm[0] = I0;
-    for (int j = 0; j + 1 < s; ++j) hm[1 + j] = Qmap[j];
-    DWT_CK(cudaMemcpyAsync(dmaps, hm.data(), sizeof(Map4) * s, cudaMemcpyHostToDevice, st));
-    DWT_CK(cudaMemsetAsync(flags, 0, 16, st));
+    unsigned* flags = reinterpret_cast<unsigned*>(ws);
+    Map4* dmaps = reinterpret_cast<Map4*>(ws + o_maps);
+    uint8_t* T = ws + o_T;
+    uint8_t* rec0 = ws + o_rec0;
+    uint8_t* rec4 = ws + o_rec4;
+    uint8_t* bmin = ws + o_bmin;
+    uint32_t* K = reinterpret_cast<uint32_t*>(ws + o_K);
+    // flags zeroed and the maps in one upload, from page-locked staging when
+    // there is some (the stream is synchronised below, before it is reused)
+    const size_t nb = o_maps + sizeof(Map4) * s;
+    std::vector<unsigned char> hv;
+    unsigned char* hb = host_staging(nb);
+    if (!hb) {
+        hv.resize(nb);
+        hb = hv.data();
+    }
+    memset(hb, 0, o_maps);
+    memcpy(hb + o_maps, &I0, sizeof(Map4));
+    for (int j = 0; j + 1 < s; ++j) memcpy(hb + o_maps + sizeof(Map4) * (1 + j), &Qmap[j], sizeof(Map4));
+    DWT_CK(cudaMemcpyAsync(ws, hb, nb, cudaMemcpyHostToDevice, st));
     const size_t smem = 4096 + kRecBytes + 8192 + 256 + 16 + (size_t)((2 * tiles + 15) & ~15ll);
     int rc = smem_limit_max(k_tiles_bwd);
     if (rc) { cleanup(); return rc; }

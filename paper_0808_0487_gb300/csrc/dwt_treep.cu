@@ -18,6 +18,7 @@
 // limits of the coarse tree (p = 3: m <= 16, p = 5: m <= 11, p = 7: m <= 8),
 // or with dependent rows, use the per-digit programme.
 #include <stdlib.h>
+#include <string.h>
 
 #include <algorithm>
 #include <vector>
@@ -797,25 +798,36 @@ int treep_tiles(dwt_plan_s* Pl, const MapP& I0, const std::vector<MapP>& Qmap, i
     const long long N = Pl->N;
     const int m = Pl->m, s = Pl->s;
     const long long tiles = N / SH::TS;
-    uint8_t *T = nullptr, *lev = nullptr;
-    uint32_t* K = nullptr;
-    MapP* dmaps = nullptr;
-    unsigned* flags = nullptr;
-    auto cleanup = [&]() {
-        dfree(T, st); dfree(lev, st); dfree(K, st); dfree(dmaps, st); dfree(flags, st);
-    };
-    if (dmalloc((void**)&T, (size_t)N, st) || dmalloc((void**)&lev, (size_t)2 * N, st) ||
-        dmalloc((void**)&K, (size_t)s * N * 4, st) || dmalloc((void**)&dmaps, sizeof(MapP) * s, st) ||
-        dmalloc((void**)&flags, 16, st) || dmalloc((void**)&Pl->d_W, (size_t)N * 4, st) ||
+    // one scratch block: flags (16 B, padded), the maps I_0, Q_0 .. Q_{s-2},
+    // then T, the levels and K (256-byte aligned pieces)
+    auto al = [](size_t x) { return (x + 255) & ~(size_t)255; };
+    const size_t o_maps = 256, o_T = al(o_maps + sizeof(MapP) * s), o_lev = al(o_T + (size_t)N),
+                 o_K = al(o_lev + (size_t)N * 2), total = al(o_K + (size_t)s * N * 4);
+    unsigned char* ws = nullptr;
+    auto cleanup = [&]() { dfree(ws, st); };
+    if (dmalloc((void**)&ws, total, st) || dmalloc((void**)&Pl->d_W, (size_t)N * 4, st) ||
         dmalloc((void**)&Pl->d_cls, (size_t)N * 2, st)) {
         cleanup();
         return DWT_ENOMEM;
     }
-    std::vector<MapP> hm(s);
-    hm[0] = I0;
-    for (int j = 0; j + 1 < s; ++j) hm[1 + j] = Qmap[j];
-    DWT_CK(cudaMemcpyAsync(dmaps, hm.data(), sizeof(MapP) * s, cudaMemcpyHostToDevice, st));
-    DWT_CK(cudaMemsetAsync(flags, 0, 16, st));
+    unsigned* flags = reinterpret_cast<unsigned*>(ws);
+    MapP* dmaps = reinterpret_cast<MapP*>(ws + o_maps);
+    uint8_t* T = ws + o_T;
+    uint8_t* lev = ws + o_lev;
+    uint32_t* K = reinterpret_cast<uint32_t*>(ws + o_K);
+    // flags zeroed and the maps in one upload, from page-locked staging when
+    // there is some (the stream is synchronised below, before it is reused)
+    const size_t nb = o_maps + sizeof(MapP) * s;
+    std::vector<unsigned char> hv;
+    unsigned char* hb = host_staging(nb);
+    if (!hb) {
+        hv.resize(nb);
+        hb = hv.data();
+    }
+    memset(hb, 0, o_maps);
+    memcpy(hb + o_maps, &I0, sizeof(MapP));
+    for (int j = 0; j + 1 < s; ++j) memcpy(hb + o_maps + sizeof(MapP) * (1 + j), &Qmap[j], sizeof(MapP));
+    DWT_CK(cudaMemcpyAsync(ws, hb, nb, cudaMemcpyHostToDevice, st));
     const size_t smem = SmemP<P, LB>::bytes(tiles);
     int rc = smem_limit_max(k_treep_bwd<P, LB, NT>);
     if (rc) { cleanup(); return rc; }
@@ -886,7 +898,7 @@ int treep(dwt_plan_s* Pl, cudaStream_t st, bool* used) {
         for (int i = 0; i < m; ++i) rows[j][i] = digits_of(R[(size_t)j * m + i], P, m);
         if (!gfp_inverse(rows[j], m, P, invc[j])) return DWT_OK;
         make_mapP<P>(invc[j], m, Imap[j]);
-        make_mapP<P>(rows[j], m, Fmap[j]);
+        if (m <= SmallTile<P>::LB) make_mapP<P>(rows[j], m, Fmap[j]);   // only the one-CTA form reads F_j
     }
     for (int j = 0; j + 1 < s; ++j) {
         std::vector<std::vector<int>> qc(m);
