@@ -30,6 +30,7 @@
 #include <algorithm>
 #include <vector>
 
+#include "dwt_grid.cuh"
 #include "dwt_internal.cuh"
 
 namespace dwt {
@@ -94,7 +95,6 @@ constexpr int kTL = 12;                    // labels per tile: 2^12
 constexpr int kTT = 256;                   // threads per tile CTA
 constexpr int kRecBytes = 8192 + 512 + 32; // one tile's records
 constexpr int kFwdL = 8;                   // labels per thread of the forward reading
-constexpr unsigned long long kGridWaitNs = 2000000000ull;
 
 struct TileArgs {
     const Map4* Q;     // Q_j, j = 0 .. s-2
@@ -122,51 +122,6 @@ __device__ __forceinline__ uint4 rec_upper(uint4 lo) {
 }
 
 __device__ __forceinline__ unsigned byte_of(uint32_t w, int b) { return (w >> (8 * b)) & 255u; }
-
-__device__ __forceinline__ unsigned ld_acquire_gpu(const unsigned* p) {
-    unsigned v;
-    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
-    return v;
-}
-
-__device__ __forceinline__ void red_release_gpu(unsigned* p, unsigned v) {
-    asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
-}
-
-__device__ __forceinline__ unsigned long long global_ns() {
-    unsigned long long t;
-    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-    return t;
-}
-
-// Every CTA of the cooperative grid arrives at flags[3]; returns false, with
-// flags[2] set, when the wait gives up after kGridWaitNs or another CTA gave up.
-__device__ bool grid_wait(unsigned* flags, unsigned& target, int* ok) {
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        target += gridDim.x;
-        __threadfence();
-        red_release_gpu(flags + 3, 1u);
-        int good = 1;
-        const unsigned long long t0 = global_ns();
-        while ((int)(ld_acquire_gpu(flags + 3) - target) < 0) {
-            if (*(volatile unsigned*)(flags + 2)) {
-                good = 0;
-                break;
-            }
-            if (global_ns() - t0 > kGridWaitNs) {
-                atomicExch(flags + 2, 1u);
-                good = 0;
-                break;
-            }
-            __nanosleep(32);
-        }
-        __threadfence();
-        *ok = good;
-    }
-    __syncthreads();
-    return *ok != 0;
-}
 
 // up, for part `part` of `parts` of tile `tile`: the groups part * G ..
 // part * G + G - 1 (G = 256 / parts), one per thread: leaves, group records,

@@ -23,6 +23,7 @@
 #include <algorithm>
 #include <vector>
 
+#include "dwt_grid.cuh"
 #include "dwt_internal.cuh"
 
 namespace dwt {
@@ -129,7 +130,6 @@ __device__ __forceinline__ unsigned sib_min(const uint8_t* S, uint32_t v) {
 //   U_0 = I_0(H),  k_j = K[j][U_j],  U_{j+1} = Q_j(U_j - k_j digit-wise)
 // and multiplies its weight denominator by (1 + k_j)^2.
 constexpr int kFwdLP = 8;   // labels per thread of the forward reading
-constexpr unsigned long long kGridWaitNsP = 2000000000ull;
 
 struct ArgsP {
     const MapP* Q;     // Q_j, j = 0 .. s-2
@@ -166,47 +166,6 @@ struct SmemP {
     static constexpr size_t kFixed = kMap + kLev + kA + 16 + ((sizeof(LevelsP) + 15) & ~(size_t)15);
     static size_t bytes(long long nLB) { return kFixed + (((size_t)2 * nLB + 15) & ~(size_t)15); }
 };
-
-__device__ __forceinline__ unsigned ld_acquire_gpu(const unsigned* p) {
-    unsigned v;
-    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
-    return v;
-}
-
-__device__ __forceinline__ unsigned long long global_ns() {
-    unsigned long long t;
-    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-    return t;
-}
-
-// Every CTA of the cooperative grid arrives at flags[3]; false, with flags[2]
-// set, when the wait gives up after kGridWaitNsP or another CTA gave up.
-__device__ bool grid_wait_p(unsigned* flags, unsigned& target, int* ok) {
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        target += gridDim.x;
-        __threadfence();
-        asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(flags + 3), "r"(1u) : "memory");
-        int good = 1;
-        const unsigned long long t0 = global_ns();
-        while ((int)(ld_acquire_gpu(flags + 3) - target) < 0) {
-            if (*(volatile unsigned*)(flags + 2)) {
-                good = 0;
-                break;
-            }
-            if (global_ns() - t0 > kGridWaitNsP) {
-                atomicExch(flags + 2, 1u);
-                good = 0;
-                break;
-            }
-            __nanosleep(32);
-        }
-        __threadfence();
-        *ok = good;
-    }
-    __syncthreads();
-    return *ok != 0;
-}
 
 template <int P, int LB>
 __device__ void levels_init(LevelsP* L, long long N, int m) {
@@ -373,7 +332,7 @@ __global__ void __launch_bounds__(NT) k_treep_bwd(ArgsP a) {
                 a.K[(size_t)j * N + U] = U;
                 if (j == 0) mx = max(mx, (unsigned)n);
             }
-            if (j > 0 && !grid_wait_p(a.flags, target, ok)) return;
+            if (j > 0 && !grid_wait(a.flags, target, ok)) return;
             continue;
         }
         load_mapP<P>(q, a.Q + j, a.ng);
@@ -382,7 +341,7 @@ __global__ void __launch_bounds__(NT) k_treep_bwd(ArgsP a) {
             tileP_up<P, LB>(a, (uint32_t)tl, q, sl, lv);
             __syncthreads();
         }
-        if (!grid_wait_p(a.flags, target, ok)) return;
+        if (!grid_wait(a.flags, target, ok)) return;
         // the coarse tree: level LB (tile minima) .. m
         for (long long v = threadIdx.x; v < nLB; v += blockDim.x) cl[v] = a.lev[lv->goff[SH::LB] + v];
         __syncthreads();
@@ -404,7 +363,7 @@ __global__ void __launch_bounds__(NT) k_treep_bwd(ArgsP a) {
             tileP_down<P, LB>(a, (uint32_t)tl, j, cl, sl, a0, a1, lv, mx);
             __syncthreads();
         }
-        if (j > 0 && !grid_wait_p(a.flags, target, ok)) return;
+        if (j > 0 && !grid_wait(a.flags, target, ok)) return;
     }
     for (int o = 16; o > 0; o >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
     if ((threadIdx.x & 31) == 0) atomicMax(a.flags, mx);
