@@ -707,6 +707,13 @@ int tiles_build(dwt_plan_s* Pl, const Map4& I0, const std::vector<Map4>& Qmap, c
                  o_K = al(o_bmin + (size_t)N / 256), total = al(o_K + (size_t)s * N * 4);
     unsigned char* ws = nullptr;
     auto cleanup = [&]() { dfree(ws, st); };
+    int rc = DWT_OK;
+    // CUDA failures after the allocation release the scratch block first
+    auto ck = [&](cudaError_t e, const char* what) -> int {
+        if (e == cudaSuccess) return DWT_OK;
+        cleanup();
+        return cuda_fail(e, what, __FILE__, __LINE__);
+    };
     if (dmalloc((void**)&ws, total, st) || dmalloc((void**)&Pl->d_W, (size_t)N * 4, st) ||
         dmalloc((void**)&Pl->d_cls, (size_t)N * 2, st)) {
         cleanup();
@@ -731,9 +738,9 @@ int tiles_build(dwt_plan_s* Pl, const Map4& I0, const std::vector<Map4>& Qmap, c
     memset(hb, 0, o_maps);
     memcpy(hb + o_maps, &I0, sizeof(Map4));
     for (int j = 0; j + 1 < s; ++j) memcpy(hb + o_maps + sizeof(Map4) * (1 + j), &Qmap[j], sizeof(Map4));
-    DWT_CK(cudaMemcpyAsync(ws, hb, nb, cudaMemcpyHostToDevice, st));
+    if ((rc = ck(cudaMemcpyAsync(ws, hb, nb, cudaMemcpyHostToDevice, st), "cudaMemcpyAsync"))) return rc;
     const size_t smem = 4096 + kRecBytes + 8192 + 256 + 16 + (size_t)((2 * tiles + 15) & ~15ll);
-    int rc = smem_limit_max(k_tiles_bwd);
+    rc = smem_limit_max(k_tiles_bwd);
     if (rc) { cleanup(); return rc; }
     // every resident CTA busy in the down pass: parts per tile (a power of two
     // <= 16); the grid is capped by DWT_TILE_GRID if set (a tuning and testing
@@ -772,7 +779,10 @@ int tiles_build(dwt_plan_s* Pl, const Map4& I0, const std::vector<Map4>& Qmap, c
     {
         LaunchScope ls("tree_sweep", st);
         void* args[] = {&A, &parts};
-        DWT_CK(cudaLaunchCooperativeKernel((const void*)k_tiles_bwd, dim3((unsigned)grid), dim3(kTT), args, smem, st));
+        if ((rc = ck(cudaLaunchCooperativeKernel((const void*)k_tiles_bwd, dim3((unsigned)grid), dim3(kTT), args, smem,
+                                                 st),
+                     "cooperative launch")))
+            return rc;
     }
     {
         const long long per_cta = 256ll * kFwdL;
@@ -780,10 +790,10 @@ int tiles_build(dwt_plan_s* Pl, const Map4& I0, const std::vector<Map4>& Qmap, c
         LaunchScope ls("tree_read", st);
         k_tiles_fwd<<<fg, 256, 0, st>>>(K, dmaps, dmaps + 1, flags, Pl->d_W, Pl->d_cls, N, s);
     }
-    DWT_CK_LAUNCH("tiled coset tables");
+    if ((rc = ck(cudaGetLastError(), "tiled coset tables"))) return rc;
     unsigned hf[4] = {0, 0, 0, 0};
-    DWT_CK(cudaMemcpyAsync(hf, flags, 16, cudaMemcpyDeviceToHost, st));
-    DWT_CK(cudaStreamSynchronize(st));
+    if ((rc = ck(cudaMemcpyAsync(hf, flags, 16, cudaMemcpyDeviceToHost, st), "cudaMemcpyAsync"))) return rc;
+    if ((rc = ck(cudaStreamSynchronize(st), "cudaStreamSynchronize"))) return rc;
     cleanup();
     if (hf[2]) {
         set_error("tiled coset tables: a grid-wide wait gave up");

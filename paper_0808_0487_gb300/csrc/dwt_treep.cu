@@ -764,6 +764,13 @@ int treep_tiles(dwt_plan_s* Pl, const MapP& I0, const std::vector<MapP>& Qmap, i
                  o_K = al(o_lev + (size_t)N * 2), total = al(o_K + (size_t)s * N * 4);
     unsigned char* ws = nullptr;
     auto cleanup = [&]() { dfree(ws, st); };
+    int rc = DWT_OK;
+    // CUDA failures after the allocation release the scratch block first
+    auto ck = [&](cudaError_t e, const char* what) -> int {
+        if (e == cudaSuccess) return DWT_OK;
+        cleanup();
+        return cuda_fail(e, what, __FILE__, __LINE__);
+    };
     if (dmalloc((void**)&ws, total, st) || dmalloc((void**)&Pl->d_W, (size_t)N * 4, st) ||
         dmalloc((void**)&Pl->d_cls, (size_t)N * 2, st)) {
         cleanup();
@@ -786,9 +793,9 @@ int treep_tiles(dwt_plan_s* Pl, const MapP& I0, const std::vector<MapP>& Qmap, i
     memset(hb, 0, o_maps);
     memcpy(hb + o_maps, &I0, sizeof(MapP));
     for (int j = 0; j + 1 < s; ++j) memcpy(hb + o_maps + sizeof(MapP) * (1 + j), &Qmap[j], sizeof(MapP));
-    DWT_CK(cudaMemcpyAsync(ws, hb, nb, cudaMemcpyHostToDevice, st));
+    if ((rc = ck(cudaMemcpyAsync(ws, hb, nb, cudaMemcpyHostToDevice, st), "cudaMemcpyAsync"))) return rc;
     const size_t smem = SmemP<P, LB>::bytes(tiles);
-    int rc = smem_limit_max(k_treep_bwd<P, LB, NT>);
+    rc = smem_limit_max(k_treep_bwd<P, LB, NT>);
     if (rc) { cleanup(); return rc; }
     const int grid = treep_grid<P, LB, NT>(tiles, smem);
     if (grid < 1) {
@@ -809,8 +816,10 @@ int treep_tiles(dwt_plan_s* Pl, const MapP& I0, const std::vector<MapP>& Qmap, i
     {
         LaunchScope ls("tree_sweep", st);
         void* args[] = {&A};
-        DWT_CK(cudaLaunchCooperativeKernel((const void*)k_treep_bwd<P, LB, NT>, dim3((unsigned)grid), dim3(NT), args,
-                                           smem, st));
+        if ((rc = ck(cudaLaunchCooperativeKernel((const void*)k_treep_bwd<P, LB, NT>, dim3((unsigned)grid), dim3(NT),
+                                                 args, smem, st),
+                     "cooperative launch")))
+            return rc;
     }
     {
         const long long per_cta = 256ll * kFwdLP;
@@ -818,10 +827,10 @@ int treep_tiles(dwt_plan_s* Pl, const MapP& I0, const std::vector<MapP>& Qmap, i
         LaunchScope ls("tree_read", st);
         k_treep_read<P><<<fg, 256, 0, st>>>(K, dmaps, dmaps + 1, flags, Pl->d_W, Pl->d_cls, N, m, s, ng);
     }
-    DWT_CK_LAUNCH("tiled coset tables");
+    if ((rc = ck(cudaGetLastError(), "tiled coset tables"))) return rc;
     unsigned hf[4] = {0, 0, 0, 0};
-    DWT_CK(cudaMemcpyAsync(hf, flags, 16, cudaMemcpyDeviceToHost, st));
-    DWT_CK(cudaStreamSynchronize(st));
+    if ((rc = ck(cudaMemcpyAsync(hf, flags, 16, cudaMemcpyDeviceToHost, st), "cudaMemcpyAsync"))) return rc;
+    if ((rc = ck(cudaStreamSynchronize(st), "cudaStreamSynchronize"))) return rc;
     cleanup();
     if (hf[2]) {
         set_error("tiled coset tables: a grid-wide wait gave up");
