@@ -67,7 +67,7 @@ typedef struct dwt_plan_s *dwt_plan_t;
 
 /*
  * dwt_plan: build a plan for the digital net P(C) of Def. 1.1 (eq. defy).
- *   p: prime, 2 <= p <= 13;  m >= 1 with p^m <= 2^31;  1 <= s <= 255.
+ *   p: prime, 2 <= p <= 31;  m >= 1 with p^m <= 2^31;  1 <= s <= 255.
  *   C: HOST array uint8 [s][m][m], C[j][i][c] in 0..p-1.  Row i of C_j gives
  *      the point digit y_{j,n,i+1}; column c multiplies the index digit n_c.
  *   flags: DWT_PLAN_* bits.
