@@ -52,7 +52,7 @@ extern "C" {
 #define DWT_ECUDA 4         /* a CUDA call failed (message in dwt_last_error) */
 #define DWT_ETIMEOUT 5      /* a bounded device-side wait expired */
 #define DWT_EBUSY 6         /* serving queue full */
-#define DWT_EUNSUPPORTED 7  /* valid request this build does not serve (e.g. I32 with p != 2) */
+#define DWT_EUNSUPPORTED 7  /* valid request the library does not serve (e.g. I32 with p != 2) */
 
 typedef enum { DWT_F32 = 0, DWT_F64 = 1, DWT_I32 = 2, DWT_C64 = 3, DWT_C128 = 4 } dwt_dtype;
 typedef enum { DWT_ALGO_AUTO = 0, DWT_ALGO_BUTTERFLY = 1, DWT_ALGO_TC_SPLIT_BF16 = 2 } dwt_algo;
